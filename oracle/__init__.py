@@ -1,0 +1,298 @@
+"""FP64 CPU oracle for the pore-scale CDI model of arXiv 2110.13055.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, the smoke check and the
+benchmark's CPU-baseline leg may import this package.  The product path (the
+CUDA library and its binding) never touches it, and it shares no code with
+that path: the heavy loops live in ``cdi_oracle.c`` (plain C, FP64), built
+here with gcc; the light post-processing below is plain numpy.
+
+Every function cites the passage it follows (Sec./Eq. of the paper).  The
+readings taken where the paper is silent are listed at the top of
+``cdi_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cdi_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+# Physical constants.  e and k_B are the values printed with Eq. 9-10.
+E_CHARGE = 1.6e-19      # C
+K_B = 1.38e-23          # J/K
+FARADAY = 96485.0       # C/mol
+EPS0 = 8.854e-12        # F/m
+T_DEFAULT = 298.15      # K (the paper's temperature unit is garbled; kelvin)
+EPS_R_DEFAULT = 78.5    # water (not stated in the paper)
+
+
+def thermal_voltage(T=T_DEFAULT):
+    """k_B T / e, the scale of psi in Eq. 3 and Eq. 9."""
+    return K_B * T / E_CHARGE
+
+
+def debye_length(c_bulk, T=T_DEFAULT, eps_r=EPS_R_DEFAULT):
+    """The length in the exponent of Eq. 10: sqrt(eps_r eps0 k_B T / (2 C e F))."""
+    return np.sqrt(eps_r * EPS0 * K_B * T / (2.0 * c_bulk * E_CHARGE * FARADAY))
+
+
+def build(force: bool = False) -> str:
+    """Compile ``cdi_oracle.c`` into ``_build/liboracle.so`` with gcc."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
+        lib.orc_lbm.argtypes = [i, i, i, i, P, i, i, d, d, d, i, l, P, P, P]
+        lib.orc_lbm.restype = i
+        lib.orc_psi.argtypes = [i, i, i, i, P, i, d, d, d, i, P, P, P]
+        lib.orc_psi.restype = i
+        lib.orc_np_dt.argtypes = [i, i, i, i, P, i, P, P, i, P, P, d, d, d, d]
+        lib.orc_np_dt.restype = d
+        lib.orc_np_run.argtypes = [i, i, i, i, P, i, P, P, i, P, P, d, d, d, d,
+                                   d, l, P, P, P, P]
+        lib.orc_np_run.restype = i
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dims(mask: np.ndarray):
+    if mask.ndim == 2:
+        ny, nx = mask.shape
+        return 2, nx, ny, 1
+    nz, ny, nx = mask.shape
+    return 3, nx, ny, nz
+
+
+def _mask(mask):
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    if m.min(initial=0) < 0 or m.max(initial=0) > 1:
+        raise ValueError("mask values must be 0 (pore) or 1 (solid)")
+    return m
+
+
+# --------------------------------------------------------------------------
+# Flow (Sec. 2, Eq. 1-2 solved by Eq. 7-8)
+# --------------------------------------------------------------------------
+def lbm(mask, *, mirror=True, lateral_walls=False, tau=1.0, force=1e-6,
+        tol=1e-8, check_every=100, max_steps=2_000_000):
+    """Steady Stokes flow by the lattice Boltzmann method (Eq. 7-8, bounce-back
+    and body force of Sec. 2).
+
+    Returns ``(u_flow, steps, residual, status)``; ``u_flow`` has shape
+    ``(dim,) + flow_grid_shape`` in lattice units, where the flow grid is the
+    mask followed by its mirror image along x when ``mirror``.  ``status`` is 0
+    when converged (or when ``tol <= 0`` and ``max_steps`` were run), 1 when
+    ``tol`` was not reached.
+    """
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    NX = 2 * nx if mirror else nx
+    shape = (ny, NX) if dim == 2 else (nz, ny, NX)
+    u = np.zeros((dim,) + shape, dtype=np.float64)
+    steps = ctypes.c_long(0)
+    res = ctypes.c_double(0.0)
+    st = _load().orc_lbm(dim, nx, ny, nz, _ptr(m), int(mirror), int(lateral_walls),
+                         float(tau), float(force), float(tol), int(check_every),
+                         int(max_steps), _ptr(u), ctypes.byref(steps),
+                         ctypes.byref(res))
+    if st < 0:
+        raise ValueError("orc_lbm rejected its arguments")
+    return u, steps.value, res.value, st
+
+
+def velocity_export(mask, u_flow, U_target):
+    """Scale the lattice velocity on the original (unmirrored) grid so that the
+    pore-mean x velocity U = sum u / (N phi) of Sec. 4 equals ``U_target``
+    (m/s).  Returns ``(u_phys, U_lattice)``; u_phys is 0 in solid cells."""
+    m = _mask(mask)
+    nx = m.shape[-1]
+    u = np.array(u_flow[..., :nx], dtype=np.float64)
+    pore = m == 0
+    n_pore = int(pore.sum())
+    U_lat = float(u[0][pore].sum() / n_pore) if n_pore else 0.0
+    if U_target == 0.0:
+        return np.zeros_like(u), U_lat
+    if U_lat == 0.0:
+        raise ValueError("no net flow through the pore space")
+    u_phys = u * (U_target / U_lat)
+    u_phys[:, ~pore] = 0.0
+    return u_phys, U_lat
+
+
+# --------------------------------------------------------------------------
+# Potential (Eq. 4-5, Dirichlet at the solid surface)
+# --------------------------------------------------------------------------
+def psi(mask, psi_s, *, dx=1e-7, c_bulk=10.0, T=T_DEFAULT, eps_r=EPS_R_DEFAULT,
+        mode="debye", lambda_D=None, lateral_walls=False, tol=1e-13,
+        max_iter=200000):
+    """Frozen potential field in volts (0 in solid cells).
+
+    ``mode='debye'`` screens Eq. 4 with the Debye length of Eq. 10 (or
+    ``lambda_D`` when given); ``mode='laplace'`` solves Eq. 4 with zero charge
+    (the electroneutral initial state)."""
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    if mode == "laplace":
+        kdx2 = 0.0
+    else:
+        lam = lambda_D if lambda_D else debye_length(c_bulk, T, eps_r)
+        kdx2 = (dx / lam) ** 2
+    out = np.zeros(m.shape, dtype=np.float64)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _load().orc_psi(dim, nx, ny, nz, _ptr(m), int(lateral_walls), float(psi_s),
+                         float(kdx2), float(tol), int(max_iter), _ptr(out),
+                         ctypes.byref(it), ctypes.byref(rel))
+    if st < 0:
+        raise ValueError("orc_psi rejected its arguments")
+    return out, it.value, rel.value
+
+
+# --------------------------------------------------------------------------
+# Transport (Eq. 3) with adsorption (Eq. 6)
+# --------------------------------------------------------------------------
+def _species(z, D):
+    z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.int32)
+    D = np.ascontiguousarray(np.atleast_1d(D), dtype=np.float64)
+    assert z.shape == D.shape
+    return z, D
+
+
+def np_dt(mask, u, psi_field, z, D, *, dx=1e-7, Ka=1e-6, T=T_DEFAULT,
+          lateral_walls=False, safety=0.9):
+    """Explicit step: ``safety`` over the largest outflow rate of any cell."""
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    z, D = _species(z, D)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    p = np.ascontiguousarray(psi_field, dtype=np.float64)
+    return _load().orc_np_dt(dim, nx, ny, nz, _ptr(m), int(lateral_walls), _ptr(u),
+                             _ptr(p), len(z), _ptr(z), _ptr(D), float(dx),
+                             float(Ka), thermal_voltage(T), float(safety))
+
+
+def np_run(mask, u, psi_field, z, D, *, c0, dt, n_steps, dx=1e-7, Ka=1e-6,
+           T=T_DEFAULT, lateral_walls=False, C=None, acc=None):
+    """Advance ``n_steps`` explicit Nernst-Planck steps.
+
+    Starts from C = c0 in every pore cell (the saturated initial state of
+    Sec. 4) unless ``C`` is given.  Returns ``(C, Gamma, In, Out)``; C has shape
+    ``(ns,) + mask.shape`` (mol/m^3); Gamma, In, Out are per species (mol, or
+    mol per metre of depth in 2D), accumulated onto ``acc`` when given."""
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    z, D = _species(z, D)
+    ns = len(z)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    p = np.ascontiguousarray(psi_field, dtype=np.float64)
+    if C is None:
+        C = np.where(m[None] == 0, float(c0), 0.0) * np.ones((ns,) + m.shape)
+    C = np.ascontiguousarray(C, dtype=np.float64).copy()
+    if acc is None:
+        acc = (np.zeros(ns), np.zeros(ns), np.zeros(ns))
+    G, I, O = (np.ascontiguousarray(a, dtype=np.float64).copy() for a in acc)
+    st = _load().orc_np_run(dim, nx, ny, nz, _ptr(m), int(lateral_walls), _ptr(u),
+                            _ptr(p), ns, _ptr(z), _ptr(D), float(dx), float(Ka),
+                            float(c0), thermal_voltage(T), float(dt),
+                            int(n_steps), _ptr(C), _ptr(G), _ptr(I), _ptr(O))
+    if st < 0:
+        raise ValueError("orc_np_run rejected its arguments")
+    return C, G, I, O
+
+
+# --------------------------------------------------------------------------
+# Outputs (Sec. 4.1: outlet concentration, salt removal, averaged profiles)
+# --------------------------------------------------------------------------
+def outlet_concentration(mask, u, C):
+    """Flux-weighted concentration over the pore cells of the outlet column:
+    sum u_x C / sum u_x.  Falls back to the plain mean when sum u_x = 0."""
+    m = _mask(mask)
+    pore = m[..., -1] == 0
+    ux = u[0][..., -1][pore]
+    out = []
+    for Ci in C:
+        c = Ci[..., -1][pore]
+        s = ux.sum()
+        out.append(float((ux * c).sum() / s) if s != 0.0 else float(c.mean()))
+    return np.array(out)
+
+
+def salt_removal(c_in, c_out):
+    """P_rm = (C_in - C_out) / C_in (Sec. 4.1)."""
+    return (c_in - c_out) / c_in
+
+
+def mass(mask, C, dx):
+    """Dissolved amount per species: sum over pore cells of C dx^d (per metre
+    of depth in 2D)."""
+    m = _mask(mask)
+    vol = dx ** m.ndim
+    return np.array([float(Ci[m == 0].sum() * vol) for Ci in C])
+
+
+def column_means(mask, C):
+    """Mean over the pore cells of each x column (the vertically averaged
+    profile of Fig. 6 and Fig. 9)."""
+    m = _mask(mask)
+    pore = (m == 0)
+    axes = tuple(range(m.ndim - 1))
+    cnt = pore.sum(axis=axes)
+    out = []
+    for Ci in C:
+        s = np.where(pore, Ci, 0.0).sum(axis=axes)
+        out.append(np.where(cnt > 0, s / np.maximum(cnt, 1), 0.0))
+    return np.array(out)
+
+
+def run_case(mask, *, mirror=True, lateral_walls=False, tau=1.0, force=1e-6,
+             flow_tol=1e-8, check_every=100, max_flow_steps=2_000_000,
+             U_target=1e-4, applied_V=1.0, c0=10.0, z=(1, -1),
+             D=(1.33e-9, 2.03e-9), Ka=1e-6, dx=1e-7, T=T_DEFAULT,
+             eps_r=EPS_R_DEFAULT, psi_mode="debye", lambda_D=None,
+             psi_tol=1e-13, n_np_steps=2000, dt=None):
+    """The whole path on one geometry: flow to steady state, velocity scaling,
+    frozen potential (surface value -applied_V), time step, n_np_steps
+    transport steps, then the outputs.  Returns a dict."""
+    u_flow, steps, res, st = lbm(mask, mirror=mirror, lateral_walls=lateral_walls,
+                                 tau=tau, force=force, tol=flow_tol,
+                                 check_every=check_every, max_steps=max_flow_steps)
+    u, U_lat = velocity_export(mask, u_flow, U_target)
+    ps, it, rel = psi(mask, -applied_V, dx=dx, c_bulk=c0, T=T, eps_r=eps_r,
+                      mode=psi_mode, lambda_D=lambda_D,
+                      lateral_walls=lateral_walls, tol=psi_tol)
+    if dt is None:
+        dt = np_dt(mask, u, ps, z, D, dx=dx, Ka=Ka, T=T, lateral_walls=lateral_walls)
+    C, G, I, O = np_run(mask, u, ps, z, D, c0=c0, dt=dt, n_steps=n_np_steps,
+                        dx=dx, Ka=Ka, T=T, lateral_walls=lateral_walls)
+    return dict(u_flow=u_flow, flow_steps=steps, flow_residual=res, flow_status=st,
+                u=u, U_lattice=U_lat, psi=ps, psi_iters=it, psi_relres=rel, dt=dt,
+                C=C, Gamma=G, In=I, Out=O,
+                C_out=outlet_concentration(mask, u, C),
+                M=mass(mask, C, dx), M0=mass(mask, np.where(np.asarray(mask)[None] == 0, c0, 0.0)
+                                               * np.ones((len(z),) + np.asarray(mask).shape), dx))
