@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled pore-scale CDI path on GB300.
+
+One step = the whole hot path on one synthetic electrode image: Stokes flow
+by lattice Boltzmann to steady state, the potential solve, the explicit time
+step bound, the Nernst-Planck transport steps, and the outputs (adsorbed
+amount, outlet concentration, mass balance).  The metric is coupled
+lattice-site updates per second,
+    (flow steps x flow sites + transport steps x cells) / time,
+in MLUPS, with the dominant kernel's bandwidth against the measured HBM peak.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   (the FP64 CPU oracle, as it stands)
+
+Under torchrun each rank runs its own instance (independent problems, no
+data-path collective; weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2110_13055_gb300 import cdi, inputs  # noqa: E402
+
+METRIC = "coupled MLUPS & % HBM peak; sweep solves/s + p99 latency vs plain, equal error"
+
+WORKLOADS = {
+    "2d-1024x512": dict(
+        desc=("2D 1024x512 polydisperse discs r~U[4,16] lu (overlap), porosity 0.5, seed 1; "
+              "D2Q9 BGK tau=1, body force 1e-6 lu, Stokes to K-lag residual 1e-8 (FP64 "
+              "residual, K=100), mirror along x, periodic laterally; screened potential at "
+              "0.8 V (c_bulk 10 mol/m^3, dx 100 nm); Na+/Cl- z=+1/-1, D=1.33e-9/2.03e-9 m^2/s, "
+              "c0=10 mol/m^3, Ka=1e-6 m/s, pore-mean velocity 1e-4 m/s; 50000 explicit "
+              "Nernst-Planck steps; FP32 storage"),
+        mask=lambda: inputs.disc_pack_1024x512()[0], prec=cdi.FP32, V=0.8, U=1e-4, c0=10.0,
+        np_steps=50000, flow_tol=1e-8, max_flow=1_000_000),
+    "2d-128x64": dict(
+        desc=("2D 128x64 non-overlapping discs r=6 lu, porosity 0.6, seed 0; D2Q9 tau=1, "
+              "Stokes to residual 1e-8; 1.0 V; Na+/Cl-, c0=10 mol/m^3; 2000 Nernst-Planck "
+              "steps; FP64"),
+        mask=lambda: inputs.disc_pack_128x64()[0], prec=cdi.FP64, V=1.0, U=1e-4, c0=10.0,
+        np_steps=2000, flow_tol=1e-8, max_flow=1_000_000),
+}
+
+Z, D = (1, -1), (1.33e-9, 2.03e-9)
+REASONS = {  # nvidia-smi clocks_event_reasons bit names
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+    0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+    0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting"}
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class Clocks:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) every 200 ms."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[2], 16)
+            except ValueError:
+                continue
+            for b, name in REASONS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2110_13055_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("csrc_sha") != csrc_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_pipeline(dom, w):
+    """The hot path on a resident domain; returns the step's counters."""
+    steps, res, st = dom.solve_flow(tol=w["flow_tol"], max_steps=w["max_flow"],
+                                    U_target=w["U"], allow_not_converged=True)
+    dom.set_potential(w["V"], c_bulk=w["c0"], tol=1e-12)
+    dom.init_transport(Z, D, c0=w["c0"], Ka=1e-6)
+    dom.step(w["np_steps"])
+    G = dom.adsorbed()
+    Cout = dom.outlet()
+    M, _, I, O = dom.mass_balance()
+    return dict(flow_steps=steps, flow_residual=res, flow_status=st, Gamma=G, C_out=Cout)
+
+
+def ours(args, w, mask):
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    res = cdi.TorchResources(local)
+    dim = mask.ndim
+    nx = mask.shape[-1]
+    N = mask.size
+    n_pore = int((mask == 0).sum())
+    Nf = 2 * N
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    dom = cdi.Domain(mask, precision=w["prec"], torch_resources=res)
+    for _ in range(args.warmup):
+        run_pipeline(dom, w)
+    torch.cuda.synchronize()
+    dom.timing(reset=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    units = 0
+    info = None
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(res.stream)
+        for _ in range(args.steps):
+            with torch.cuda.stream(res.stream):
+                flush.zero_()          # evict the previous step's data from L2
+            info = run_pipeline(dom, w)
+            units += info["flow_steps"] * Nf + w["np_steps"] * N
+        ev1.record(res.stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    dev_ms = ev0.elapsed_time(ev1)
+    tim = dom.timing(reset=True)
+    elapsed = dev_ms / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed, float(units)], dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        elapsed_all, units_all = tmax[0].item(), t[1].item()
+    else:
+        elapsed_all, units_all = elapsed, float(units)
+
+    # dominant kernel and its roofline
+    T = 4 if w["prec"] == cdi.FP32 else 8
+    Q = 9 if dim == 2 else 19
+    flag_b = 2 if dim == 2 else 4
+    lbm_bytes = 2 * n_pore * Q * 2 * T + Nf * flag_b
+    np_bytes = n_pore * (2 * 2 * T + dim * T + T + 1) + (N - n_pore)
+    lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
+    np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3
+    if tim["flow_ms"] >= tim["np_ms"]:
+        kname, abytes, avg = "k_lbm_step", lbm_bytes, lbm_avg
+    else:
+        kname, abytes, avg = "k_np_step", np_bytes, np_avg
+    peak, peak_kind = measured_peak_gbs()
+    achieved = abytes / avg / 1e9 if avg > 0 else 0.0
+    traffic = recorded_traffic(kname)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            d2 = cdi.Domain(mask, precision=w["prec"], torch_resources=res)   # H2D of the mask
+            run_pipeline(d2, w)
+            C = d2.C()                                                          # D2H of the fields
+            d2.close()
+            d2h = C.nbytes + 8 * 2 * 6
+        torch.cuda.synchronize()
+        e2e_t = time.perf_counter() - t0
+        e2e = {"value": units / args.steps * args.e2e_steps / e2e_t / 1e6 * world,
+               "unit": "MLUPS", "h2d_bytes_per_step": int(mask.nbytes),
+               "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+    dom.close()
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC,
+        "value": units_all / elapsed_all / 1e6,
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if w["prec"] == cdi.FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "name": args.workload,
+                   "flow_sites": Nf, "cells": N, "pore_cells": n_pore,
+                   "flow_steps": info["flow_steps"], "flow_residual": info["flow_residual"],
+                   "flow_converged": info["flow_status"] == 0,
+                   "np_steps": w["np_steps"], "Gamma_mol_per_m": list(info["Gamma"]),
+                   "C_out_molm3": list(info["C_out"]),
+                   "l2": "flushed between steps (256 MB write); working set is L2-resident "
+                         "within a step",
+                   "phase_ms_per_step": {
+                       "flow": tim["flow_ms"] / args.steps,
+                       "flow_check": tim["flow_check_ms"] / args.steps,
+                       "psi": tim["psi_ms"] / args.steps,
+                       "np": tim["np_ms"] / args.steps},
+                   "wall_s": wall},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": abytes,
+                     "avg_launch_us": avg * 1e6,
+                     "other": {"k_lbm_step_GBps": lbm_bytes / lbm_avg / 1e9 if lbm_avg else None,
+                               "k_np_step_GBps": np_bytes / np_avg / 1e9 if np_avg else None}},
+        "e2e": e2e,
+        "gpu_launches": int(tim["kernel_launches"]),
+        "clocks": clk.summary(),
+    }
+    return line
+
+
+def oracle_sample(mask, w, flow_steps, np_steps):
+    """Time the FP64 oracle as it stands on a bounded sample of the workload:
+    flow_steps LBM steps on the full flow grid, the potential solve, np_steps
+    transport steps on the full grid.  Returns (MLUPS, seconds, sample text)."""
+    import oracle as O
+    O.build()
+    N = mask.size
+    t0 = time.perf_counter()
+    uf, *_ = O.lbm(mask, tol=0.0, check_every=flow_steps, max_steps=flow_steps)
+    u, _ = O.velocity_export(mask, uf, w["U"])
+    ps, *_ = O.psi(mask, -w["V"], c_bulk=w["c0"], tol=1e-12)
+    dt = O.np_dt(mask, u, ps, Z, D)
+    O.np_run(mask, u, ps, Z, D, c0=w["c0"], dt=dt, n_steps=np_steps)
+    t = time.perf_counter() - t0
+    units = flow_steps * 2 * N + np_steps * N
+    return units / t / 1e6, t, (f"{flow_steps} LBM steps on the full {2 * N}-site flow grid + "
+                                f"potential solve + {np_steps} transport steps on {N} cells")
+
+
+def reference(args, w, mask):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return None
+    fs, ns = args.ref_flow_steps, args.ref_np_steps
+    for _ in range(args.warmup):
+        oracle_sample(mask, w, max(2, fs // 10) // 2 * 2, max(1, ns // 10))
+    vals, ts = [], []
+    for _ in range(args.steps):
+        v, t, sample = oracle_sample(mask, w, fs, ns)
+        vals.append(v)
+        ts.append(t)
+    value = float(np.mean(vals))
+    return {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(ts)) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w["desc"], "name": args.workload},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d-1024x512", choices=list(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-flow-steps", type=int, default=100)
+    ap.add_argument("--ref-np-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_info()
+    w = WORKLOADS[args.workload]
+    mask = w["mask"]()
+    if args.impl == "reference":
+        # the oracle runs on rank 0 alone; the other ranks exit without work
+        line = reference(args, w, mask)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if True:
+        line = ours(args, w, mask)
+        if line is not None and not args.no_cpu_baseline and world == 1:
+            v, t, sample = oracle_sample(mask, w, args.ref_flow_steps, args.ref_np_steps)
+            line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                    "sample": sample, "seconds": t}
+        elif line is not None:
+            line["cpu_baseline"] = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * cdi.h - C ABI of the GB300 pore-scale capacitive-deionization solver.
+ *
+ * Method: Liu, Waugh, Komini Babu, Spendelow, Kang, "Numerical Modeling of Ion
+ * Transport and Adsorption in Porous Media: A Pore-scale Study for Capacitive
+ * Deionization Desalination" (arXiv 2110.13055).
+ *
+ * One domain = one voxel image of a porous electrode.  The calls follow the
+ * paper's pipeline:
+ *   cdi_create_domain   voxel mask in (Sec. 2: one grid block per voxel)
+ *   cdi_solve_flow      Stokes flow by lattice Boltzmann to steady state
+ *                       (Sec. 2, Eq. 1-2 solved with Eq. 7-8, bounce-back,
+ *                       body force, mirror image along the flow axis)
+ *   cdi_set_potential   electric potential (Eq. 4-5, Dirichlet at the solid)
+ *   cdi_init_transport  species, feed concentration, adsorption constant,
+ *                       explicit time step (Sec. 4: saturated initial state)
+ *   cdi_step_transport  explicit finite-volume Nernst-Planck steps (Eq. 3)
+ *                       with the adsorption flux of Eq. 6 at solid faces
+ *   cdi_query_*         adsorbed amount, outlet concentration (Sec. 4.1),
+ *                       mass balance, vertically averaged profiles
+ *
+ * Conventions
+ *   - Grids are x-fastest: cell (x,y,z) is element ((z*ny)+y)*nx + x; x is the
+ *     flow direction (inlet at x = -1/2, outlet at x = nx - 1/2).
+ *   - The mask is uint8, 1 = solid (carbon), 0 = pore; host memory owned by
+ *     the caller and copied by cdi_create_domain.
+ *   - All device memory belongs to the domain.  It is obtained from the
+ *     caller's allocator when one is given, else from cudaMalloc; everything
+ *     is released by cdi_destroy_domain.
+ *   - Work runs on the domain's stream: the caller's stream if given, else a
+ *     stream the domain creates.  cdi_step_transport returns without waiting;
+ *     the queries and cdi_copy_field wait for the stream.
+ *   - Calls on one domain must not overlap (not thread-safe per domain);
+ *     different domains are independent.
+ *   - Every call returns a cdi_status; on failure cdi_last_error(dom) gives a
+ *     message (cdi_last_error(NULL) for failures of cdi_create_domain).
+ *     A call made out of order (e.g. stepping before cdi_init_transport)
+ *     returns CDI_ERR_STATE and changes nothing.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     computes returns CDI_ERR_CUDA.
+ */
+#ifndef CDI_H
+#define CDI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cdi_domain cdi_domain; /* opaque; owned by the library */
+
+typedef enum {
+  CDI_OK = 0,
+  CDI_ERR_INVALID_ARG = 1,   /* bad sizes, values or null pointers */
+  CDI_ERR_OOM = 2,           /* an allocation failed; nothing leaked */
+  CDI_ERR_CUDA = 3,          /* a CUDA call failed (message has the detail) */
+  CDI_ERR_NOT_CONVERGED = 4, /* max_steps / max_iter reached; state is valid */
+  CDI_ERR_TIMEOUT = 5,       /* reserved for bounded device-side waits */
+  CDI_ERR_STATE = 6          /* call out of order */
+} cdi_status;
+
+typedef enum {
+  CDI_FP64 = 0, /* populations, velocity, potential, concentrations in FP64 */
+  CDI_FP32 = 1  /* the same fields stored and updated in FP32; reductions,
+                   the potential solve and all accumulators stay FP64 */
+} cdi_precision;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns NULL on failure; free receives the pointer and its size. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *ctx);
+  void *ctx;
+} cdi_allocator;
+
+typedef struct {
+  int dim;           /* 2 (D2Q9, 5-point faces) or 3 (D3Q19, 7-point) */
+  int nx, ny, nz;    /* voxels; nz must be 1 when dim == 2 */
+  double dx_m;       /* voxel edge in metres (> 0) */
+  int lateral_walls; /* 0: y (and z) periodic; 1: inert walls there */
+  int mirror_x;      /* 1: flow grid = image + its mirror image along x,
+                        periodic in x (Sec. 2's mirror boundary); 0: the image
+                        alone, periodic in x */
+  int precision;     /* cdi_precision */
+} cdi_domain_desc;
+
+/* Lattice Boltzmann flow parameters (Sec. 2, Eq. 7-8). */
+typedef struct {
+  double tau;          /* BGK relaxation time (> 1/2); nu = (tau - 1/2) / 3 */
+  double force_lu;     /* body force along x in lattice units (the pressure
+                          gradient of Sec. 2); the flow is linear in it */
+  double tol;          /* steady state when ||u(t)-u(t-K)|| / ||u(t)|| < tol
+                          over pore sites; tol <= 0 runs exactly max_steps */
+  int check_every;     /* K: even, >= 2 */
+  int64_t max_steps;   /* multiple of check_every, >= 0 */
+  double U_target_mps; /* pore-mean x velocity U = sum(u) / (N phi) of Sec. 4
+                          that the lattice velocity is scaled to (m/s) */
+} cdi_flow_params;
+
+/* Potential parameters (Eq. 4-5, Eq. 10). */
+typedef struct {
+  double T_K;          /* temperature (K) */
+  double eps_r;        /* relative permittivity of the solution */
+  double c_bulk_molm3; /* bulk salt concentration setting the Debye length of
+                          Eq. 10's exponent */
+  double lambda_D_m;   /* > 0 overrides that Debye length */
+  int mode;            /* 0: screened (Debye-Hueckel) field; 1: Laplace */
+  double tol;          /* relative residual of the conjugate-gradient solve */
+  int max_iter;
+} cdi_elec_params;
+
+typedef struct {
+  int z;        /* valence (Eq. 3) */
+  double D_m2s; /* diffusion coefficient (Eq. 3) */
+} cdi_species;
+
+/* Field ids for cdi_copy_field (all copied out as double). */
+enum {
+  CDI_FIELD_U_LATTICE = 0, /* dim*NX*ny*nz: flow-grid velocity, lattice units,
+                              component-major; NX = 2 nx with mirror_x */
+  CDI_FIELD_U = 1,         /* dim*nx*ny*nz: scaled velocity (m/s) */
+  CDI_FIELD_PSI = 2,       /* nx*ny*nz: potential (V), 0 in solid */
+  CDI_FIELD_C = 3          /* CDI_FIELD_C + k: species k concentration
+                              (mol/m^3), nx*ny*nz, 0 in solid */
+};
+
+typedef struct {
+  double flow_ms;      /* device time of the LBM step kernels */
+  int64_t flow_launches;
+  double flow_check_ms;/* device time of the residual checks */
+  double psi_ms;       /* device time of the potential solve */
+  int64_t psi_iters;
+  double np_ms;        /* device time of the Nernst-Planck step kernels */
+  int64_t np_launches;
+  int64_t kernel_launches; /* all kernels this domain launched */
+} cdi_timing;
+
+/* Create a domain from a voxel mask (Sec. 2: marker-and-cell grid, one grid
+ * block per image voxel).  Copies the mask to the device, builds the flow
+ * and face neighbour tables there and allocates every field.  The mask needs
+ * at least one pore cell in the inlet column x = 0.  stream: a cudaStream_t
+ * or NULL.  On success *out owns the domain. */
+cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
+                             const cdi_allocator *alloc, void *stream,
+                             cdi_domain **out);
+
+/* Run the lattice Boltzmann Stokes solve from rest (Sec. 2, Eq. 7-8): BGK
+ * collision with the Stokes-linear equilibrium, halfway bounce-back at solid
+ * links, body force along x, mirror domain.  Stops at the first residual
+ * check below tol, else after max_steps (CDI_ERR_NOT_CONVERGED, state kept).
+ * Then scales the velocity to U_target_mps.  Blocks until done.
+ * steps_out / residual_out may be NULL. */
+cdi_status cdi_solve_flow(cdi_domain *dom, const cdi_flow_params *p,
+                          int64_t *steps_out, double *residual_out);
+
+/* Rescale the solved Stokes field to another pore-mean velocity (the flow is
+ * linear in the force, so one solve serves every velocity).  Requires a
+ * solved flow; invalidates an initialised transport state. */
+cdi_status cdi_set_velocity(cdi_domain *dom, double U_target_mps);
+
+/* Solve the potential with surface value psi_s = -applied_V on every solid
+ * face (Eq. 4 with the Dirichlet condition of Sec. 2), psi = 0 in the inlet
+ * feed, no flux through the outlet and lateral walls.  Invalidates an
+ * initialised transport state.  iters_out / relres_out may be NULL. */
+cdi_status cdi_set_potential(cdi_domain *dom, double applied_V,
+                             const cdi_elec_params *p, int *iters_out,
+                             double *relres_out);
+
+/* Set up transport (Sec. 4): n_species (1..4) ions, every pore cell at c0
+ * (the saturated start), feed at c0, adsorption constant Ka (Eq. 6) on every
+ * solid face.  dt_s > 0 fixes the time step; dt_s == 0 takes
+ * 0.9 / (largest outflow rate of any cell and species), which keeps the
+ * explicit update positive.  Needs a solved flow (or U_target 0 and no flow
+ * solve: then u = 0) and a potential.  Resets Gamma/In/Out to zero. */
+cdi_status cdi_init_transport(cdi_domain *dom, const cdi_species *sp,
+                              int n_species, double c0_molm3, double Ka_mps,
+                              double dt_s, double *dt_used);
+
+/* Advance n_steps >= 0 explicit steps (Eq. 3 with Eq. 6); asynchronous. */
+cdi_status cdi_step_transport(cdi_domain *dom, int64_t n_steps);
+
+/* Adsorbed amount per species since cdi_init_transport: mol (3D) or mol per
+ * metre of depth (2D).  Waits for the stream. */
+cdi_status cdi_query_adsorbed(cdi_domain *dom, double *per_species);
+
+/* Outlet concentration per species (Sec. 4.1), flux weighted over the pore
+ * cells of the last column: sum(u_x C) / sum(u_x) (plain mean if the sum of
+ * u_x is 0).  Waits for the stream. */
+cdi_status cdi_query_outlet(cdi_domain *dom, double *per_species);
+
+/* Per species: dissolved amount M = sum C dx^d, adsorbed Gamma, inflow In
+ * and outflow Out (all FP64; M + Gamma + Out - In is conserved).  Any
+ * pointer may be NULL.  Waits for the stream. */
+cdi_status cdi_query_mass_balance(cdi_domain *dom, double *M, double *Gamma,
+                                  double *In, double *Out);
+
+/* Vertically averaged profile (Fig. 6, Fig. 9): the mean of species k over
+ * the pore cells of each x column into out[nx] (0 for all-solid columns). */
+cdi_status cdi_query_column_means(cdi_domain *dom, int species, double *out);
+
+/* Copy a field to host memory as doubles (layouts in the CDI_FIELD_* list).
+ * count is the number of doubles host_dst holds; it must match exactly. */
+cdi_status cdi_copy_field(cdi_domain *dom, int field, double *host_dst,
+                          size_t count);
+
+/* Device-time counters (CUDA events on the domain stream) since the last
+ * reset; waits for the stream.  reset != 0 zeroes them afterwards. */
+cdi_status cdi_query_timing(cdi_domain *dom, cdi_timing *out, int reset);
+
+/* Message for the last failed call on dom (NULL: the last failed create on
+ * this thread).  Valid until the next call on the same domain. */
+const char *cdi_last_error(const cdi_domain *dom);
+
+/* Release the domain and all its device memory.  NULL is ignored. */
+void cdi_destroy_domain(cdi_domain *dom);
+
+/* ABI version (major * 100 + minor). */
+int cdi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDI_H */

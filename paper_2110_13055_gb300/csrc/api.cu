@@ -1,0 +1,485 @@
+// C ABI of the CDI library: domain lifecycle, argument checking, errors,
+// device memory, event timing, field copies and queries.  The numerical work
+// lives in flow.cu, potential.cu and transport.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "cdi_internal.cuh"
+
+static thread_local std::string g_create_error;
+
+cdi_status cdi_fail(cdi_domain *d, cdi_status s, const std::string &msg) {
+  if (d)
+    d->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+cdi_status cdi_cuda_fail(cdi_domain *d, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                  cudaGetErrorString(e) + ")";
+  (void)cudaGetLastError();
+  return cdi_fail(d, e == cudaErrorMemoryAllocation ? CDI_ERR_OOM : CDI_ERR_CUDA, m);
+}
+
+void *cdi_dev_alloc(cdi_domain *d, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void *p = nullptr;
+  if (d->has_alloc) {
+    p = d->alloc.alloc(bytes, d->alloc.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) d->blocks.push_back({p, bytes});
+  return p;
+}
+
+static void free_all(cdi_domain *d) {
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  for (auto &b : d->blocks) {
+    if (d->has_alloc)
+      d->alloc.free(b.p, b.bytes, d->alloc.ctx);
+    else
+      cudaFree(b.p);
+  }
+  d->blocks.clear();
+  if (d->h_scal) cudaFreeHost(d->h_scal);
+  d->h_scal = nullptr;
+  if (d->flow_graph) cudaGraphExecDestroy(d->flow_graph);
+  if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
+  d->flow_graph = d->np_graph = nullptr;
+  for (auto &p : d->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  d->pending.clear();
+  for (auto e : d->ev_pool) cudaEventDestroy(e);
+  d->ev_pool.clear();
+  if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+  if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
+  d->cap_stream = d->stream = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Event timing: pairs of events on the domain stream around groups of
+// launches, resolved at the next synchronisation point.
+// ---------------------------------------------------------------------------
+static cudaEvent_t take_event(cdi_domain *d) {
+  if (!d->ev_pool.empty()) {
+    cudaEvent_t e = d->ev_pool.back();
+    d->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void cdi_timing_begin(cdi_domain *d, cudaEvent_t *a) {
+  *a = take_event(d);
+  cudaEventRecord(*a, d->stream);
+}
+
+void cdi_timing_end(cdi_domain *d, cudaEvent_t a, int phase, int64_t launches) {
+  cudaEvent_t b = take_event(d);
+  cudaEventRecord(b, d->stream);
+  d->pending.push_back({a, b, phase, launches});
+}
+
+cudaError_t cdi_timing_resolve(cdi_domain *d) {
+  for (auto &p : d->pending) {
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e != cudaSuccess) return e;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    switch (p.phase) {
+      case PH_FLOW: d->timing.flow_ms += ms; d->timing.flow_launches += p.launches; break;
+      case PH_CHECK: d->timing.flow_check_ms += ms; break;
+      case PH_PSI: d->timing.psi_ms += ms; d->timing.psi_iters += p.launches; break;
+      case PH_NP: d->timing.np_ms += ms; d->timing.np_launches += p.launches; break;
+    }
+    d->ev_pool.push_back(p.a);
+    d->ev_pool.push_back(p.b);
+  }
+  d->pending.clear();
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Conversion kernel for cdi_copy_field.
+// ---------------------------------------------------------------------------
+__global__ void k_to_double_f(const float *s, double *d, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    d[i] = (double)s[i];
+}
+
+cdi_status cdi_convert_to_double(cdi_domain *d, const void *src, int is_float, double *dst,
+                                 size_t n) {
+  if (!is_float) {
+    CDI_TRY(d, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, d->stream),
+            "copy field");
+    return CDI_OK;
+  }
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  if (blocks < 1) blocks = 1;
+  k_to_double_f<<<blocks, 256, 0, d->stream>>>((const float *)src, dst, n);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "convert field");
+  return CDI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int cdi_version(void) { return 100; }
+
+const char *cdi_last_error(const cdi_domain *d) {
+  return d ? d->err.c_str() : g_create_error.c_str();
+}
+
+cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
+                             const cdi_allocator *alloc, void *stream, cdi_domain **out) {
+  if (!out) return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc || !mask) return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "desc or mask is NULL");
+  const cdi_domain_desc &D = *desc;
+  if (D.dim != 2 && D.dim != 3)
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (D.nx < 1 || D.ny < 1 || D.nz < 1 || (D.dim == 2 && D.nz != 1))
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "bad grid size (nz must be 1 in 2D)");
+  if (D.ny > 65535 || D.nz > 65535)
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "ny and nz must be <= 65535");
+  if (!(D.dx_m > 0.0) || !std::isfinite(D.dx_m))
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "dx_m must be positive");
+  if (D.precision != CDI_FP64 && D.precision != CDI_FP32)
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "unknown precision");
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "allocator needs alloc and free");
+  const long long N = (long long)D.nx * D.ny * D.nz;
+  const int NX = D.mirror_x ? 2 * D.nx : D.nx;
+  const long long Nf = (long long)NX * D.ny * D.nz;
+  if (Nf > (1LL << 31) - 1)
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "grid too large (flow sites >= 2^31)");
+  long long n_pore = 0, n_inlet = 0;
+  for (long long i = 0; i < N; i++) {
+    if (mask[i] > 1) return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "mask values must be 0 or 1");
+    if (!mask[i]) {
+      n_pore++;
+      if (i % D.nx == 0) n_inlet++;
+    }
+  }
+  if (n_inlet == 0)
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "no pore cell in the inlet column x = 0");
+
+  cdi_domain *d = new cdi_domain();
+  d->dim = D.dim; d->nx = D.nx; d->ny = D.ny; d->nz = D.nz;
+  d->walls = D.lateral_walls ? 1 : 0;
+  d->mirror = D.mirror_x ? 1 : 0;
+  d->prec = D.precision;
+  d->dx = D.dx_m;
+  d->NX = NX; d->N = N; d->Nf = Nf;
+  d->n_pore = n_pore; d->n_pore_inlet = n_inlet;
+  if (alloc) {
+    d->alloc = *alloc;
+    d->has_alloc = true;
+  }
+  cudaError_t e;
+  if (stream) {
+    d->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cdi_cuda_fail(nullptr, e, "create stream");
+      delete d;
+      return CDI_ERR_CUDA;
+    }
+    d->own_stream = true;
+  }
+  e = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cdi_cuda_fail(nullptr, e, "create capture stream");
+    free_all(d);
+    delete d;
+    return CDI_ERR_CUDA;
+  }
+
+  const size_t T = d->prec == CDI_FP32 ? 4 : 8;
+  const int Q = D.dim == 2 ? 9 : 19;
+  const size_t fflag = D.dim == 2 ? 2 : 4;
+  d->np_blocks = (int)(((D.nx + cdi::kRowBlock - 1) / cdi::kRowBlock) * (long long)D.ny * D.nz);
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void *p = cdi_dev_alloc(d, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  d->d_mask = (uint8_t *)A(N);
+  d->d_fflags = A(Nf * fflag);
+  d->d_nflags = (uint8_t *)A(N);
+  d->d_g = A((size_t)Q * Nf * T);
+  d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
+  d->d_u = A((size_t)D.dim * N * T);
+  d->d_psi = (double *)A(N * 8);
+  d->d_phi = (double *)A(N * 8);
+  d->d_C[0] = A((size_t)cdi::kMaxSpecies * N * T);
+  d->d_C[1] = A((size_t)cdi::kMaxSpecies * N * T);
+  d->d_acc = (double *)A((size_t)3 * cdi::kMaxSpecies * d->np_blocks * 8);
+  d->d_part = (double *)A((size_t)16 * cdi::kRedBlocks * 8);
+  d->d_counter = (unsigned int *)A(16 * sizeof(unsigned int));
+  d->d_scal = (double *)A(64 * 8);
+  d->d_cg = (double *)A((size_t)4 * N * 8);
+  d->d_colout = (double *)A((size_t)D.nx * 8);
+  if (!ok) {
+    free_all(d);
+    delete d;
+    return cdi_fail(nullptr, CDI_ERR_OOM, "device allocation failed");
+  }
+  e = cudaMallocHost(&d->h_scal, 64 * 8);
+  if (e != cudaSuccess) {
+    cdi_cuda_fail(nullptr, e, "pinned scalars");
+    free_all(d);
+    delete d;
+    return CDI_ERR_CUDA;
+  }
+  std::memset(d->h_scal, 0, 64 * 8);
+  cdi_status s = CDI_OK;
+  auto chk = [&](cudaError_t ee, const char *w) {
+    if (s == CDI_OK && ee != cudaSuccess) s = cdi_cuda_fail(d, ee, w);
+  };
+  chk(cudaMemcpyAsync(d->d_mask, mask, N, cudaMemcpyHostToDevice, d->stream), "upload mask");
+  chk(cudaMemsetAsync(d->d_counter, 0, 16 * sizeof(unsigned int), d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_scal, 0, 64 * 8, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_g, 0, (size_t)Q * Nf * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_uflow, 0, (size_t)D.dim * Nf * 8, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_u, 0, (size_t)D.dim * N * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_psi, 0, N * 8, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_phi, 0, N * 8, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_C[0], 0, (size_t)cdi::kMaxSpecies * N * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_C[1], 0, (size_t)cdi::kMaxSpecies * N * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_acc, 0, (size_t)3 * cdi::kMaxSpecies * d->np_blocks * 8, d->stream),
+      "memset");
+  if (s == CDI_OK) s = cdi_flow_build_flags(d);
+  if (s == CDI_OK) s = cdi_np_build_flags(d);
+  if (s == CDI_OK) chk(cudaStreamSynchronize(d->stream), "create domain");
+  if (s != CDI_OK) {
+    g_create_error = d->err;
+    free_all(d);
+    delete d;
+    return s;
+  }
+  *out = d;
+  return CDI_OK;
+}
+
+void cdi_destroy_domain(cdi_domain *d) {
+  if (!d) return;
+  free_all(d);
+  delete d;
+}
+
+cdi_status cdi_solve_flow(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
+                          double *residual_out) {
+  if (!d || !p) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "tau must be > 1/2");
+  if (p->check_every < 2 || (p->check_every % 2) != 0)
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "check_every must be even and >= 2");
+  if (p->max_steps < 0 || (p->max_steps % p->check_every) != 0)
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "max_steps must be a multiple of check_every");
+  if (!std::isfinite(p->force_lu) || !std::isfinite(p->U_target_mps))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "non-finite force or velocity");
+  d->flow_done = false;
+  d->np_ready = false;
+  int64_t steps = 0;
+  double res = 0.0;
+  cdi_status s = cdi_flow_run(d, p, &steps, &res);
+  if (steps_out) *steps_out = steps;
+  if (residual_out) *residual_out = res;
+  if (s != CDI_OK && s != CDI_ERR_NOT_CONVERGED) return s;
+  cdi_status s2 = cdi_flow_export(d, p->U_target_mps);
+  if (s2 != CDI_OK) return s2;
+  d->flow_done = true;
+  if (s == CDI_ERR_NOT_CONVERGED)
+    return cdi_fail(d, s, "flow residual did not reach tol within max_steps");
+  return CDI_OK;
+}
+
+cdi_status cdi_set_velocity(cdi_domain *d, double U) {
+  if (!d) return CDI_ERR_INVALID_ARG;
+  if (!d->flow_done) return cdi_fail(d, CDI_ERR_STATE, "no solved flow");
+  if (!std::isfinite(U)) return cdi_fail(d, CDI_ERR_INVALID_ARG, "non-finite velocity");
+  d->np_ready = false;
+  return cdi_flow_export(d, U);
+}
+
+cdi_status cdi_set_potential(cdi_domain *d, double applied_V, const cdi_elec_params *p,
+                             int *iters_out, double *relres_out) {
+  if (!d || !p) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (!(p->T_K > 0) || !(p->eps_r > 0) || !std::isfinite(applied_V))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "T_K and eps_r must be positive");
+  if (p->mode != 0 && p->mode != 1) return cdi_fail(d, CDI_ERR_INVALID_ARG, "mode must be 0 or 1");
+  if (p->mode == 0 && !(p->lambda_D_m > 0) && !(p->c_bulk_molm3 > 0))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "screened mode needs c_bulk or lambda_D");
+  if (!(p->tol > 0) || p->max_iter < 1)
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "tol must be > 0 and max_iter >= 1");
+  // Physical constants (e and k_B as printed with Eq. 9-10).
+  const double e = 1.6e-19, kB = 1.38e-23, F = 96485.0, eps0 = 8.854e-12;
+  double kdx2 = 0.0;
+  if (p->mode == 0) {
+    double lam = p->lambda_D_m > 0
+                     ? p->lambda_D_m
+                     : std::sqrt(p->eps_r * eps0 * kB * p->T_K / (2.0 * p->c_bulk_molm3 * e * F));
+    kdx2 = (d->dx / lam) * (d->dx / lam);
+  }
+  d->VT = kB * p->T_K / e;
+  d->np_ready = false;
+  d->psi_done = false;
+  int it = 0;
+  double rel = 0.0;
+  cdi_status s = cdi_psi_solve(d, -applied_V, kdx2, p->tol, p->max_iter, &it, &rel);
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = rel;
+  if (s == CDI_OK || s == CDI_ERR_NOT_CONVERGED) d->psi_done = true;
+  if (s == CDI_ERR_NOT_CONVERGED)
+    return cdi_fail(d, s, "potential solve did not reach tol within max_iter");
+  return s;
+}
+
+cdi_status cdi_init_transport(cdi_domain *d, const cdi_species *sp, int n, double c0,
+                              double Ka, double dt_s, double *dt_used) {
+  if (!d || !sp) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n > cdi::kMaxSpecies) return cdi_fail(d, CDI_ERR_INVALID_ARG, "1..4 species");
+  for (int k = 0; k < n; k++)
+    if (!(sp[k].D_m2s > 0) || !std::isfinite(sp[k].D_m2s) || sp[k].z < -8 || sp[k].z > 8)
+      return cdi_fail(d, CDI_ERR_INVALID_ARG, "species need D > 0 and |z| <= 8");
+  if (!(c0 >= 0) || !(Ka >= 0) || !(dt_s >= 0) || !std::isfinite(c0) || !std::isfinite(Ka) ||
+      !std::isfinite(dt_s))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "c0, Ka, dt must be finite and >= 0");
+  if (!d->flow_done) return cdi_fail(d, CDI_ERR_STATE, "solve the flow first");
+  if (!d->psi_done) return cdi_fail(d, CDI_ERR_STATE, "set the potential first");
+  d->ns = n;
+  for (int k = 0; k < cdi::kMaxSpecies; k++) {
+    d->z[k] = k < n ? sp[k].z : 0;
+    d->D[k] = k < n ? sp[k].D_m2s : 1.0;
+  }
+  d->c0 = c0;
+  d->Ka = Ka;
+  d->np_ready = false;
+  cdi_status s = cdi_np_init(d, dt_s, dt_used);
+  if (s == CDI_OK) d->np_ready = true;
+  return s;
+}
+
+cdi_status cdi_step_transport(cdi_domain *d, int64_t n) {
+  if (!d) return CDI_ERR_INVALID_ARG;
+  if (n < 0) return cdi_fail(d, CDI_ERR_INVALID_ARG, "n_steps < 0");
+  if (!d->np_ready) return cdi_fail(d, CDI_ERR_STATE, "call cdi_init_transport first");
+  return cdi_np_steps(d, n);
+}
+
+cdi_status cdi_query_mass_balance(cdi_domain *d, double *M, double *G, double *In, double *Out) {
+  if (!d) return CDI_ERR_INVALID_ARG;
+  if (!d->np_ready) return cdi_fail(d, CDI_ERR_STATE, "no transport state");
+  cdi_status s = cdi_np_reduce(d);
+  if (s != CDI_OK) return s;
+  const double area = d->dim == 2 ? d->dx : d->dx * d->dx;
+  for (int k = 0; k < d->ns; k++) {
+    if (M) M[k] = d->h_scal[S_MASS + k];
+    if (G) G[k] = d->h_scal[S_ACC + 3 * k + 0] * d->dt * area;
+    if (In) In[k] = d->h_scal[S_ACC + 3 * k + 1] * d->dt * area;
+    if (Out) Out[k] = d->h_scal[S_ACC + 3 * k + 2] * d->dt * area;
+  }
+  return CDI_OK;
+}
+
+cdi_status cdi_query_adsorbed(cdi_domain *d, double *per_species) {
+  if (!d || !per_species) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  return cdi_query_mass_balance(d, nullptr, per_species, nullptr, nullptr);
+}
+
+cdi_status cdi_query_outlet(cdi_domain *d, double *per_species) {
+  if (!d || !per_species) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (!d->np_ready) return cdi_fail(d, CDI_ERR_STATE, "no transport state");
+  cdi_status s = cdi_np_reduce(d);
+  if (s != CDI_OK) return s;
+  for (int k = 0; k < d->ns; k++) {
+    double num = d->h_scal[S_OUT + 2 * k], den = d->h_scal[S_OUT + 2 * k + 1];
+    double cnt = d->h_scal[S_OUTN];
+    if (den != 0.0)
+      per_species[k] = num / den;
+    else
+      per_species[k] = cnt > 0 ? d->h_scal[S_OUTP + k] / cnt : 0.0;
+  }
+  return CDI_OK;
+}
+
+cdi_status cdi_query_column_means(cdi_domain *d, int species, double *out) {
+  if (!d || !out) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (!d->np_ready) return cdi_fail(d, CDI_ERR_STATE, "no transport state");
+  if (species < 0 || species >= d->ns) return cdi_fail(d, CDI_ERR_INVALID_ARG, "bad species");
+  cdi_status s = cdi_np_column_means(d, species);
+  if (s != CDI_OK) return s;
+  CDI_TRY(d, cudaMemcpyAsync(out, d->d_colout, (size_t)d->nx * 8, cudaMemcpyDeviceToHost,
+                             d->stream), "copy column means");
+  CDI_TRY(d, cudaStreamSynchronize(d->stream), "column means");
+  return CDI_OK;
+}
+
+cdi_status cdi_copy_field(cdi_domain *d, int field, double *host, size_t count) {
+  if (!d || !host) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  const int isf = d->prec == CDI_FP32;
+  const size_t T = isf ? 4 : 8;
+  const void *src = nullptr;
+  size_t n = 0;
+  double *tmp = d->d_cg;  // 4*N doubles of scratch outside a potential solve
+  if (field == CDI_FIELD_U_LATTICE) {
+    n = (size_t)d->dim * d->Nf;
+    if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
+    CDI_TRY(d, cudaMemcpyAsync(host, d->d_uflow, n * 8, cudaMemcpyDeviceToHost, d->stream),
+            "copy u lattice");
+    CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");
+    return CDI_OK;
+  } else if (field == CDI_FIELD_U) {
+    n = (size_t)d->dim * d->N;
+    src = d->d_u;
+  } else if (field == CDI_FIELD_PSI) {
+    n = (size_t)d->N;
+    if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
+    CDI_TRY(d, cudaMemcpyAsync(host, d->d_psi, n * 8, cudaMemcpyDeviceToHost, d->stream),
+            "copy psi");
+    CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");
+    return CDI_OK;
+  } else if (field >= CDI_FIELD_C && field < CDI_FIELD_C + cdi::kMaxSpecies) {
+    int k = field - CDI_FIELD_C;
+    if (!d->np_ready || k >= d->ns) return cdi_fail(d, CDI_ERR_STATE, "no such species state");
+    n = (size_t)d->N;
+    src = (const char *)d->d_C[d->cur] + (size_t)k * d->N * T;
+  } else {
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "unknown field");
+  }
+  if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
+  if (n > (size_t)4 * d->N) return cdi_fail(d, CDI_ERR_INVALID_ARG, "field too large");
+  cdi_status s = cdi_convert_to_double(d, src, isf, tmp, n);
+  if (s != CDI_OK) return s;
+  CDI_TRY(d, cudaMemcpyAsync(host, tmp, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy field");
+  CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");
+  return CDI_OK;
+}
+
+cdi_status cdi_query_timing(cdi_domain *d, cdi_timing *out, int reset) {
+  if (!d || !out) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  CDI_TRY(d, cdi_timing_resolve(d), "timing events");
+  *out = d->timing;
+  if (reset) d->timing = cdi_timing{};
+  return CDI_OK;
+}
+
+}  // extern "C"

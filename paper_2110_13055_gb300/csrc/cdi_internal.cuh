@@ -1,0 +1,299 @@
+// Internal declarations of the GB300 CDI library: the domain object, device
+// helpers shared by the kernels, and the lattice tables.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cdi.h"
+
+namespace cdi {
+
+constexpr int kMaxSpecies = 4;
+constexpr int kRowBlock = 128;      // threads per block along x for stencils
+constexpr int kRedThreads = 256;    // threads per block for reductions
+constexpr int kRedBlocks = 4 * 152; // fixed grid of the grid-stride reductions
+
+// ---------------------------------------------------------------------------
+// Lattices (D2Q9 and D3Q19 of Sec. 2).  Direction i and its opposite are
+// paired as i <-> i + (Q-1)/2 so that opp() is arithmetic.
+// ---------------------------------------------------------------------------
+template <int DIM> struct Lat;
+
+template <> struct Lat<2> {
+  static constexpr int Q = 9;
+  static constexpr int H = 4;
+  __host__ __device__ static constexpr int ex(int i) {
+    return i == 1 || i == 3 || i == 8 ? 1 : (i == 4 || i == 5 || i == 7 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int ey(int i) {
+    return i == 2 || i == 3 || i == 4 ? 1 : (i == 6 || i == 7 || i == 8 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int ez(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : ((ex(i) * ex(i) + ey(i) * ey(i)) == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= H ? i + H : i - H);
+  }
+};
+
+template <> struct Lat<3> {
+  static constexpr int Q = 19;
+  static constexpr int H = 9;
+  // 1:(1,0,0) 2:(0,1,0) 3:(0,0,1) 4:(1,1,0) 5:(1,-1,0) 6:(1,0,1) 7:(1,0,-1)
+  // 8:(0,1,1) 9:(0,1,-1); 10..18 are their negatives.
+  __host__ __device__ static constexpr int bx(int k) {
+    return k == 1 || k == 4 || k == 5 || k == 6 || k == 7 ? 1 : 0;
+  }
+  __host__ __device__ static constexpr int by(int k) {
+    return k == 2 || k == 4 || k == 8 || k == 9 ? 1 : (k == 5 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int bz(int k) {
+    return k == 3 || k == 6 || k == 8 ? 1 : (k == 7 || k == 9 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int ex(int i) {
+    return i == 0 ? 0 : (i <= H ? bx(i) : -bx(i - H));
+  }
+  __host__ __device__ static constexpr int ey(int i) {
+    return i == 0 ? 0 : (i <= H ? by(i) : -by(i - H));
+  }
+  __host__ __device__ static constexpr int ez(int i) {
+    return i == 0 ? 0 : (i <= H ? bz(i) : -bz(i - H));
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0
+                  : ((ex(i) * ex(i) + ey(i) * ey(i) + ez(i) * ez(i)) == 1 ? 1.0 / 18.0
+                                                                         : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= H ? i + H : i - H);
+  }
+};
+
+// Flow-site flag word: bit 0 = the site is solid; bit i (1..Q-1) = the
+// neighbour along e_i is solid or lies beyond a lateral wall.
+template <int DIM> struct FlowFlag;
+template <> struct FlowFlag<2> { using type = uint16_t; };
+template <> struct FlowFlag<3> { using type = uint32_t; };
+
+// Transport-cell flag byte: bit 0 = solid; bit 1 + f = the neighbour across
+// face f (f = +x,-x,+y,-y,+z,-z) is a solid voxel inside the image.
+constexpr int kFaceBit = 1;
+
+// ---------------------------------------------------------------------------
+// Deterministic block reductions (fixed order, no floating-point atomics).
+// ---------------------------------------------------------------------------
+template <int NV, typename Op>
+__device__ __forceinline__ void warp_reduce(double (&v)[NV], Op op) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = op(v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+}
+
+struct OpSum {
+  __device__ double operator()(double a, double b) const { return a + b; }
+};
+struct OpMax {
+  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+
+// Reduces v over the block; the result is valid in thread 0.  smem must hold
+// NV * 32 doubles.  All threads of the block must call it.
+template <int NV, typename Op>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double *smem, Op op,
+                                             double identity) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  warp_reduce<NV>(v, op);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; k++) smem[k * 32 + w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = lane < nw ? smem[k * 32 + lane] : identity;
+    warp_reduce<NV>(v, op);
+  }
+  __syncthreads();
+}
+
+// Called by every thread after the block wrote its partials: returns true in
+// the last block to finish (which then combines all partials in a fixed
+// order and must reset *counter to 0).
+__device__ __forceinline__ bool last_block(unsigned int *counter, int nblocks) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == (unsigned)(nblocks - 1));
+  __syncthreads();
+  return am_last;
+}
+
+// Sums partials[k * nblocks + b] over b for each k (fixed order) in the last
+// block; the result lands in thread 0's v.
+template <int NV, typename Op>
+__device__ __forceinline__ void combine_partials(const double *partials, int nblocks,
+                                                 double (&v)[NV], double *smem, Op op,
+                                                 double identity) {
+#pragma unroll
+  for (int k = 0; k < NV; k++) v[k] = identity;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = op(v[k], __ldcg(partials + (size_t)k * nblocks + b));
+  block_reduce<NV>(v, smem, op, identity);
+}
+
+// Bernoulli function pair B(x), B(-x) with B(x) = x / (exp(x) - 1), from one
+// expm1 of |x|: B(|x|) directly (series near 0) and B(-|x|) = B(|x|) + |x|,
+// both positive so neither loses precision.
+template <typename T>
+__device__ __forceinline__ void bernoulli_pair(T x, T &Bx, T &Bmx) {
+  const T a = fabs(x);
+  T Ba;
+  if (a < T(1e-3)) {
+    const T a2 = a * a;
+    Ba = T(1) - a * T(0.5) + a2 * (T(1) / T(12)) - a2 * a2 * (T(1) / T(720));
+  } else {
+    Ba = a / expm1(a);
+  }
+  const T Bma = Ba + a;
+  if (x >= T(0)) {
+    Bx = Ba;
+    Bmx = Bma;
+  } else {
+    Bx = Bma;
+    Bmx = Ba;
+  }
+}
+
+}  // namespace cdi
+
+// ---------------------------------------------------------------------------
+// The domain object behind the opaque handle.
+// ---------------------------------------------------------------------------
+struct cdi_domain {
+  // geometry
+  int dim = 2, nx = 0, ny = 0, nz = 1, walls = 0, mirror = 1, prec = CDI_FP64;
+  double dx = 1e-7;
+  int NX = 0;         // flow-grid extent along x (2 nx with the mirror)
+  long long N = 0;    // transport cells nx*ny*nz
+  long long Nf = 0;   // flow sites NX*ny*nz
+  long long n_pore = 0, n_pore_inlet = 0;
+
+  // execution
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for capture
+  cdi_allocator alloc{};
+  bool has_alloc = false;
+  std::string err;
+  struct Block {
+    void *p;
+    size_t bytes;
+  };
+  std::vector<Block> blocks;
+
+  // device buffers
+  uint8_t *d_mask = nullptr;    // N
+  void *d_fflags = nullptr;     // Nf flow flags
+  uint8_t *d_nflags = nullptr;  // N face flags
+  void *d_g = nullptr;          // Q*Nf populations (shifted), precision T
+  double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64
+  void *d_u = nullptr;          // dim*N scaled velocity, precision T
+  double *d_psi = nullptr;      // N potential (V), FP64
+  double *d_phi = nullptr;      // N psi / V_T, FP64 (exp(z phi) needs it)
+  void *d_C[2] = {nullptr, nullptr};  // ns*N concentrations, ping-pong, T
+  double *d_acc = nullptr;      // 3*kMaxSpecies*np_blocks per-block sums
+  double *d_part = nullptr;     // reduction partials (8*kRedBlocks)
+  unsigned int *d_counter = nullptr;  // last-block counters (8 slots)
+  double *d_scal = nullptr;     // device scalars (64)
+  double *h_scal = nullptr;     // pinned host copy of the scalars (64)
+  double *d_cg = nullptr;       // 4*N CG work vectors (r, p, q, diag)
+  double *d_colout = nullptr;   // nx column means
+
+  // state
+  bool flow_done = false, psi_done = false, np_ready = false;
+  int64_t flow_steps = 0;
+  double flow_residual = 0.0;
+  double U_lat = 0.0;           // pore-mean lattice x velocity
+  double U_target = 0.0;
+  double tau = 1.0, force = 0.0;
+  int ns = 0;
+  int z[cdi::kMaxSpecies] = {0, 0, 0, 0};
+  double D[cdi::kMaxSpecies] = {0, 0, 0, 0};
+  double c0 = 0.0, Ka = 0.0, dt = 0.0, VT = 0.0;
+  int cur = 0;                  // which of d_C holds the current state
+  int64_t np_steps = 0;
+  int np_blocks = 0;
+
+  // graphs
+  cudaGraphExec_t flow_graph = nullptr;
+  int flow_graph_K = 0;
+  double flow_graph_tau = 0.0, flow_graph_force = 0.0;
+  cudaGraphExec_t np_graph = nullptr;
+  int np_graph_steps = 0;
+
+  // timing
+  struct EvPair {
+    cudaEvent_t a, b;
+    int phase;
+    int64_t launches;
+  };
+  std::vector<EvPair> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  cdi_timing timing{};
+};
+
+// Scalar slots in d_scal / h_scal.
+enum {
+  S_RES_NUM = 0, S_RES_DEN = 1, S_RES = 2,  // flow residual
+  S_ULAT = 3, S_SCALE = 4,                  // velocity export
+  S_CG_RZ = 8, S_CG_PQ = 9, S_CG_ALPHA = 10, S_CG_BETA = 11, S_CG_RR = 12,
+  S_CG_BB = 13, S_CG_REL = 14, S_CG_DONE = 15, S_CG_TOL = 16, S_CG_IT = 17,
+  S_RATE = 20, S_DT = 21,                   // time step
+  S_OUT = 24,                               // 2*kMaxSpecies: outlet sums
+  S_MASS = 32,                              // kMaxSpecies
+  S_OUTP = 36,                              // kMaxSpecies: plain outlet sums
+  S_ACC = 40,                               // 3*kMaxSpecies: Gamma/In/Out sums
+  S_OUTN = 52                               // pore cells in the outlet column
+};
+
+// Counter slots in d_counter.
+enum { C_RES = 0, C_ULAT = 1, C_CG1 = 2, C_CG2 = 3, C_DT = 4, C_OUT = 5, C_MASS = 6, C_ACC = 7 };
+
+enum { PH_FLOW = 0, PH_CHECK = 1, PH_PSI = 2, PH_NP = 3 };
+
+// Host helpers (api.cu).
+cdi_status cdi_fail(cdi_domain *d, cdi_status s, const std::string &msg);
+cdi_status cdi_cuda_fail(cdi_domain *d, cudaError_t e, const char *what);
+void *cdi_dev_alloc(cdi_domain *d, size_t bytes);
+void cdi_timing_begin(cdi_domain *d, cudaEvent_t *a);
+void cdi_timing_end(cdi_domain *d, cudaEvent_t a, int phase, int64_t launches);
+cudaError_t cdi_timing_resolve(cdi_domain *d);
+
+#define CDI_TRY(d, call, what)                           \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cdi_cuda_fail(d, e_, what); \
+  } while (0)
+
+// Kernel-side entry points used by the API layer.
+cdi_status cdi_flow_build_flags(cdi_domain *d);
+cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
+                        double *res);
+cdi_status cdi_flow_export(cdi_domain *d, double U_target);
+cdi_status cdi_flow_velocity_lattice(cdi_domain *d);
+cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol,
+                         int max_iter, int *iters, double *relres);
+cdi_status cdi_np_build_flags(cdi_domain *d);
+cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used);
+cdi_status cdi_np_steps(cdi_domain *d, int64_t n);
+cdi_status cdi_np_reduce(cdi_domain *d);
+cdi_status cdi_np_column_means(cdi_domain *d, int species);
+cdi_status cdi_convert_to_double(cdi_domain *d, const void *src, int is_float,
+                                 double *dst, size_t n);

@@ -1,0 +1,528 @@
+// Explicit finite-volume Nernst-Planck transport (Eq. 3) with the adsorption
+// flux of Eq. 6, and the transport queries.
+//
+// Per pore cell P, species k, face f with outward normal n:
+//   pore or ghost neighbour:  P_f = (u_f . n) dx / D_k - z_k (phi_nb - phi_P)
+//                             J   = (D_k/dx) [B(-P_f) C_P - B(P_f) C_nb]
+//                                 = (D_k/dx) [B(-P_f) (C_P - C_nb) + P_f C_nb]
+//   solid face (Eq. 6):       J   = K_eff C_P,  K_eff = Ka / (1 + Ka dx/(2 D_k))
+//   lateral wall:             J   = 0
+// with B(x) = x / (exp(x) - 1) (exponential fitting of advection and
+// migration against diffusion), u_f the mean of the two cell velocities,
+// phi = psi / V_T (kept in FP64; the face difference is rounded to the
+// storage precision only after subtraction).  The inlet ghost holds C = c0,
+// phi = 0, u = u_P; the outlet ghost copies the cell (zero gradient).  Update: C_P -= (dt/dx) sum_f J.
+// Adsorbed / inflow / outflow fluxes are summed per block in FP64 into
+// per-block accumulators (fixed block -> cells map, so the totals are
+// deterministic).
+#include <cmath>
+
+#include "cdi_internal.cuh"
+
+using namespace cdi;
+
+namespace {
+
+enum { F_PORE = 0, F_SOLID = 1, F_INLET = 2, F_OUTLET = 3, F_WALL = 4 };
+
+template <typename T> struct NPConst {
+  T dxD[kMaxSpecies];   // dx / D_k
+  T Ddx[kMaxSpecies];   // D_k / dx
+  T Keff[kMaxSpecies];  // half-cell closure of Eq. 6
+  T zf[kMaxSpecies];    // valence
+  T dtdx;               // dt / dx
+  T c0;                 // feed concentration
+};
+
+template <int DIM>
+__global__ void k_np_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ fl, int nx,
+                           int ny, int nz, int walls) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const long long P = ((long long)z * ny + y) * nx + x;
+  uint8_t f = mask[P] ? 1 : 0;
+  for (int fc = 0; fc < 2 * DIM; fc++) {
+    const int a = fc >> 1, s = (fc & 1) ? -1 : 1;
+    int X = x, Y = y, Z = z;
+    if (a == 0) {
+      X += s;
+      if (X < 0 || X >= nx) continue;
+    } else if (a == 1) {
+      Y += s;
+      if (Y < 0 || Y >= ny) {
+        if (walls) continue;
+        Y = (Y + ny) % ny;
+      }
+    } else {
+      Z += s;
+      if (Z < 0 || Z >= nz) {
+        if (walls) continue;
+        Z = (Z + nz) % nz;
+      }
+    }
+    if (mask[((long long)Z * ny + Y) * nx + X]) f |= (uint8_t)(1u << (kFaceBit + fc));
+  }
+  fl[P] = f;
+}
+
+// Face kind and neighbour index of face fc of cell (x,y,z).
+template <int DIM>
+__device__ __forceinline__ int np_face(unsigned f, int fc, int x, int y, int z, int nx, int ny,
+                                       int nz, int walls, long long P, long long &Q) {
+  const int a = fc >> 1, s = (fc & 1) ? -1 : 1;
+  if (a == 0) {
+    if (x + s < 0) return F_INLET;
+    if (x + s >= nx) return F_OUTLET;
+    if ((f >> (kFaceBit + fc)) & 1u) return F_SOLID;
+    Q = P + s;
+    return F_PORE;
+  }
+  if (a == 1) {
+    int Y = y + s;
+    if (Y < 0 || Y >= ny) {
+      if (walls) return F_WALL;
+      Y = Y < 0 ? ny - 1 : 0;
+    }
+    if ((f >> (kFaceBit + fc)) & 1u) return F_SOLID;
+    Q = ((long long)z * ny + Y) * nx + x;
+    return F_PORE;
+  }
+  int Z = z + s;
+  if (Z < 0 || Z >= nz) {
+    if (walls) return F_WALL;
+    Z = Z < 0 ? nz - 1 : 0;
+  }
+  if ((f >> (kFaceBit + fc)) & 1u) return F_SOLID;
+  Q = ((long long)Z * ny + y) * nx + x;
+  return F_PORE;
+}
+
+template <typename T, int DIM, int NS>
+__global__ void __launch_bounds__(kRowBlock)
+    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
+              const double *__restrict__ phi, const uint8_t *__restrict__ fl, NPConst<T> c,
+              double *__restrict__ acc, int nx, int ny, int nz, long long N, int walls,
+              int nblocks) {
+  __shared__ double sm[3 * NS * 32];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  double v[3 * NS];
+#pragma unroll
+  for (int j = 0; j < 3 * NS; j++) v[j] = 0.0;
+  if (x < nx) {
+    const long long P = ((long long)z * ny + y) * nx + x;
+    const unsigned f = fl[P];
+    if (!(f & 1u)) {
+      T CP[NS], sumJ[NS];
+#pragma unroll
+      for (int k = 0; k < NS; k++) {
+        CP[k] = Cin[(size_t)k * N + P];
+        sumJ[k] = T(0);
+      }
+      const double phiP = phi[P];
+      T uP[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * N + P];
+#pragma unroll
+      for (int fc = 0; fc < 2 * DIM; fc++) {
+        const int a = fc >> 1;
+        const T sg = (fc & 1) ? T(-1) : T(1);
+        long long Q = 0;
+        const int kind = np_face<DIM>(f, fc, x, y, z, nx, ny, nz, walls, P, Q);
+        if (kind == F_WALL) continue;
+        if (kind == F_SOLID) {
+#pragma unroll
+          for (int k = 0; k < NS; k++) {
+            const T J = c.Keff[k] * CP[k];
+            sumJ[k] += J;
+            v[k] += (double)J;
+          }
+          continue;
+        }
+        T unb, Cnb[NS];
+        double phinb;
+        if (kind == F_PORE) {
+          unb = u[(size_t)a * N + Q];
+          phinb = phi[Q];
+#pragma unroll
+          for (int k = 0; k < NS; k++) Cnb[k] = Cin[(size_t)k * N + Q];
+        } else if (kind == F_INLET) {
+          unb = uP[a];
+          phinb = 0.0;
+#pragma unroll
+          for (int k = 0; k < NS; k++) Cnb[k] = c.c0;
+        } else {
+          unb = uP[a];
+          phinb = phiP;
+#pragma unroll
+          for (int k = 0; k < NS; k++) Cnb[k] = CP[k];
+        }
+        const T uf = T(0.5) * (uP[a] + unb) * sg;
+        const T dphi = (T)(phinb - phiP);
+#pragma unroll
+        for (int k = 0; k < NS; k++) {
+          const T Pf = uf * c.dxD[k] - c.zf[k] * dphi;
+          T Bp, Bm;
+          bernoulli_pair(Pf, Bp, Bm);
+          const T J = c.Ddx[k] * (Bm * (CP[k] - Cnb[k]) + Pf * Cnb[k]);
+          sumJ[k] += J;
+          if (kind == F_INLET) v[NS + k] -= (double)J;
+          if (kind == F_OUTLET) v[2 * NS + k] += (double)J;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NS; k++) Cout[(size_t)k * N + P] = CP[k] - c.dtdx * sumJ[k];
+    }
+  }
+  block_reduce<3 * NS>(v, sm, OpSum(), 0.0);
+  if (threadIdx.x == 0) {
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    // accumulator layout: [(3*k + kind) * nblocks + block], kind 0 Gamma, 1 In, 2 Out
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      acc[(size_t)(3 * k + 0) * nblocks + bid] += v[k];
+      acc[(size_t)(3 * k + 1) * nblocks + bid] += v[NS + k];
+      acc[(size_t)(3 * k + 2) * nblocks + bid] += v[2 * NS + k];
+    }
+  }
+}
+
+// Largest outflow rate over pore cells and species, in FP64 from the FP64
+// lattice velocity and potential:  (1/dx) [sum_{open faces} (D/dx) B(-P_f)
+// + n_solid K_eff]; dt = safety / max.
+template <int DIM>
+__global__ void __launch_bounds__(kRedThreads)
+    k_np_rate(const uint8_t *__restrict__ fl, const double *__restrict__ uflow,
+              const double *__restrict__ psi, NPConst<double> c, int ns, double scale,
+              double inv_vt, double inv_dx, double safety, int nx, int NX, int ny, int nz,
+              long long N, long long Nf, int walls, double *__restrict__ part,
+              unsigned int *counter, double *scal) {
+  __shared__ double sm[32];
+  double v[1] = {0.0};
+  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
+       P += (long long)gridDim.x * blockDim.x) {
+    const unsigned f = fl[P];
+    if (f & 1u) continue;
+    const long long row = P / nx;
+    const int x = (int)(P - row * nx);
+    const int z = (int)(row / ny);
+    const int y = (int)(row - (long long)z * ny);
+    const long long sP = row * NX + x;
+    for (int k = 0; k < ns; k++) {
+      double rate = 0.0;
+      for (int fc = 0; fc < 2 * DIM; fc++) {
+        const int a = fc >> 1;
+        const double sg = (fc & 1) ? -1.0 : 1.0;
+        long long Q = 0;
+        const int kind = np_face<DIM>(f, fc, x, y, z, nx, ny, nz, walls, P, Q);
+        if (kind == F_WALL) continue;
+        if (kind == F_SOLID) {
+          rate += c.Keff[k];
+          continue;
+        }
+        const double uP = scale * uflow[(size_t)a * Nf + sP];
+        double unb = uP, psinb = 0.0;
+        const double psiP = psi[P];
+        if (kind == F_PORE) {
+          const long long rq = Q / nx;
+          unb = scale * uflow[(size_t)a * Nf + rq * NX + (Q - rq * nx)];
+          psinb = psi[Q];
+        } else if (kind == F_OUTLET) {
+          psinb = psiP;
+        }
+        const double Pf = 0.5 * (uP + unb) * sg * c.dxD[k] - c.zf[k] * (psinb - psiP) * inv_vt;
+        double Bp, Bm;
+        bernoulli_pair(Pf, Bp, Bm);
+        rate += c.Ddx[k] * Bm;
+      }
+      v[0] = fmax(v[0], rate * inv_dx);
+    }
+  }
+  block_reduce<1>(v, sm, OpMax(), 0.0);
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (last_block(counter, gridDim.x)) {
+    combine_partials<1>(part, gridDim.x, v, sm, OpMax(), 0.0);
+    if (threadIdx.x == 0) {
+      scal[S_RATE] = v[0];
+      scal[S_DT] = v[0] > 0.0 ? safety / v[0] : 0.0;
+      *counter = 0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_np_init(const uint8_t *__restrict__ fl, T *__restrict__ C0, T *__restrict__ C1,
+                          long long N, int ns, T c0) {
+  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
+       P += (long long)gridDim.x * blockDim.x) {
+    const bool pore = !(fl[P] & 1);
+#pragma unroll
+    for (int k = 0; k < kMaxSpecies; k++) {
+      const T v = (pore && k < ns) ? c0 : T(0);
+      C0[(size_t)k * N + P] = v;
+      C1[(size_t)k * N + P] = v;
+    }
+  }
+}
+
+// Dissolved amount, outlet sums (flux weighted and plain) per species.
+// Values: [0,4) mass, [4,8) sum u_x C at the outlet, 8 sum u_x, [9,13) plain
+// sum of C at the outlet, 13 pore cells in the outlet column.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    k_np_sums(const uint8_t *__restrict__ fl, const T *__restrict__ C, const T *__restrict__ u,
+              long long N, int nx, int ns, double cell_vol, double *__restrict__ part,
+              unsigned int *counter, double *scal) {
+  constexpr int NV = 14;
+  __shared__ double sm[NV * 32];
+  double v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; j++) v[j] = 0.0;
+  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
+       P += (long long)gridDim.x * blockDim.x) {
+    if (fl[P] & 1u) continue;
+    const bool outlet = (P % nx) == nx - 1;
+    const double ux = (double)u[P];
+#pragma unroll
+    for (int k = 0; k < kMaxSpecies; k++) {
+      if (k >= ns) break;
+      const double ck = (double)C[(size_t)k * N + P];
+      v[k] += ck;
+      if (outlet) {
+        v[4 + k] += ux * ck;
+        v[9 + k] += ck;
+      }
+    }
+    if (outlet) {
+      v[8] += ux;
+      v[13] += 1.0;
+    }
+  }
+  block_reduce<NV>(v, sm, OpSum(), 0.0);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NV; j++) part[(size_t)j * gridDim.x + blockIdx.x] = v[j];
+  if (last_block(counter, gridDim.x)) {
+    combine_partials<NV>(part, gridDim.x, v, sm, OpSum(), 0.0);
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < kMaxSpecies; k++) {
+        scal[S_MASS + k] = v[k] * cell_vol;
+        scal[S_OUT + 2 * k] = v[4 + k];
+        scal[S_OUT + 2 * k + 1] = v[8];
+        scal[S_OUTP + k] = v[9 + k];
+      }
+      scal[S_OUTN] = v[13];
+      *counter = 0;
+    }
+  }
+}
+
+// Totals of the per-block Gamma/In/Out accumulators (one block, fixed order).
+__global__ void __launch_bounds__(kRedThreads)
+    k_acc_total(const double *__restrict__ acc, int nblocks, double *scal) {
+  constexpr int NV = 3 * kMaxSpecies;
+  __shared__ double sm[NV * 32];
+  double v[NV];
+  combine_partials<NV>(acc, nblocks, v, sm, OpSum(), 0.0);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NV; j++) scal[S_ACC + j] = v[j];
+}
+
+// Mean of species k over the pore cells of each x column.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    k_colmeans(const uint8_t *__restrict__ fl, const T *__restrict__ C, int nx, long long rows,
+               double *__restrict__ out) {
+  __shared__ double sm[2 * 32];
+  const int x = blockIdx.x;
+  double v[2] = {0.0, 0.0};
+  for (long long r = threadIdx.x; r < rows; r += blockDim.x) {
+    const long long P = r * nx + x;
+    if (fl[P] & 1u) continue;
+    v[0] += (double)C[P];
+    v[1] += 1.0;
+  }
+  block_reduce<2>(v, sm, OpSum(), 0.0);
+  if (threadIdx.x == 0) out[x] = v[1] > 0.0 ? v[0] / v[1] : 0.0;
+}
+
+template <typename T> NPConst<T> make_const(const cdi_domain *d) {
+  NPConst<T> c{};
+  for (int k = 0; k < kMaxSpecies; k++) {
+    c.dxD[k] = (T)(d->dx / d->D[k]);
+    c.Ddx[k] = (T)(d->D[k] / d->dx);
+    c.Keff[k] = (T)(d->Ka / (1.0 + d->Ka * d->dx / (2.0 * d->D[k])));
+    c.zf[k] = (T)d->z[k];
+  }
+  c.dtdx = (T)(d->dt / d->dx);
+  c.c0 = (T)d->c0;
+  return c;
+}
+
+template <typename T, int DIM, int NS>
+void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
+  dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
+  k_np_step<T, DIM, NS><<<grid, kRowBlock, 0, st>>>(
+      (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u, d->d_phi,
+      d->d_nflags, make_const<T>(d), d->d_acc, d->nx, d->ny, d->nz, d->N, d->walls,
+      d->np_blocks);
+}
+
+template <typename T, int DIM>
+void launch_step_d(cdi_domain *d, cudaStream_t st, int in) {
+  switch (d->ns) {
+    case 1: launch_step_t<T, DIM, 1>(d, st, in); break;
+    case 2: launch_step_t<T, DIM, 2>(d, st, in); break;
+    case 3: launch_step_t<T, DIM, 3>(d, st, in); break;
+    default: launch_step_t<T, DIM, 4>(d, st, in); break;
+  }
+}
+
+void launch_step(cdi_domain *d, cudaStream_t st, int in) {
+  if (d->prec == CDI_FP64) {
+    if (d->dim == 2) launch_step_d<double, 2>(d, st, in);
+    else launch_step_d<double, 3>(d, st, in);
+  } else {
+    if (d->dim == 2) launch_step_d<float, 2>(d, st, in);
+    else launch_step_d<float, 3>(d, st, in);
+  }
+}
+
+constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
+
+}  // namespace
+
+cdi_status cdi_np_build_flags(cdi_domain *d) {
+  dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
+  if (d->dim == 2)
+    k_np_flags<2><<<grid, kRowBlock, 0, d->stream>>>(d->d_mask, d->d_nflags, d->nx, d->ny, d->nz,
+                                                     d->walls);
+  else
+    k_np_flags<3><<<grid, kRowBlock, 0, d->stream>>>(d->d_mask, d->d_nflags, d->nx, d->ny, d->nz,
+                                                     d->walls);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "face flags");
+  return CDI_OK;
+}
+
+cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
+  if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
+  d->np_graph = nullptr;
+  double dt = dt_s;
+  if (dt <= 0.0) {
+    NPConst<double> c = make_const<double>(d);
+    const double scale = d->h_scal[S_SCALE];
+    if (d->dim == 2)
+      k_np_rate<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+          d->d_nflags, d->d_uflow, d->d_psi, c, d->ns, scale, 1.0 / d->VT, 1.0 / d->dx, 0.9,
+          d->nx, d->NX, d->ny, d->nz, d->N, d->Nf, d->walls, d->d_part, d->d_counter + C_DT,
+          d->d_scal);
+    else
+      k_np_rate<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+          d->d_nflags, d->d_uflow, d->d_psi, c, d->ns, scale, 1.0 / d->VT, 1.0 / d->dx, 0.9,
+          d->nx, d->NX, d->ny, d->nz, d->N, d->Nf, d->walls, d->d_part, d->d_counter + C_DT,
+          d->d_scal);
+    d->timing.kernel_launches++;
+    CDI_TRY(d, cudaGetLastError(), "time step kernel");
+    CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_RATE, d->d_scal + S_RATE, 2 * sizeof(double),
+                               cudaMemcpyDeviceToHost, d->stream),
+            "time step copy");
+    CDI_TRY(d, cudaStreamSynchronize(d->stream), "time step");
+    dt = d->h_scal[S_DT];
+    if (!(dt > 0.0) || !std::isfinite(dt))
+      return cdi_fail(d, CDI_ERR_INVALID_ARG, "no finite time step (no flux anywhere?)");
+  }
+  d->dt = dt;
+  if (dt_used) *dt_used = dt;
+  if (d->prec == CDI_FP64)
+    k_np_init<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, (double *)d->d_C[0], (double *)d->d_C[1], d->N, d->ns, d->c0);
+  else
+    k_np_init<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, (float *)d->d_C[0], (float *)d->d_C[1], d->N, d->ns, (float)d->c0);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "transport init");
+  CDI_TRY(d, cudaMemsetAsync(d->d_acc, 0, (size_t)3 * kMaxSpecies * d->np_blocks * 8, d->stream),
+          "reset accumulators");
+  d->cur = 0;
+  d->np_steps = 0;
+  return CDI_OK;
+}
+
+cdi_status cdi_np_steps(cdi_domain *d, int64_t n) {
+  if (n == 0) return CDI_OK;
+  cudaEvent_t ev;
+  cdi_timing_begin(d, &ev);
+  int64_t left = n;
+  if (d->cur == 1) {
+    launch_step(d, d->stream, 1);
+    d->cur = 0;
+    left--;
+  }
+  if (left >= kGraphSteps) {
+    if (!d->np_graph) {
+      cudaGraph_t graph;
+      CDI_TRY(d, cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal),
+              "begin capture");
+      for (int k = 0; k < kGraphSteps; k++) launch_step(d, d->cap_stream, k & 1);
+      cudaError_t e = cudaStreamEndCapture(d->cap_stream, &graph);
+      CDI_TRY(d, e, "end capture");
+      e = cudaGraphInstantiate(&d->np_graph, graph, 0);
+      cudaGraphDestroy(graph);
+      CDI_TRY(d, e, "instantiate transport graph");
+    }
+    while (left >= kGraphSteps) {
+      CDI_TRY(d, cudaGraphLaunch(d->np_graph, d->stream), "transport graph");
+      left -= kGraphSteps;
+    }
+  }
+  while (left > 0) {
+    launch_step(d, d->stream, d->cur);
+    d->cur = 1 - d->cur;
+    left--;
+  }
+  CDI_TRY(d, cudaGetLastError(), "transport step");
+  cdi_timing_end(d, ev, PH_NP, n);
+  d->timing.kernel_launches += n;
+  d->np_steps += n;
+  return CDI_OK;
+}
+
+cdi_status cdi_np_reduce(cdi_domain *d) {
+  const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
+  if (d->prec == CDI_FP64)
+    k_np_sums<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, (const double *)d->d_C[d->cur], (const double *)d->d_u, d->N, d->nx, d->ns,
+        vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
+  else
+    k_np_sums<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, (const float *)d->d_C[d->cur], (const float *)d->d_u, d->N, d->nx, d->ns,
+        vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
+  k_acc_total<<<1, kRedThreads, 0, d->stream>>>(d->d_acc, d->np_blocks, d->d_scal);
+  d->timing.kernel_launches += 2;
+  CDI_TRY(d, cudaGetLastError(), "transport sums");
+  CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_OUT, d->d_scal + S_OUT,
+                             (S_OUTN - S_OUT + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                             d->stream),
+          "sums copy");
+  CDI_TRY(d, cudaStreamSynchronize(d->stream), "transport sums");
+  CDI_TRY(d, cdi_timing_resolve(d), "timing");
+  return CDI_OK;
+}
+
+cdi_status cdi_np_column_means(cdi_domain *d, int k) {
+  const size_t T = d->prec == CDI_FP64 ? 8 : 4;
+  const void *C = (const char *)d->d_C[d->cur] + (size_t)k * d->N * T;
+  const long long rows = (long long)d->ny * d->nz;
+  if (d->prec == CDI_FP64)
+    k_colmeans<double><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_nflags, (const double *)C,
+                                                             d->nx, rows, d->d_colout);
+  else
+    k_colmeans<float><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_nflags, (const float *)C, d->nx,
+                                                            rows, d->d_colout);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "column means");
+  return CDI_OK;
+}

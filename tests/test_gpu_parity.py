@@ -1,0 +1,302 @@
+"""GPU path (C ABI -> CUDA kernels) against the FP64 oracle, element by
+element on the same seeded inputs.
+
+Tolerances: FP64 storage agrees with the oracle up to summation order
+(relative L2 <= 1e-11 on u, psi and C after thousands of steps).  FP32
+storage is held to the stated per-field bounds: relative L2 of the velocity
+<= 1e-5, of the concentrations <= 1e-4, of the adsorbed amount <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_13055_gb300 import cdi, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL_U32, TOL_C32, TOL_G32 = 1e-5, 1e-4, 1e-6
+Z, D = (1, -1), (1.33e-9, 2.03e-9)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+# --------------------------------------------------------------------------
+# flow
+# --------------------------------------------------------------------------
+def slit(nx, H, dim=2, nz=3):
+    if dim == 2:
+        m = np.zeros((H + 2, nx), np.uint8)
+        m[[0, -1], :] = 1
+    else:
+        m = np.zeros((nz, H + 2, nx), np.uint8)
+        m[:, [0, -1], :] = 1
+    return m
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+def test_poiseuille(dim, prec):
+    """Exact plane Poiseuille at (tau - 1/2)^2 = 3/16 (as in the oracle pin)."""
+    H, g, tau = 12, 1e-6, 0.5 + np.sqrt(3) / 4
+    with cdi.Domain(slit(6, H, dim), precision=prec) as d:
+        steps, res, st = d.solve_flow(tau=tau, force=g, tol=1e-12 if prec == cdi.FP64 else 1e-7,
+                                      check_every=200, max_steps=200_000, U_target=0.0,
+                                      allow_not_converged=prec == cdi.FP32)
+        u = d.u_lattice()
+    y = np.arange(H) + 0.5
+    ua = g * y * (H - y) / (2 * (tau - 0.5) / 3)
+    ux = u[0][1:-1, 0] if dim == 2 else u[0][1, 1:-1, 0]
+    tol = 1e-9 if prec == cdi.FP64 else 2e-5
+    assert np.max(np.abs(ux - ua)) / ua.max() < tol
+
+
+CASES = {
+    "discs128x64": lambda: inputs.disc_pack_128x64()[0],
+    "ragged37x23": lambda: inputs.grain_pack((23, 37), 0.62, 2.0, 4.5, seed=9)[0],
+    "spheres19x13x11": lambda: inputs.grain_pack((11, 13, 19), 0.6, 1.5, 3.0, seed=4)[0],
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("mirror,walls", [(True, False), (False, True)])
+def test_flow_fixed_steps_fp64(case, mirror, walls):
+    m = CASES[case]()
+    ref, *_ = O.lbm(m, mirror=mirror, lateral_walls=walls, tau=0.9, force=2e-6, tol=0.0,
+                    check_every=100, max_steps=1200)
+    with cdi.Domain(m, precision=cdi.FP64, mirror=mirror, lateral_walls=walls) as d:
+        steps, res, _ = d.solve_flow(tau=0.9, force=2e-6, tol=0.0, check_every=100,
+                                     max_steps=1200, U_target=0.0)
+        u = d.u_lattice()
+    assert steps == 1200
+    assert rel(u, ref) < TOL64
+
+
+@pytest.fixture(scope="module")
+def cfg1_oracle():
+    m, _ = inputs.disc_pack_128x64()
+    r = O.run_case(m, flow_tol=1e-8, n_np_steps=2000)
+    return m, r
+
+
+def test_flow_converged_cfg1(cfg1_oracle):
+    """128x64 discs: FP64 stops at the same check with the same field; FP32
+    within 1e-5 relative L2."""
+    m, r = cfg1_oracle
+    with cdi.Domain(m, precision=cdi.FP64) as d:
+        steps, res, _ = d.solve_flow(tol=1e-8)
+        u64 = d.u_lattice()
+    assert steps == r["flow_steps"]
+    assert rel(u64, r["u_flow"]) < TOL64
+    with cdi.Domain(m, precision=cdi.FP32) as d:
+        steps32, res32, _ = d.solve_flow(tol=1e-8, max_steps=200_000, allow_not_converged=True)
+        u32 = d.u_lattice()
+    assert rel(u32, r["u_flow"]) < TOL_U32
+
+
+# --------------------------------------------------------------------------
+# potential
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode,lam", [("debye", None), ("debye", 1.5e-7), ("laplace", None)])
+@pytest.mark.parametrize("case", ["discs128x64", "spheres19x13x11"])
+def test_potential(mode, lam, case):
+    m = CASES[case]()
+    ref, it, relres = O.psi(m, -0.8, dx=1e-7, c_bulk=10.0, mode=mode, lambda_D=lam, tol=1e-14)
+    with cdi.Domain(m) as d:
+        d.solve_flow(tol=0.0, max_steps=0, U_target=0.0)
+        git, grel = d.set_potential(0.8, c_bulk=10.0, lambda_D=lam or 0.0, mode=mode, tol=1e-14)
+        ps = d.psi()
+    assert grel < 1e-14
+    assert rel(ps, ref) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# coupled pipeline
+# --------------------------------------------------------------------------
+def run_gpu(m, prec, *, flow_tol=1e-8, max_flow=2_000_000, U=1e-4, V=1.0, c0=10.0,
+            lam=None, n_np=2000, Ka=1e-6, chunks=None, res=None):
+    with cdi.Domain(m, precision=prec, torch_resources=res) as d:
+        steps, fres, _ = d.solve_flow(tol=flow_tol, max_steps=max_flow, U_target=U,
+                                      allow_not_converged=True)
+        d.set_potential(V, c_bulk=c0, lambda_D=lam or 0.0, tol=1e-13)
+        dt = d.init_transport(Z, D, c0=c0, Ka=Ka)
+        for n in (chunks or [n_np]):
+            d.step(n)
+        out = dict(flow_steps=steps, dt=dt, u=d.u(), psi=d.psi(), C=d.C(),
+                   Gamma=d.adsorbed(), C_out=d.outlet(), cols=d.column_means(0))
+        out["M"], _, out["In"], out["Out"] = d.mass_balance()
+        out["timing"] = d.timing()
+    return out
+
+
+def test_pipeline_cfg1_fp64(cfg1_oracle):
+    m, r = cfg1_oracle
+    g = run_gpu(m, cdi.FP64)
+    assert g["flow_steps"] == r["flow_steps"]
+    assert abs(g["dt"] - r["dt"]) <= 1e-13 * r["dt"]
+    assert rel(g["u"], r["u"]) < TOL64
+    assert rel(g["psi"], r["psi"]) < TOL64
+    assert rel(g["C"], r["C"]) < TOL64
+    np.testing.assert_allclose(g["Gamma"], r["Gamma"], rtol=1e-11)
+    np.testing.assert_allclose(g["In"], r["In"], rtol=1e-11)
+    np.testing.assert_allclose(g["Out"], r["Out"], rtol=1e-10)
+    np.testing.assert_allclose(g["C_out"], r["C_out"], rtol=1e-11)
+    np.testing.assert_allclose(g["M"], r["M"], rtol=1e-12)
+    np.testing.assert_allclose(g["cols"], O.column_means(m, r["C"])[0], rtol=1e-11)
+    # exact mass balance on the device accounts
+    np.testing.assert_allclose(g["M"] + g["Gamma"] + g["Out"] - g["In"], r["M0"], rtol=1e-12)
+
+
+def test_pipeline_cfg1_fp32(cfg1_oracle):
+    m, r = cfg1_oracle
+    g = run_gpu(m, cdi.FP32, max_flow=200_000)
+    assert rel(g["u"], r["u"]) < TOL_U32
+    assert rel(g["C"], r["C"]) < TOL_C32
+    assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < TOL_G32
+    np.testing.assert_allclose(g["C_out"], r["C_out"], rtol=TOL_C32)
+
+
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+def test_pipeline_crop_of_1024x512(prec):
+    """256x128 crop of the 1024x512 polydisperse pack (0.8 V, strong EDL
+    override so migration matters), fixed flow horizon, 3000 transport
+    steps."""
+    big, _ = inputs.disc_pack_1024x512()
+    m = inputs.crop(big, (128, 256))
+    kw = dict(V=0.8, lam=2e-7)
+    r = O.run_case(m, flow_tol=0.0, max_flow_steps=3000, applied_V=0.8, lambda_D=2e-7,
+                   n_np_steps=3000)
+    g = run_gpu(m, prec, flow_tol=0.0, max_flow=3000, n_np=3000, **kw)
+    if prec == cdi.FP64:
+        assert rel(g["u"], r["u"]) < TOL64 and rel(g["C"], r["C"]) < TOL64
+        np.testing.assert_allclose(g["Gamma"], r["Gamma"], rtol=1e-11)
+    else:
+        assert rel(g["u"], r["u"]) < TOL_U32
+        assert rel(g["C"], r["C"]) < TOL_C32
+        assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < TOL_G32
+
+
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+def test_pipeline_3d(prec):
+    m, _ = inputs.grain_pack((14, 16, 22), 0.55, 2.0, 3.5, seed=12)
+    r = O.run_case(m, flow_tol=0.0, max_flow_steps=1000, applied_V=1.2, c0=20.0,
+                   lambda_D=1.5e-7, n_np_steps=600, U_target=1e-4)
+    g = run_gpu(m, prec, flow_tol=0.0, max_flow=1000, V=1.2, c0=20.0, lam=1.5e-7, n_np=600)
+    tolu, tolc, tolg = (TOL64, TOL64, 1e-11) if prec == cdi.FP64 else (TOL_U32, TOL_C32, TOL_G32)
+    assert rel(g["u"], r["u"]) < tolu
+    assert rel(g["psi"], r["psi"]) < TOL64
+    assert rel(g["C"], r["C"]) < tolc
+    assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < tolg
+
+
+# --------------------------------------------------------------------------
+# edge cases and invariants
+# --------------------------------------------------------------------------
+def test_step_chunking_is_invisible():
+    """Graph-launched and single launches give bitwise the same state, for
+    any split of the step count (including 0 and odd counts)."""
+    m = CASES["ragged37x23"]()
+    a = run_gpu(m, cdi.FP32, flow_tol=0.0, max_flow=400, chunks=[259])
+    b = run_gpu(m, cdi.FP32, flow_tol=0.0, max_flow=400, chunks=[1, 0, 63, 65, 130])
+    assert np.array_equal(a["C"], b["C"])
+    assert np.array_equal(a["Gamma"], b["Gamma"])
+
+
+def test_deterministic_and_torch_allocator():
+    m = CASES["ragged37x23"]()
+    a = run_gpu(m, cdi.FP64, flow_tol=0.0, max_flow=600, n_np=300)
+    b = run_gpu(m, cdi.FP64, flow_tol=0.0, max_flow=600, n_np=300,
+                res=cdi.TorchResources(0))
+    for k in ("u", "psi", "C", "Gamma", "In", "Out", "C_out"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_zero_steps_and_uniform_state():
+    """No flow, no potential, no adsorption: C stays c0 exactly."""
+    m = CASES["discs128x64"]()
+    g = run_gpu(m, cdi.FP32, flow_tol=0.0, max_flow=0, U=0.0, V=0.0, Ka=0.0, n_np=100)
+    assert np.all(g["C"][:, m == 0] == np.float32(10.0))
+    assert np.all(g["Gamma"] == 0)
+
+
+def test_velocity_rescale_and_linearity():
+    m = CASES["discs128x64"]()
+    with cdi.Domain(m) as d:
+        d.solve_flow(tol=0.0, max_steps=400, U_target=1e-4)
+        u1 = d.u()
+        d.set_velocity(3e-4)
+        u3 = d.u()
+    np.testing.assert_allclose(u3, 3 * u1, rtol=1e-15, atol=0)
+    assert abs(u1[0][m == 0].mean() - 1e-4) < 1e-18
+
+
+def test_call_order_and_argument_errors():
+    m = CASES["ragged37x23"]()
+    with cdi.Domain(m) as d:
+        with pytest.raises(cdi.CDIError) as e:
+            d.step(1)
+        assert e.value.status == 6
+        with pytest.raises(cdi.CDIError) as e:
+            d.init_transport()
+        assert e.value.status == 6
+        with pytest.raises(cdi.CDIError) as e:
+            d.solve_flow(check_every=3)
+        assert e.value.status == 1
+        with pytest.raises(cdi.CDIError) as e:
+            d.solve_flow(tau=0.5)
+        assert e.value.status == 1
+        steps, res, st = d.solve_flow(tol=1e-30, max_steps=200, allow_not_converged=True)
+        assert st == 4 and steps == 200
+        d.set_potential(1.0)
+        with pytest.raises(cdi.CDIError) as e:
+            d.init_transport(z=(1, -1, 1, -1, 2), D=(1e-9,) * 5)
+        assert e.value.status == 1
+
+
+def test_full_size_1024x512_properties():
+    """The 1024x512 pack in the benchmark's FP32 configuration: the mirror
+    symmetry of the flow, the potential against the oracle at full size,
+    transport without flow against the oracle at full size, and the exact
+    mass balance of the device accounts."""
+    m, _ = inputs.disc_pack_1024x512()
+    with cdi.Domain(m, precision=cdi.FP32) as d:
+        d.solve_flow(tol=0.0, max_steps=2000, U_target=1e-4)
+        uf = d.u_lattice()
+        R = uf[..., ::-1]
+        scale = np.abs(uf[0]).max()
+        assert np.max(np.abs(R[0] - uf[0])) < 1e-6 * scale
+        assert np.max(np.abs(R[1] + uf[1])) < 1e-6 * scale
+        d.set_potential(0.8, c_bulk=10.0, tol=1e-13)
+        ps = d.psi()
+        dt = d.init_transport(Z, D, c0=10.0, Ka=1e-6)
+        d.step(500)
+        M, G, I, Ou = d.mass_balance()
+        C = d.C()
+    ref_ps, *_ = O.psi(m, -0.8, c_bulk=10.0, tol=1e-14)
+    assert rel(ps, ref_ps) < 1e-12
+    assert C.min() >= 0.0
+    M0 = 10.0 * (m == 0).sum() * 1e-14
+    np.testing.assert_allclose(M + G + Ou - I, M0, rtol=1e-6)
+    # transport without flow: u = 0 on both sides, full grid, 200 steps
+    with cdi.Domain(m, precision=cdi.FP32) as d:
+        d.solve_flow(tol=0.0, max_steps=0, U_target=0.0)
+        d.set_potential(0.8, c_bulk=10.0, lambda_D=2e-7, tol=1e-13)
+        dt = d.init_transport(Z, D, c0=10.0, Ka=1e-6)
+        d.step(200)
+        C = d.C()
+        G = d.adsorbed()
+    ps, *_ = O.psi(m, -0.8, c_bulk=10.0, lambda_D=2e-7, tol=1e-14)
+    u0 = np.zeros((2,) + m.shape)
+    dt_ref = O.np_dt(m, u0, ps, Z, D)
+    assert abs(dt - dt_ref) < 1e-12 * dt_ref
+    Cr, Gr, _, _ = O.np_run(m, u0, ps, Z, D, c0=10.0, dt=dt_ref, n_steps=200)
+    assert rel(C, Cr) < TOL_C32
+    assert np.max(np.abs(G - Gr) / Gr) < TOL_G32
