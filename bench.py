@@ -46,6 +46,20 @@ WORKLOADS = {
               "Nernst-Planck steps; FP32 storage"),
         mask=lambda: inputs.disc_pack_1024x512()[0], prec=cdi.FP32, V=0.8, U=1e-4, c0=10.0,
         np_steps=50000, flow_tol=1e-8, max_flow=1_000_000),
+    "2d-2048x1024": dict(
+        desc=("2D 2048x1024 polydisperse discs r~U[4,16] lu (overlap), porosity 0.5, seed 1; "
+              "as 2d-1024x512 but the populations (151 MB) exceed L2; flow to 1e-8; "
+              "50000 Nernst-Planck steps; FP32 storage"),
+        mask=lambda: inputs.grain_pack((1024, 2048), 0.5, 4.0, 16.0, seed=1)[0],
+        prec=cdi.FP32, V=0.8, U=1e-4, c0=10.0, np_steps=50000, flow_tol=1e-8,
+        max_flow=1_000_000),
+    "3d-256": dict(
+        desc=("3D 256^3 sphere pack r~U[6,12] lu (overlap), porosity 0.45, seed 2; D3Q19 BGK "
+              "tau=1, body force 1e-6 lu, mirror along x; flow capped at 20000 steps (residual "
+              "reported; the 1e-7 target takes O(1e5) steps); 1.2 V, c0=20 mol/m^3, pore-mean "
+              "velocity 1e-6 m/s; 20000 Nernst-Planck steps; FP32 storage"),
+        mask=lambda: inputs.sphere_pack_256()[0], prec=cdi.FP32, V=1.2, U=1e-6, c0=20.0,
+        np_steps=20000, flow_tol=1e-7, max_flow=20000),
     "2d-128x64": dict(
         desc=("2D 128x64 non-overlapping discs r=6 lu, porosity 0.6, seed 0; D2Q9 tau=1, "
               "Stokes to residual 1e-8; 1.0 V; Na+/Cl-, c0=10 mol/m^3; 2000 Nernst-Planck "
@@ -149,6 +163,21 @@ def recorded_traffic(kernel):
     return rec.get("dram_bytes_per_launch")
 
 
+def aggregate(elapsed, units):
+    """Whole-job figures under torchrun: the max over ranks of the timed
+    region and the sum of the units every rank processed (a host-side gloo
+    reduction of two numbers; the ranks' solves never exchange data)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed, float(units)
+    t = torch.tensor([float(elapsed)], dtype=torch.float64)
+    u = torch.tensor([float(units)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item()
+
+
 def run_pipeline(dom, w):
     """The hot path on a resident domain; returns the step's counters."""
     steps, res, st = dom.solve_flow(tol=w["flow_tol"], max_steps=w["max_flow"],
@@ -201,15 +230,7 @@ def ours(args, w, mask):
     dev_ms = ev0.elapsed_time(ev1)
     tim = dom.timing(reset=True)
     elapsed = dev_ms / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed, float(units)], dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        elapsed_all, units_all = tmax[0].item(), t[1].item()
-    else:
-        elapsed_all, units_all = elapsed, float(units)
+    elapsed_all, units_all = aggregate(elapsed, units)
 
     # dominant kernel and its roofline
     T = 4 if w["prec"] == cdi.FP32 else 8
@@ -347,9 +368,20 @@ def main():
     ap.add_argument("--ref-flow-steps", type=int, default=100)
     ap.add_argument("--ref-np-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flow-steps", type=int, default=0,
+                    help="run exactly this many flow steps (multiple of 100) instead of "
+                         "converging; for short profiling runs")
+    ap.add_argument("--np-steps", type=int, default=0,
+                    help="override the number of transport steps")
     args = ap.parse_args()
     rank, world, local = dist_info()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.flow_steps:
+        w.update(flow_tol=0.0, max_flow=args.flow_steps)
+        w["desc"] += f" [override: exactly {args.flow_steps} flow steps]"
+    if args.np_steps:
+        w["np_steps"] = args.np_steps
+        w["desc"] += f" [override: {args.np_steps} transport steps]"
     mask = w["mask"]()
     if args.impl == "reference":
         # the oracle runs on rank 0 alone; the other ranks exit without work

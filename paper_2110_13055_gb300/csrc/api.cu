@@ -228,7 +228,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
   d->d_u = A((size_t)D.dim * N * T);
   d->d_psi = (double *)A(N * 8);
-  d->d_phi = (double *)A(N * 8);
+  d->d_phi = A(N * 8);
   d->d_C[0] = A((size_t)cdi::kMaxSpecies * N * T);
   d->d_C[1] = A((size_t)cdi::kMaxSpecies * N * T);
   d->d_acc = (double *)A((size_t)3 * cdi::kMaxSpecies * d->np_blocks * 8);

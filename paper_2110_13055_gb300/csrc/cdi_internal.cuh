@@ -87,8 +87,8 @@ constexpr int kFaceBit = 1;
 // ---------------------------------------------------------------------------
 // Deterministic block reductions (fixed order, no floating-point atomics).
 // ---------------------------------------------------------------------------
-template <int NV, typename Op>
-__device__ __forceinline__ void warp_reduce(double (&v)[NV], Op op) {
+template <int NV, typename V, typename Op>
+__device__ __forceinline__ void warp_reduce(V (&v)[NV], Op op) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -96,17 +96,16 @@ __device__ __forceinline__ void warp_reduce(double (&v)[NV], Op op) {
 }
 
 struct OpSum {
-  __device__ double operator()(double a, double b) const { return a + b; }
+  template <typename V> __device__ V operator()(V a, V b) const { return a + b; }
 };
 struct OpMax {
-  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+  template <typename V> __device__ V operator()(V a, V b) const { return a > b ? a : b; }
 };
 
 // Reduces v over the block; the result is valid in thread 0.  smem must hold
-// NV * 32 doubles.  All threads of the block must call it.
-template <int NV, typename Op>
-__device__ __forceinline__ void block_reduce(double (&v)[NV], double *smem, Op op,
-                                             double identity) {
+// NV * 32 values.  All threads of the block must call it.
+template <int NV, typename V, typename Op>
+__device__ __forceinline__ void block_reduce(V (&v)[NV], V *smem, Op op, V identity) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
   warp_reduce<NV>(v, op);
@@ -147,6 +146,29 @@ __device__ __forceinline__ void combine_partials(const double *partials, int nbl
     for (int k = 0; k < NV; k++) v[k] = op(v[k], __ldcg(partials + (size_t)k * nblocks + b));
   block_reduce<NV>(v, smem, op, identity);
 }
+
+// psi / V_T as stored for the transport kernel: FP64, or an unevaluated
+// FP32 pair hi + lo (so that face differences keep FP64-like accuracy while
+// the arithmetic stays on the FP32 units).
+template <typename T> struct PhiStore;
+template <> struct PhiStore<double> {
+  using type = double;
+  __device__ static double make(double v) { return v; }
+  __device__ static double diff(double a, double b) { return a - b; }
+  __device__ static double zero() { return 0.0; }
+};
+template <> struct PhiStore<float> {
+  using type = float2;
+  __device__ static float2 make(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  }
+  // (a - b) from two hi/lo pairs, rounded once to FP32
+  __device__ static float diff(float2 a, float2 b) {
+    return __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+  }
+  __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+};
 
 // Bernoulli function pair B(x), B(-x) with B(x) = x / (exp(x) - 1), from one
 // expm1 of |x|: B(|x|) directly (series near 0) and B(-|x|) = B(|x|) + |x|,
@@ -206,7 +228,8 @@ struct cdi_domain {
   double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64
   void *d_u = nullptr;          // dim*N scaled velocity, precision T
   double *d_psi = nullptr;      // N potential (V), FP64
-  double *d_phi = nullptr;      // N psi / V_T, FP64 (exp(z phi) needs it)
+  void *d_phi = nullptr;        // N psi / V_T, 8 bytes a cell: double (FP64)
+                                // or a float2 (hi, lo) pair (FP32)
   void *d_C[2] = {nullptr, nullptr};  // ns*N concentrations, ping-pong, T
   double *d_acc = nullptr;      // 3*kMaxSpecies*np_blocks per-block sums
   double *d_part = nullptr;     // reduction partials (8*kRedBlocks)

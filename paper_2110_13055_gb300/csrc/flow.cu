@@ -19,6 +19,16 @@ using namespace cdi;
 
 namespace {
 
+// s + c += v with s carrying the rounded sum and c the accumulated rounding
+// errors (Knuth's two-sum: the error of each addition is exact in FP32).
+__device__ __forceinline__ void two_sum_acc(float v, float &s, float &c) {
+  const float t = __fadd_rn(s, v);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+  s = t;
+  c = __fadd_rn(c, err);
+}
+
 template <int DIM>
 __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
                              typename FlowFlag<DIM>::type *__restrict__ fl, int nx, int NX,
@@ -93,11 +103,29 @@ __global__ void __launch_bounds__(kRowBlock)
     if (L::ey(i)) jy += T(L::ey(i)) * gi[i];
     if (DIM == 3 && L::ez(i)) jz += T(L::ez(i)) * gi[i];
   }
+  T go_all[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     const T eu = T(L::ex(i)) * jx + T(L::ey(i)) * jy + T(L::ez(i)) * jz;
     const T geq = T(L::w(i)) * (drho + T(3) * eu);
-    const T go = gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
+    go_all[i] = gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
+  }
+  if (sizeof(T) == 4) {
+    // FP32 storage: the collision conserves mass exactly, but rounding the
+    // stored values does not, and the leak is biased; it feeds the slowest
+    // (pressure-diffusion) modes of the porous flow.  The rest population
+    // closes the balance: g*_0 = sum_i g_i - sum_{i>0} g*_i, both sums carried
+    // exactly as (sum, error) pairs by the two-sum transformation.
+    float ms = 0.f, mc = 0.f, ss = 0.f, sc = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; i++) two_sum_acc((float)gi[i], ms, mc);
+#pragma unroll
+    for (int i = 1; i < Q; i++) two_sum_acc((float)go_all[i], ss, sc);
+    go_all[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
+  }
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const T go = go_all[i];
     if (!ODD) {
       g[(size_t)L::opp(i) * Nf + s] = go;
     } else {

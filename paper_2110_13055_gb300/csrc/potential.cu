@@ -204,13 +204,13 @@ __global__ void k_cg_dir(long long N, double *__restrict__ p, const double *__re
     p[P] = zq[P] + beta * p[P];
 }
 
-// phi = psi / V_T (0 in solid cells).
+// phi = psi / V_T (0 in solid cells) in the transport kernel's format.
 template <typename T>
 __global__ void k_phi(long long N, const uint8_t *__restrict__ fl, const double *__restrict__ psi,
-                      T *__restrict__ phi, double inv_vt) {
+                      typename PhiStore<T>::type *__restrict__ phi, double inv_vt) {
   for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
        P += (long long)gridDim.x * blockDim.x)
-    phi[P] = (fl[P] & 1) ? T(0) : (T)(psi[P] * inv_vt);
+    phi[P] = (fl[P] & 1) ? PhiStore<T>::zero() : PhiStore<T>::make(psi[P] * inv_vt);
 }
 
 }  // namespace
@@ -251,11 +251,16 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol, i
     }
     chunk = std::min(chunk * 2, 256);
   }
-  // phi stays FP64 in both precisions: the Boltzmann factor exp(z phi) of a
-  // face turns an absolute error of phi into a relative error of C.
+  // phi keeps FP64 accuracy in both precisions (a double, or an FP32 hi/lo
+  // pair): the Boltzmann factor exp(z phi) of a face turns an absolute error
+  // of phi into a relative error of C.
   const double inv_vt = 1.0 / d->VT;
-  k_phi<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->N, d->d_nflags, d->d_psi,
-                                                           d->d_phi, inv_vt);
+  if (d->prec == CDI_FP64)
+    k_phi<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->N, d->d_nflags, d->d_psi,
+                                                             (double *)d->d_phi, inv_vt);
+  else
+    k_phi<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->N, d->d_nflags, d->d_psi,
+                                                            (float2 *)d->d_phi, inv_vt);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "phi");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_CG_REL, d->d_scal + S_CG_REL, 4 * sizeof(double),

@@ -4,13 +4,14 @@
 // Per pore cell P, species k, face f with outward normal n:
 //   pore or ghost neighbour:  P_f = (u_f . n) dx / D_k - z_k (phi_nb - phi_P)
 //                             J   = (D_k/dx) [B(-P_f) C_P - B(P_f) C_nb]
-//                                 = (D_k/dx) [B(-P_f) (C_P - C_nb) + P_f C_nb]
+// (each product is accurate on its own; the equivalent form
+// B(-P)(C_P - C_nb) + P C_nb cancels catastrophically for large |P|)
 //   solid face (Eq. 6):       J   = K_eff C_P,  K_eff = Ka / (1 + Ka dx/(2 D_k))
 //   lateral wall:             J   = 0
 // with B(x) = x / (exp(x) - 1) (exponential fitting of advection and
 // migration against diffusion), u_f the mean of the two cell velocities,
-// phi = psi / V_T (kept in FP64; the face difference is rounded to the
-// storage precision only after subtraction).  The inlet ghost holds C = c0,
+// phi = psi / V_T (kept to FP64 accuracy; the face difference is rounded to
+// the storage precision only after subtraction).  The inlet ghost holds C = c0,
 // phi = 0, u = u_P; the outlet ghost copies the cell (zero gradient).  Update: C_P -= (dt/dx) sum_f J.
 // Adsorbed / inflow / outflow fluxes are summed per block in FP64 into
 // per-block accumulators (fixed block -> cells map, so the totals are
@@ -101,15 +102,20 @@ __device__ __forceinline__ int np_face(unsigned f, int fc, int x, int y, int z, 
 template <typename T, int DIM, int NS>
 __global__ void __launch_bounds__(kRowBlock)
     k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
-              const double *__restrict__ phi, const uint8_t *__restrict__ fl, NPConst<T> c,
+              const typename PhiStore<T>::type *__restrict__ phi,
+              const uint8_t *__restrict__ fl, NPConst<T> c,
               double *__restrict__ acc, int nx, int ny, int nz, long long N, int walls,
               int nblocks) {
-  __shared__ double sm[3 * NS * 32];
+  using PS = PhiStore<T>;
+  using PT = typename PS::type;
+  // per-step block sums of the adsorbed / inflow / outflow fluxes in T; each
+  // block adds them to its own FP64 account
+  __shared__ T sm[3 * NS * 32];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
-  double v[3 * NS];
+  T v[3 * NS];
 #pragma unroll
-  for (int j = 0; j < 3 * NS; j++) v[j] = 0.0;
+  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
   if (x < nx) {
     const long long P = ((long long)z * ny + y) * nx + x;
     const unsigned f = fl[P];
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(kRowBlock)
         CP[k] = Cin[(size_t)k * N + P];
         sumJ[k] = T(0);
       }
-      const double phiP = phi[P];
+      const PT phiP = phi[P];
       T uP[DIM];
 #pragma unroll
       for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * N + P];
@@ -136,12 +142,12 @@ __global__ void __launch_bounds__(kRowBlock)
           for (int k = 0; k < NS; k++) {
             const T J = c.Keff[k] * CP[k];
             sumJ[k] += J;
-            v[k] += (double)J;
+            v[k] += J;
           }
           continue;
         }
         T unb, Cnb[NS];
-        double phinb;
+        PT phinb;
         if (kind == F_PORE) {
           unb = u[(size_t)a * N + Q];
           phinb = phi[Q];
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(kRowBlock)
           for (int k = 0; k < NS; k++) Cnb[k] = Cin[(size_t)k * N + Q];
         } else if (kind == F_INLET) {
           unb = uP[a];
-          phinb = 0.0;
+          phinb = PS::zero();
 #pragma unroll
           for (int k = 0; k < NS; k++) Cnb[k] = c.c0;
         } else {
@@ -159,31 +165,31 @@ __global__ void __launch_bounds__(kRowBlock)
           for (int k = 0; k < NS; k++) Cnb[k] = CP[k];
         }
         const T uf = T(0.5) * (uP[a] + unb) * sg;
-        const T dphi = (T)(phinb - phiP);
+        const T dphi = PS::diff(phinb, phiP);
 #pragma unroll
         for (int k = 0; k < NS; k++) {
           const T Pf = uf * c.dxD[k] - c.zf[k] * dphi;
           T Bp, Bm;
           bernoulli_pair(Pf, Bp, Bm);
-          const T J = c.Ddx[k] * (Bm * (CP[k] - Cnb[k]) + Pf * Cnb[k]);
+          const T J = c.Ddx[k] * (Bm * CP[k] - Bp * Cnb[k]);
           sumJ[k] += J;
-          if (kind == F_INLET) v[NS + k] -= (double)J;
-          if (kind == F_OUTLET) v[2 * NS + k] += (double)J;
+          if (kind == F_INLET) v[NS + k] -= J;
+          if (kind == F_OUTLET) v[2 * NS + k] += J;
         }
       }
 #pragma unroll
       for (int k = 0; k < NS; k++) Cout[(size_t)k * N + P] = CP[k] - c.dtdx * sumJ[k];
     }
   }
-  block_reduce<3 * NS>(v, sm, OpSum(), 0.0);
+  block_reduce<3 * NS>(v, sm, OpSum(), T(0));
   if (threadIdx.x == 0) {
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     // accumulator layout: [(3*k + kind) * nblocks + block], kind 0 Gamma, 1 In, 2 Out
 #pragma unroll
     for (int k = 0; k < NS; k++) {
-      acc[(size_t)(3 * k + 0) * nblocks + bid] += v[k];
-      acc[(size_t)(3 * k + 1) * nblocks + bid] += v[NS + k];
-      acc[(size_t)(3 * k + 2) * nblocks + bid] += v[2 * NS + k];
+      acc[(size_t)(3 * k + 0) * nblocks + bid] += (double)v[k];
+      acc[(size_t)(3 * k + 1) * nblocks + bid] += (double)v[NS + k];
+      acc[(size_t)(3 * k + 2) * nblocks + bid] += (double)v[2 * NS + k];
     }
   }
 }
@@ -365,7 +371,8 @@ template <typename T, int DIM, int NS>
 void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
   dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
   k_np_step<T, DIM, NS><<<grid, kRowBlock, 0, st>>>(
-      (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u, d->d_phi,
+      (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
+      (const typename PhiStore<T>::type *)d->d_phi,
       d->d_nflags, make_const<T>(d), d->d_acc, d->nx, d->ny, d->nz, d->N, d->walls,
       d->np_blocks);
 }
