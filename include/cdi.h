@@ -209,6 +209,31 @@ cdi_status cdi_copy_field(cdi_domain *dom, int field, double *host_dst,
  * reset; waits for the stream.  reset != 0 zeroes them afterwards. */
 cdi_status cdi_query_timing(cdi_domain *dom, cdi_timing *out, int reset);
 
+/* Dissolved amount and outlet concentration of caller-owned FP64 device
+ * fields, with no device allocation by the library.  The paper has no
+ * counterpart: this exists for callers that cannot let a library allocate
+ * device memory (programs that manage all device memory in their own pool or
+ * under a fixed budget, and loops where a cudaMalloc/cudaFree would
+ * synchronise the device).
+ *   C     device, n_species*nx*ny*nz doubles (species-major, x fastest)
+ *   ux    device, nx*ny*nz doubles: x velocity (weights the outlet mean)
+ *   mask  device, nx*ny*nz bytes, 1 = solid (excluded)
+ *   out   device, 2*n_species doubles: out[k] = sum over pore cells of
+ *         C_k dx^dim (mol, or mol per metre in 2D); out[n_species + k] =
+ *         sum(u_x C_k)/sum(u_x) over the pore cells of the last column (plain
+ *         mean if sum(u_x) = 0)
+ *   stream  cudaStream_t or NULL; the call is asynchronous on it.
+ * Scratch is a fixed static device array (34,304 bytes per device, held
+ * until the process exits); n_species above 4 is rejected with
+ * CDI_ERR_INVALID_ARG.  The first call on each device looks up the array's
+ * device address, so make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race and must be
+ * serialised.  Errors: cdi_last_error(NULL). */
+cdi_status cdi_transport_sums_noalloc(const double *C, const double *ux,
+                                      const uint8_t *mask, int dim, int nx, int ny,
+                                      int nz, int n_species, double dx_m,
+                                      double *out, void *stream);
+
 /* Message for the last failed call on dom (NULL: the last failed create on
  * this thread).  Valid until the next call on the same domain. */
 const char *cdi_last_error(const cdi_domain *dom);

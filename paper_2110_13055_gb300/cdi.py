@@ -88,6 +88,8 @@ SIGNATURES = [
     ("cdi_query_column_means", c_int, [c_void_p, c_int, c_void_p]),
     ("cdi_copy_field", c_int, [c_void_p, c_int, c_void_p, c_size_t]),
     ("cdi_query_timing", c_int, [c_void_p, ctypes.POINTER(cdi_timing), c_int]),
+    ("cdi_transport_sums_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                           c_int, c_int, c_double, c_void_p, c_void_p]),
     ("cdi_last_error", ctypes.c_char_p, [c_void_p]),
     ("cdi_destroy_domain", None, [c_void_p]),
     ("cdi_version", c_int, []),
@@ -217,6 +219,17 @@ def query_timing(handle, reset=False) -> dict:
     t = cdi_timing()
     _check(load().cdi_query_timing(handle, ctypes.byref(t), int(bool(reset))), handle)
     return {name: getattr(t, name) for name, _ in cdi_timing._fields_}
+
+
+def transport_sums_noalloc(C_ptr, ux_ptr, mask_ptr, dim, nx, ny, nz, n_species, dx, out_ptr,
+                           stream=None):
+    """Dissolved amount and outlet concentration of caller-owned device
+    arrays (raw device pointers) without any allocation by the library; for
+    callers that keep every device byte in their own memory pool.  See
+    ``cdi_transport_sums_noalloc`` in include/cdi.h."""
+    _check(load().cdi_transport_sums_noalloc(
+        c_void_p(C_ptr), c_void_p(ux_ptr), c_void_p(mask_ptr), dim, nx, ny, nz, n_species,
+        c_double(dx), c_void_p(out_ptr), c_void_p(stream) if stream else None), None)
 
 
 def destroy_domain(handle):
