@@ -62,9 +62,13 @@ typedef enum {
 } cdi_status;
 
 typedef enum {
-  CDI_FP64 = 0, /* populations, velocity, potential, concentrations in FP64 */
-  CDI_FP32 = 1  /* the same fields stored and updated in FP32; reductions,
-                   the potential solve and all accumulators stay FP64 */
+  CDI_FP64 = 0,      /* populations, velocity, potential, concentrations in FP64 */
+  CDI_FP32 = 1,      /* the same fields stored and updated in FP32; reductions,
+                        the potential solve and all accumulators stay FP64 */
+  CDI_FP32_SPLIT = 2 /* as CDI_FP32, but every population is an unevaluated pair
+                        of FP32 words (hi + lo) updated with error-free FP32
+                        transformations: FP64-class flow accuracy at FP32
+                        arithmetic rates, twice the population memory */
 } cdi_precision;
 
 /* Optional device allocator (e.g. a framework's caching allocator).

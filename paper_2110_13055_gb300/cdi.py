@@ -21,7 +21,7 @@ c_int, c_double, c_size_t, c_int64, c_void_p = (ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_size_t, ctypes.c_int64,
                                                 ctypes.c_void_p)
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_SPLIT = 0, 1, 2
 FIELD_U_LATTICE, FIELD_U, FIELD_PSI, FIELD_C = 0, 1, 2, 3
 STATUS = {0: "CDI_OK", 1: "CDI_ERR_INVALID_ARG", 2: "CDI_ERR_OOM", 3: "CDI_ERR_CUDA",
           4: "CDI_ERR_NOT_CONVERGED", 5: "CDI_ERR_TIMEOUT", 6: "CDI_ERR_STATE"}

@@ -159,7 +159,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "ny and nz must be <= 65535");
   if (!(D.dx_m > 0.0) || !std::isfinite(D.dx_m))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "dx_m must be positive");
-  if (D.precision != CDI_FP64 && D.precision != CDI_FP32)
+  if (D.precision != CDI_FP64 && D.precision != CDI_FP32 && D.precision != CDI_FP32_SPLIT)
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "unknown precision");
   if (alloc && (!alloc->alloc || !alloc->free))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "allocator needs alloc and free");
@@ -211,7 +211,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
     return CDI_ERR_CUDA;
   }
 
-  const size_t T = d->prec == CDI_FP32 ? 4 : 8;
+  const size_t T = d->prec == CDI_FP64 ? 8 : 4;
   const int Q = D.dim == 2 ? 9 : 19;
   const size_t fflag = D.dim == 2 ? 2 : 4;
   d->np_blocks = (int)(((D.nx + cdi::kRowBlock - 1) / cdi::kRowBlock) * (long long)D.ny * D.nz);
@@ -225,6 +225,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->d_fflags = A(Nf * fflag);
   d->d_nflags = (uint8_t *)A(N);
   d->d_g = A((size_t)Q * Nf * T);
+  if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A((size_t)Q * Nf * 4);
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
   d->d_u = A((size_t)D.dim * N * T);
   d->d_psi = (double *)A(N * 8);
@@ -435,7 +436,7 @@ cdi_status cdi_query_column_means(cdi_domain *d, int species, double *out) {
 
 cdi_status cdi_copy_field(cdi_domain *d, int field, double *host, size_t count) {
   if (!d || !host) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
-  const int isf = d->prec == CDI_FP32;
+  const int isf = d->prec != CDI_FP64;
   const size_t T = isf ? 4 : 8;
   const void *src = nullptr;
   size_t n = 0;

