@@ -43,15 +43,17 @@ WORKLOADS = {
               "residual, K=100), mirror along x, periodic laterally; screened potential at "
               "0.8 V (c_bulk 10 mol/m^3, dx 100 nm); Na+/Cl- z=+1/-1, D=1.33e-9/2.03e-9 m^2/s, "
               "c0=10 mol/m^3, Ka=1e-6 m/s, pore-mean velocity 1e-4 m/s; 50000 explicit "
-              "Nernst-Planck steps; FP32 storage"),
-        mask=lambda: inputs.disc_pack_1024x512()[0], prec=cdi.FP32, V=0.8, U=1e-4, c0=10.0,
+              "Nernst-Planck steps; FP32 arithmetic: populations stored as FP32 pairs "
+              "(plain FP32 stalls at residual 7e-7 with a 4e-5 velocity error here), "
+              "transport fields in FP32"),
+        mask=lambda: inputs.disc_pack_1024x512()[0], prec=cdi.FP32_SPLIT, V=0.8, U=1e-4, c0=10.0,
         np_steps=50000, flow_tol=1e-8, max_flow=1_000_000),
     "2d-2048x1024": dict(
         desc=("2D 2048x1024 polydisperse discs r~U[4,16] lu (overlap), porosity 0.5, seed 1; "
-              "as 2d-1024x512 but the populations (151 MB) exceed L2; flow to 1e-8; "
-              "50000 Nernst-Planck steps; FP32 storage"),
+              "as 2d-1024x512 but the populations exceed L2; flow to 1e-8; "
+              "50000 Nernst-Planck steps; FP32 pair populations, FP32 transport"),
         mask=lambda: inputs.grain_pack((1024, 2048), 0.5, 4.0, 16.0, seed=1)[0],
-        prec=cdi.FP32, V=0.8, U=1e-4, c0=10.0, np_steps=50000, flow_tol=1e-8,
+        prec=cdi.FP32_SPLIT, V=0.8, U=1e-4, c0=10.0, np_steps=50000, flow_tol=1e-8,
         max_flow=1_000_000),
     "3d-256": dict(
         desc=("3D 256^3 sphere pack r~U[6,12] lu (overlap), porosity 0.45, seed 2; D3Q19 BGK "
@@ -233,11 +235,18 @@ def ours(args, w, mask):
     elapsed_all, units_all = aggregate(elapsed, units)
 
     # dominant kernel and its roofline
-    T = 4 if w["prec"] == cdi.FP32 else 8
+    # algorithmic bytes per launch: every pore site of the flow grid reads and
+    # writes its Q populations (8 B each for FP64 and FP32 pairs, 4 B for
+    # FP32) plus its list index (4 B) and flag word; every pore cell of the
+    # transport grid reads and writes 2 species, reads d velocity components,
+    # the 8-byte potential, its list index and its 2-byte flags
+    Tp = 4 if w["prec"] == cdi.FP32 else 8
+    Tt = 8 if w["prec"] == cdi.FP64 else 4
     Q = 9 if dim == 2 else 19
     flag_b = 2 if dim == 2 else 4
-    lbm_bytes = 2 * n_pore * Q * 2 * T + Nf * flag_b
-    np_bytes = n_pore * (2 * 2 * T + dim * T + T + 1) + (N - n_pore)
+    n_flow_pore = 2 * n_pore
+    lbm_bytes = n_flow_pore * (Q * 2 * Tp + 4 + flag_b)
+    np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 4 + 2)
     lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
     np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3
     if tim["flow_ms"] >= tim["np_ms"]:
@@ -283,7 +292,8 @@ def ours(args, w, mask):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if w["prec"] == cdi.FP32 else "f64",
+        "dtype": "f64" if w["prec"] == cdi.FP64 else "f32",
+        "storage": {cdi.FP64: "fp64", cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations"}[w["prec"]],
         "data": "synthetic",
         "config": {"workload": w["desc"], "name": args.workload,
                    "flow_sites": Nf, "cells": N, "pore_cells": n_pore,
@@ -373,9 +383,14 @@ def main():
                          "converging; for short profiling runs")
     ap.add_argument("--np-steps", type=int, default=0,
                     help="override the number of transport steps")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-pair"], default=None,
+                    help="override the workload's storage precision")
     args = ap.parse_args()
     rank, world, local = dist_info()
     w = dict(WORKLOADS[args.workload])
+    if args.precision:
+        w["prec"] = {"fp64": cdi.FP64, "fp32": cdi.FP32, "fp32-pair": cdi.FP32_SPLIT}[args.precision]
+        w["desc"] += f" [override: {args.precision} storage]"
     if args.flow_steps:
         w.update(flow_tol=0.0, max_flow=args.flow_steps)
         w["desc"] += f" [override: exactly {args.flow_steps} flow steps]"

@@ -214,7 +214,8 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   const size_t T = d->prec == CDI_FP64 ? 8 : 4;
   const int Q = D.dim == 2 ? 9 : 19;
   const size_t fflag = D.dim == 2 ? 2 : 4;
-  d->np_blocks = (int)(((D.nx + cdi::kRowBlock - 1) / cdi::kRowBlock) * (long long)D.ny * D.nz);
+  d->n_flow_pore = n_pore * (D.mirror_x ? 2 : 1);
+  d->np_blocks = (int)((n_pore + cdi::kRowBlock - 1) / cdi::kRowBlock);
   bool ok = true;
   auto A = [&](size_t bytes) {
     void *p = cdi_dev_alloc(d, bytes);
@@ -223,7 +224,10 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   };
   d->d_mask = (uint8_t *)A(N);
   d->d_fflags = A(Nf * fflag);
-  d->d_nflags = (uint8_t *)A(N);
+  d->d_nflags = (cdi::NFlag *)A(N * sizeof(cdi::NFlag));
+  d->d_flow_list = (int *)A((size_t)d->n_flow_pore * sizeof(int));
+  d->d_cell_list = (int *)A((size_t)n_pore * sizeof(int));
+  int *list_work = (int *)A(cdi_lists_work_ints(Nf) * sizeof(int));
   d->d_g = A((size_t)Q * Nf * T);
   if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A((size_t)Q * Nf * 4);
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
@@ -269,6 +273,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
       "memset");
   if (s == CDI_OK) s = cdi_flow_build_flags(d);
   if (s == CDI_OK) s = cdi_np_build_flags(d);
+  if (s == CDI_OK) s = cdi_build_lists(d, list_work);
   if (s == CDI_OK) chk(cudaStreamSynchronize(d->stream), "create domain");
   if (s != CDI_OK) {
     g_create_error = d->err;

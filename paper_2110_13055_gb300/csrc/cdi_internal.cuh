@@ -75,14 +75,23 @@ template <> struct Lat<3> {
 };
 
 // Flow-site flag word: bit 0 = the site is solid; bit i (1..Q-1) = the
-// neighbour along e_i is solid or lies beyond a lateral wall.
+// neighbour along e_i is solid or lies beyond a lateral wall; bits Q..Q+5 =
+// the site lies on the high/low x, y, z edge of the flow grid, where the
+// periodic neighbour offsets wrap around.
 template <int DIM> struct FlowFlag;
 template <> struct FlowFlag<2> { using type = uint16_t; };
 template <> struct FlowFlag<3> { using type = uint32_t; };
+template <int DIM> struct WrapBit {
+  static constexpr int XHI = Lat<DIM>::Q, XLO = XHI + 1, YHI = XHI + 2, YLO = XHI + 3,
+                       ZHI = XHI + 4, ZLO = XHI + 5;
+};
 
-// Transport-cell flag byte: bit 0 = solid; bit 1 + f = the neighbour across
-// face f (f = +x,-x,+y,-y,+z,-z) is a solid voxel inside the image.
+// Transport-cell flag word: bit 0 = solid; bit 1 + f = the neighbour across
+// face f (f = +x,-x,+y,-y,+z,-z) is a solid voxel inside the image (after the
+// periodic wrap); bit 7 + f = face f lies on the image boundary.
+using NFlag = uint16_t;
 constexpr int kFaceBit = 1;
+constexpr int kEdgeBit = 7;
 
 // ---------------------------------------------------------------------------
 // Deterministic block reductions (fixed order, no floating-point atomics).
@@ -218,7 +227,10 @@ struct cdi_domain {
   // device buffers
   uint8_t *d_mask = nullptr;    // N
   void *d_fflags = nullptr;     // Nf flow flags
-  uint8_t *d_nflags = nullptr;  // N face flags
+  cdi::NFlag *d_nflags = nullptr;  // N face flags
+  int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
+  long long n_flow_pore = 0;
+  int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending
   void *d_g = nullptr;          // Q*Nf populations (shifted), precision T
   float *d_glo = nullptr;       // Q*Nf low parts of the populations (pair storage)
   double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64
@@ -303,6 +315,8 @@ cudaError_t cdi_timing_resolve(cdi_domain *d);
 
 // Kernel-side entry points used by the API layer.
 cdi_status cdi_flow_build_flags(cdi_domain *d);
+size_t cdi_lists_work_ints(long long n);
+cdi_status cdi_build_lists(cdi_domain *d, int *work);
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
                         double *res);
 cdi_status cdi_flow_export(cdi_domain *d, double U_target);

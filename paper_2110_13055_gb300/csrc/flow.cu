@@ -68,18 +68,20 @@ F2 host_pair(double v) {
 }
 
 // Site index and neighbour offsets in 32 bits (domains are limited to < 2^31
-// flow sites); periodic wrap folded into the offsets.
-struct SiteIdx {
+// flow sites); the periodic wrap is folded into the offsets from the edge
+// bits of the flag word, so no coordinates are needed.
+template <int DIM> struct SiteIdx {
   int s, oxp, oxm, oyp, oym, ozp, ozm;
-  __device__ __forceinline__ SiteIdx(int x, int y, int z, int NX, int ny, int nz) {
+  __device__ __forceinline__ SiteIdx(int site, unsigned f, int NX, int ny, int nz) {
+    using W = WrapBit<DIM>;
     const int plane = NX * ny;
-    s = (z * ny + y) * NX + x;
-    oxp = x + 1 == NX ? 1 - NX : 1;
-    oxm = x == 0 ? NX - 1 : -1;
-    oyp = y + 1 == ny ? (1 - ny) * NX : NX;
-    oym = y == 0 ? (ny - 1) * NX : -NX;
-    ozp = z + 1 == nz ? (1 - nz) * plane : plane;
-    ozm = z == 0 ? (nz - 1) * plane : -plane;
+    s = site;
+    oxp = (f >> W::XHI) & 1u ? 1 - NX : 1;
+    oxm = (f >> W::XLO) & 1u ? NX - 1 : -1;
+    oyp = (f >> W::YHI) & 1u ? (1 - ny) * NX : NX;
+    oym = (f >> W::YLO) & 1u ? (ny - 1) * NX : -NX;
+    ozp = (f >> W::ZHI) & 1u ? (1 - nz) * plane : plane;
+    ozm = (f >> W::ZLO) & 1u ? (nz - 1) * plane : -plane;
   }
   __device__ __forceinline__ int nb(int ex, int ey, int ez) const {
     return s + (ex > 0 ? oxp : (ex < 0 ? oxm : 0)) + (ey > 0 ? oyp : (ey < 0 ? oym : 0)) +
@@ -108,18 +110,25 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
     const int xs = X < nx ? X : 2 * nx - 1 - X;  // mirror image along x
     return mask[((size_t)Z * ny + Y) * nx + xs] != 0;
   };
-  typename FlowFlag<DIM>::type f = solid_at(x, y, z) ? 1 : 0;
+  using W = WrapBit<DIM>;
+  unsigned f = solid_at(x, y, z) ? 1u : 0u;
 #pragma unroll
   for (int i = 1; i < L::Q; i++)
     if (solid_at(x + L::ex(i), y + L::ey(i), z + L::ez(i))) f |= (1u << i);
-  fl[((size_t)z * ny + y) * NX + x] = f;
+  if (x == NX - 1) f |= 1u << W::XHI;
+  if (x == 0) f |= 1u << W::XLO;
+  if (y == ny - 1) f |= 1u << W::YHI;
+  if (y == 0) f |= 1u << W::YLO;
+  if (z == nz - 1) f |= 1u << W::ZHI;
+  if (z == 0) f |= 1u << W::ZLO;
+  fl[((size_t)z * ny + y) * NX + x] = (typename FlowFlag<DIM>::type)f;
 }
 
 // Slot read by direction i at this site (ODD: the upstream neighbour's
 // opposite slot, or the own slot after a bounce-back), and slot written by the
 // post-collision value of direction i.
 template <int DIM, bool ODD>
-__device__ __forceinline__ int read_slot(const SiteIdx &ix, unsigned f, int i, long long Nf,
+__device__ __forceinline__ int read_slot(const SiteIdx<DIM> &ix, unsigned f, int i, long long Nf,
                                          size_t &base) {
   using L = Lat<DIM>;
   if (!ODD) {
@@ -135,7 +144,7 @@ __device__ __forceinline__ int read_slot(const SiteIdx &ix, unsigned f, int i, l
   return ix.nb(-L::ex(i), -L::ey(i), -L::ez(i));
 }
 template <int DIM, bool ODD>
-__device__ __forceinline__ int write_slot(const SiteIdx &ix, unsigned f, int i, long long Nf,
+__device__ __forceinline__ int write_slot(const SiteIdx<DIM> &ix, unsigned f, int i, long long Nf,
                                           size_t &base) {
   using L = Lat<DIM>;
   if (!ODD || ((f >> i) & 1u)) {  // local write, or bounce back from a solid
@@ -152,15 +161,16 @@ __device__ __forceinline__ int write_slot(const SiteIdx &ix, unsigned f, int i, 
 // force source (1 - 1/(2 tau)) 3 w_i e_i.F; omega = 1/tau.
 template <typename T, int DIM, bool ODD>
 __global__ void __launch_bounds__(kRowBlock)
-    k_lbm_step(T *__restrict__ g, const typename FlowFlag<DIM>::type *__restrict__ fl, int NX,
-               int ny, int nz, long long Nf, T omega, T fx_half, T fsrc) {
+    k_lbm_step(T *__restrict__ g, const typename FlowFlag<DIM>::type *__restrict__ fl,
+               const int *__restrict__ sites, int n_sites, int NX, int ny, int nz,
+               long long Nf, T omega, T fx_half, T fsrc) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= NX) return;
-  const SiteIdx ix(x, blockIdx.y, blockIdx.z, NX, ny, nz);
-  const unsigned f = fl[ix.s];
-  if (f & 1u) return;
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n_sites) return;
+  const int site = sites[k0];
+  const unsigned f = fl[site];
+  const SiteIdx<DIM> ix(site, f, NX, ny, nz);
   T gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -217,7 +227,8 @@ struct SplitConst {
 template <int DIM, bool ODD>
 __global__ void __launch_bounds__(kRowBlock)
     k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
-                     const typename FlowFlag<DIM>::type *__restrict__ fl, int NX, int ny, int nz,
+                     const typename FlowFlag<DIM>::type *__restrict__ fl,
+                     const int *__restrict__ sites, int n_sites, int NX, int ny, int nz,
                      long long Nf, SplitConst c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
@@ -226,11 +237,11 @@ __global__ void __launch_bounds__(kRowBlock)
   constexpr F2 kW0 = {(float)w0, (float)(w0 - (double)(float)w0)};
   constexpr F2 kWA = {(float)wa, (float)(wa - (double)(float)wa)};
   constexpr F2 kWD = {(float)wd, (float)(wd - (double)(float)wd)};
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= NX) return;
-  const SiteIdx ix(x, blockIdx.y, blockIdx.z, NX, ny, nz);
-  const unsigned f = fl[ix.s];
-  if (f & 1u) return;
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n_sites) return;
+  const int site = sites[k0];
+  const unsigned f = fl[site];
+  const SiteIdx<DIM> ix(site, f, NX, ny, nz);
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -412,23 +423,26 @@ template <int M, int DIM>
 void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
   using FT = typename FlowFlag<DIM>::type;
   using T = typename ModeT<M>::T;
-  const dim3 grid((d->NX + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
+  // one thread per pore site of the flow grid
+  const int n = (int)d->n_flow_pore;
+  const int grid = (n + kRowBlock - 1) / kRowBlock;
+  const FT *fl = (const FT *)d->d_fflags;
   if (M == M_SPLIT) {
     const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
     const SplitConst c{host_pair(1.0 / tau), host_pair(0.5 * force),
                        host_pair(fs * Lat<DIM>::w(1)),
                        host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
     k_lbm_step_split<DIM, false><<<grid, kRowBlock, 0, st>>>(
-        (float *)d->d_g, d->d_glo, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, c);
+        (float *)d->d_g, d->d_glo, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, c);
     k_lbm_step_split<DIM, true><<<grid, kRowBlock, 0, st>>>(
-        (float *)d->d_g, d->d_glo, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, c);
+        (float *)d->d_g, d->d_glo, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, c);
   } else {
     const T omega = T(1.0 / tau), fxh = T(0.5 * force);
     const T fsrc = T((1.0 - 0.5 / tau) * 3.0 * force);
     k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>(
-        (T *)d->d_g, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
+        (T *)d->d_g, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
     k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>(
-        (T *)d->d_g, (const FT *)d->d_fflags, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
+        (T *)d->d_g, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
   }
 }
 

@@ -23,7 +23,7 @@ struct Geo {
 
 // Face f of pore cell (x,y,z): 0 pore neighbour (index in *nb), 1 solid,
 // 2 inlet feed, 3 no flux (outlet or lateral wall).
-__device__ __forceinline__ int face_kind(const Geo &g, const uint8_t *fl, long long P, int x,
+__device__ __forceinline__ int face_kind(const Geo &g, const NFlag *fl, long long P, int x,
                                          int y, int z, int f, long long *nb) {
   const int a = f >> 1;
   const int s = (f & 1) ? -1 : 1;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void coords(const Geo &g, long long P, int &x, int &y
 
 // diag, right-hand side, x = 0, r = b, z = r / diag, p = z; rz and b.b.
 __global__ void __launch_bounds__(kRedThreads)
-    k_cg_setup(Geo g, const uint8_t *__restrict__ fl, double kdx2, double psi_s, double tol,
+    k_cg_setup(Geo g, const NFlag *__restrict__ fl, double kdx2, double psi_s, double tol,
                double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
                double *__restrict__ diag, double *__restrict__ part, unsigned int *counter,
                double *scal) {
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kRedThreads)
 
 // q = A p and p.q; alpha = rz / p.q.
 __global__ void __launch_bounds__(kRedThreads)
-    k_cg_spmv(Geo g, const uint8_t *__restrict__ fl, const double *__restrict__ p,
+    k_cg_spmv(Geo g, const NFlag *__restrict__ fl, const double *__restrict__ p,
               const double *__restrict__ diag, double *__restrict__ q,
               double *__restrict__ part, unsigned int *counter, double *scal) {
   if (scal[S_CG_DONE] != 0.0) return;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kRedThreads)
 
 // x += alpha p, r -= alpha q, z = r / diag (into q); beta = rz' / rz.
 __global__ void __launch_bounds__(kRedThreads)
-    k_cg_update(long long N, const uint8_t *__restrict__ fl, double *__restrict__ x,
+    k_cg_update(long long N, const NFlag *__restrict__ fl, double *__restrict__ x,
                 double *__restrict__ r, const double *__restrict__ p, double *__restrict__ q,
                 const double *__restrict__ diag, double *__restrict__ part,
                 unsigned int *counter, double *scal) {
@@ -206,7 +206,7 @@ __global__ void k_cg_dir(long long N, double *__restrict__ p, const double *__re
 
 // phi = psi / V_T (0 in solid cells) in the transport kernel's format.
 template <typename T>
-__global__ void k_phi(long long N, const uint8_t *__restrict__ fl, const double *__restrict__ psi,
+__global__ void k_phi(long long N, const NFlag *__restrict__ fl, const double *__restrict__ psi,
                       typename PhiStore<T>::type *__restrict__ phi, double inv_vt) {
   for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
        P += (long long)gridDim.x * blockDim.x)

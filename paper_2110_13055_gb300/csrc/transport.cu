@@ -36,66 +36,54 @@ template <typename T> struct NPConst {
 };
 
 template <int DIM>
-__global__ void k_np_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ fl, int nx,
+__global__ void k_np_flags(const uint8_t *__restrict__ mask, NFlag *__restrict__ fl, int nx,
                            int ny, int nz, int walls) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   const long long P = ((long long)z * ny + y) * nx + x;
-  uint8_t f = mask[P] ? 1 : 0;
+  unsigned f = mask[P] ? 1u : 0u;
   for (int fc = 0; fc < 2 * DIM; fc++) {
     const int a = fc >> 1, s = (fc & 1) ? -1 : 1;
     int X = x, Y = y, Z = z;
+    bool edge = false;
     if (a == 0) {
       X += s;
-      if (X < 0 || X >= nx) continue;
+      edge = X < 0 || X >= nx;
     } else if (a == 1) {
       Y += s;
-      if (Y < 0 || Y >= ny) {
-        if (walls) continue;
-        Y = (Y + ny) % ny;
-      }
+      edge = Y < 0 || Y >= ny;
+      Y = (Y + ny) % ny;
     } else {
       Z += s;
-      if (Z < 0 || Z >= nz) {
-        if (walls) continue;
-        Z = (Z + nz) % nz;
-      }
+      edge = Z < 0 || Z >= nz;
+      Z = (Z + nz) % nz;
     }
-    if (mask[((long long)Z * ny + Y) * nx + X]) f |= (uint8_t)(1u << (kFaceBit + fc));
+    if (edge) f |= 1u << (kEdgeBit + fc);
+    if ((a == 0 && edge) || (edge && walls)) continue;
+    if (mask[((long long)Z * ny + Y) * nx + X]) f |= 1u << (kFaceBit + fc);
   }
-  fl[P] = f;
+  fl[P] = (NFlag)f;
 }
 
-// Face kind and neighbour index of face fc of cell (x,y,z).
+// Face kind of face fc of pore cell P and, for a pore neighbour, its index Q,
+// from the flag word alone (the edge bits carry the boundary position).
 template <int DIM>
-__device__ __forceinline__ int np_face(unsigned f, int fc, int x, int y, int z, int nx, int ny,
-                                       int nz, int walls, long long P, long long &Q) {
+__device__ __forceinline__ int np_face(unsigned f, int fc, int nx, int ny, int nz, int walls,
+                                       long long P, long long &Q) {
   const int a = fc >> 1, s = (fc & 1) ? -1 : 1;
+  const bool edge = (f >> (kEdgeBit + fc)) & 1u;
   if (a == 0) {
-    if (x + s < 0) return F_INLET;
-    if (x + s >= nx) return F_OUTLET;
+    if (edge) return s > 0 ? F_OUTLET : F_INLET;
     if ((f >> (kFaceBit + fc)) & 1u) return F_SOLID;
     Q = P + s;
     return F_PORE;
   }
-  if (a == 1) {
-    int Y = y + s;
-    if (Y < 0 || Y >= ny) {
-      if (walls) return F_WALL;
-      Y = Y < 0 ? ny - 1 : 0;
-    }
-    if ((f >> (kFaceBit + fc)) & 1u) return F_SOLID;
-    Q = ((long long)z * ny + Y) * nx + x;
-    return F_PORE;
-  }
-  int Z = z + s;
-  if (Z < 0 || Z >= nz) {
-    if (walls) return F_WALL;
-    Z = Z < 0 ? nz - 1 : 0;
-  }
+  if (edge && walls) return F_WALL;
   if ((f >> (kFaceBit + fc)) & 1u) return F_SOLID;
-  Q = ((long long)Z * ny + y) * nx + x;
+  const long long stride = a == 1 ? (long long)nx : (long long)nx * ny;
+  const long long extent = a == 1 ? ny : nz;
+  Q = P + (edge ? -s * (extent - 1) * stride : s * stride);
   return F_PORE;
 }
 
@@ -154,23 +142,23 @@ template <typename T, int DIM, int NS>
 __global__ void __launch_bounds__(kRowBlock)
     k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
               const typename PhiStore<T>::type *__restrict__ phi,
-              const uint8_t *__restrict__ fl, NPConst<T> c,
-              double *__restrict__ acc, int nx, int ny, int nz, long long N, int walls,
-              int nblocks) {
+              const NFlag *__restrict__ fl, const int *__restrict__ cells, int n_cells,
+              NPConst<T> c, double *__restrict__ acc, int nx, int ny, int nz, long long N,
+              int walls) {
   using PS = PhiStore<T>;
   using PT = typename PS::type;
   // per-step block sums of the adsorbed / inflow / outflow fluxes in T; each
-  // block adds them to its own FP64 account
+  // block adds them to its own FP64 account (one thread per pore cell, so
+  // the block -> cells map is fixed and the totals are deterministic)
   __shared__ T sm[3 * NS * 32];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   T v[3 * NS];
 #pragma unroll
   for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-  if (x < nx) {
-    const long long P = ((long long)z * ny + y) * nx + x;
+  if (k0 < n_cells) {
+    const long long P = cells[k0];
     const unsigned f = fl[P];
-    if (!(f & 1u)) {
+    {
       T CP[NS], sumJ[NS];
 #pragma unroll
       for (int k = 0; k < NS; k++) {
@@ -186,7 +174,7 @@ __global__ void __launch_bounds__(kRowBlock)
         const int a = fc >> 1;
         const T sg = (fc & 1) ? T(-1) : T(1);
         long long Q = 0;
-        const int kind = np_face<DIM>(f, fc, x, y, z, nx, ny, nz, walls, P, Q);
+        const int kind = np_face<DIM>(f, fc, nx, ny, nz, walls, P, Q);
         if (kind == F_WALL) continue;
         if (kind == F_SOLID) {
 #pragma unroll
@@ -234,7 +222,7 @@ __global__ void __launch_bounds__(kRowBlock)
   }
   block_reduce<3 * NS>(v, sm, OpSum(), T(0));
   if (threadIdx.x == 0) {
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int bid = blockIdx.x, nblocks = gridDim.x;
     // accumulator layout: [(3*k + kind) * nblocks + block], kind 0 Gamma, 1 In, 2 Out
 #pragma unroll
     for (int k = 0; k < NS; k++) {
@@ -250,7 +238,7 @@ __global__ void __launch_bounds__(kRowBlock)
 // + n_solid K_eff]; dt = safety / max.
 template <int DIM>
 __global__ void __launch_bounds__(kRedThreads)
-    k_np_rate(const uint8_t *__restrict__ fl, const double *__restrict__ uflow,
+    k_np_rate(const NFlag *__restrict__ fl, const double *__restrict__ uflow,
               const double *__restrict__ psi, NPConst<double> c, int ns, double scale,
               double inv_vt, double inv_dx, double safety, int nx, int NX, int ny, int nz,
               long long N, long long Nf, int walls, double *__restrict__ part,
@@ -263,8 +251,6 @@ __global__ void __launch_bounds__(kRedThreads)
     if (f & 1u) continue;
     const long long row = P / nx;
     const int x = (int)(P - row * nx);
-    const int z = (int)(row / ny);
-    const int y = (int)(row - (long long)z * ny);
     const long long sP = row * NX + x;
     for (int k = 0; k < ns; k++) {
       double rate = 0.0;
@@ -272,7 +258,7 @@ __global__ void __launch_bounds__(kRedThreads)
         const int a = fc >> 1;
         const double sg = (fc & 1) ? -1.0 : 1.0;
         long long Q = 0;
-        const int kind = np_face<DIM>(f, fc, x, y, z, nx, ny, nz, walls, P, Q);
+        const int kind = np_face<DIM>(f, fc, nx, ny, nz, walls, P, Q);
         if (kind == F_WALL) continue;
         if (kind == F_SOLID) {
           rate += c.Keff[k];
@@ -309,7 +295,7 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 template <typename T>
-__global__ void k_np_init(const uint8_t *__restrict__ fl, T *__restrict__ C0, T *__restrict__ C1,
+__global__ void k_np_init(const NFlag *__restrict__ fl, T *__restrict__ C0, T *__restrict__ C1,
                           long long N, int ns, T c0) {
   for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
        P += (long long)gridDim.x * blockDim.x) {
@@ -328,7 +314,7 @@ __global__ void k_np_init(const uint8_t *__restrict__ fl, T *__restrict__ C0, T 
 // sum of C at the outlet, 13 pore cells in the outlet column.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_np_sums(const uint8_t *__restrict__ fl, const T *__restrict__ C, const T *__restrict__ u,
+    k_np_sums(const NFlag *__restrict__ fl, const T *__restrict__ C, const T *__restrict__ u,
               long long N, int nx, int ns, double cell_vol, double *__restrict__ part,
               unsigned int *counter, double *scal) {
   constexpr int NV = 14;
@@ -390,7 +376,7 @@ __global__ void __launch_bounds__(kRedThreads)
 // Mean of species k over the pore cells of each x column.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_colmeans(const uint8_t *__restrict__ fl, const T *__restrict__ C, int nx, long long rows,
+    k_colmeans(const NFlag *__restrict__ fl, const T *__restrict__ C, int nx, long long rows,
                double *__restrict__ out) {
   __shared__ double sm[2 * 32];
   const int x = blockIdx.x;
@@ -420,12 +406,11 @@ template <typename T> NPConst<T> make_const(const cdi_domain *d) {
 
 template <typename T, int DIM, int NS>
 void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
-  dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
-  k_np_step<T, DIM, NS><<<grid, kRowBlock, 0, st>>>(
+  // one thread per pore cell; np_blocks blocks, one FP64 account set each
+  k_np_step<T, DIM, NS><<<d->np_blocks, kRowBlock, 0, st>>>(
       (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
-      (const typename PhiStore<T>::type *)d->d_phi,
-      d->d_nflags, make_const<T>(d), d->d_acc, d->nx, d->ny, d->nz, d->N, d->walls,
-      d->np_blocks);
+      (const typename PhiStore<T>::type *)d->d_phi, d->d_nflags, d->d_cell_list,
+      (int)d->n_pore, make_const<T>(d), d->d_acc, d->nx, d->ny, d->nz, d->N, d->walls);
 }
 
 template <typename T, int DIM>
