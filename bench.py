@@ -62,6 +62,12 @@ WORKLOADS = {
               "velocity 1e-6 m/s; 20000 Nernst-Planck steps; FP32 storage"),
         mask=lambda: inputs.sphere_pack_256()[0], prec=cdi.FP32, V=1.2, U=1e-6, c0=20.0,
         np_steps=20000, flow_tol=1e-7, max_flow=20000),
+    "3d-160": dict(
+        desc=("3D 160^3 sphere pack r~U[6,12] lu (overlap), porosity 0.45, seed 2 (a profiling "
+              "case of the 256^3 recipe whose populations still exceed L2); D3Q19 tau=1; flow "
+              "capped at 20000 steps; 1.2 V, c0=20 mol/m^3; 20000 Nernst-Planck steps; FP32"),
+        mask=lambda: inputs.grain_pack((160, 160, 160), 0.45, 6.0, 12.0, seed=2)[0],
+        prec=cdi.FP32, V=1.2, U=1e-6, c0=20.0, np_steps=20000, flow_tol=1e-7, max_flow=20000),
     "2d-128x64": dict(
         desc=("2D 128x64 non-overlapping discs r=6 lu, porosity 0.6, seed 0; D2Q9 tau=1, "
               "Stokes to residual 1e-8; 1.0 V; Na+/Cl-, c0=10 mol/m^3; 2000 Nernst-Planck "
@@ -237,15 +243,15 @@ def ours(args, w, mask):
     # dominant kernel and its roofline
     # algorithmic bytes per launch: every pore site of the flow grid reads and
     # writes its Q populations (8 B each for FP64 and FP32 pairs, 4 B for
-    # FP32) plus its list index (4 B) and flag word; every pore cell of the
-    # transport grid reads and writes 2 species, reads d velocity components,
-    # the 8-byte potential, its list index and its 2-byte flags
+    # FP32); odd steps also read its Q-1 neighbour ranks (4 B each), so a
+    # launch averages half of that; every pore cell of the transport grid
+    # reads and writes 2 species, reads d velocity components, the 8-byte
+    # potential, its list index and its 2-byte flags
     Tp = 4 if w["prec"] == cdi.FP32 else 8
     Tt = 8 if w["prec"] == cdi.FP64 else 4
     Q = 9 if dim == 2 else 19
-    flag_b = 2 if dim == 2 else 4
     n_flow_pore = 2 * n_pore
-    lbm_bytes = n_flow_pore * (Q * 2 * Tp + 4 + flag_b)
+    lbm_bytes = n_flow_pore * (Q * 2 * Tp + (Q - 1) * 4 // 2)
     np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 4 + 2)
     lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
     np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3
@@ -323,6 +329,158 @@ def ours(args, w, mask):
     return line
 
 
+SWEEP_V = (0.2, 0.6, 1.0, 1.2)
+SWEEP_U = (1e-5, 1e-4, 1e-3)
+
+
+def sweep_geometries(n_geom, seed0=10):
+    """The batched-sweep recipe: seeded polydisperse disc packs (r ~ U[4,16],
+    overlap allowed), porosity ~ U[0.4, 0.7] drawn from the seed."""
+    out = []
+    for k in range(n_geom):
+        rs = np.random.default_rng(seed0 + k)
+        phi = float(rs.uniform(0.4, 0.7))
+        m, _ = inputs.grain_pack((256, 256), phi, 4.0, 16.0, seed=seed0 + k)
+        out.append(m)
+    return out
+
+
+def sweep_bench(args):
+    """Batched sweep against the plain one-solve-at-a-time loop, at equal
+    results: every (geometry, V, U) is one solve of flow + potential +
+    transport.  The plain loop runs each solve from scratch through the C ABI
+    (create, flow, potential, transport, queries, destroy); the batched path
+    solves each geometry's flow once, shares potentials across velocities and
+    advances all 12 combinations of a geometry in one fused launch per step."""
+    import torch
+    torch.cuda.set_device(0)
+    geoms = sweep_geometries(args.sweep_geometries)
+    combos = [(U, V) for V in SWEEP_V for U in SWEEP_U]
+    n_np = args.np_steps or 5000
+    prec = cdi.FP32_SPLIT
+    kw = dict(tol=1e-8, max_steps=1_000_000)
+
+    def batched(m):
+        with cdi.Domain(m, precision=prec) as d:
+            d.solve_flow(U_target=1e-4, **kw)
+            g, c, _ = d.sweep(combos, n_steps=n_np)
+        return g, c
+
+    def plain(m, U, V):
+        with cdi.Domain(m, precision=prec) as d:
+            d.solve_flow(U_target=U if U else 1e-4, **kw)
+            if U == 0:
+                d.set_velocity(0.0)
+            d.set_potential(V, c_bulk=10.0, tol=1e-12)
+            d.init_transport(Z, D, c0=10.0, Ka=1e-6)
+            d.step(n_np)
+            return d.adsorbed(), d.outlet()
+
+    batched(geoms[0])                       # warm-up (kernel loading, graphs)
+    torch.cuda.synchronize()
+    lat_b, res_b = [], []
+    t0 = time.perf_counter()
+    for m in geoms:
+        t = time.perf_counter()
+        res_b.append(batched(m))
+        lat_b.extend([time.perf_counter() - t] * len(combos))  # all finish together
+    t_b = time.perf_counter() - t0
+    lat_p, res_p = [], []
+    t0 = time.perf_counter()
+    for m in geoms:
+        gs, cs = [], []
+        for U, V in combos:
+            t = time.perf_counter()
+            g, c = plain(m, U, V)
+            lat_p.append(time.perf_counter() - t)
+            gs.append(g)
+            cs.append(c)
+        res_p.append((np.array(gs), np.array(cs)))
+    t_p = time.perf_counter() - t0
+    n_solves = len(geoms) * len(combos)
+    diff = max(float(np.max(np.abs(b[0] - p[0]) / np.abs(p[0]))) for b, p in zip(res_b, res_p))
+    same = all(np.array_equal(b[0], p[0]) and np.array_equal(b[1], p[1])
+               for b, p in zip(res_b, res_p))
+    return {
+        "metric": "sweep solves/s (batched vs plain loop, equal results)",
+        "value": n_solves / t_b, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "storage": "fp32-pair populations", "data": "synthetic",
+        "config": {"workload": (f"{len(geoms)} 2D 256x256 polydisperse disc packs (r~U[4,16], "
+                                f"porosity ~U[0.4,0.7], seeds 10..) x V {SWEEP_V} x U {SWEEP_U}; "
+                                f"flow to 1e-8 per geometry; {n_np} Nernst-Planck steps per "
+                                "solve; wall-clock with host buffers (through the C ABI)"),
+                   "solves": n_solves},
+        "plain": {"value": n_solves / t_p, "p50_s": float(np.percentile(lat_p, 50)),
+                  "p99_s": float(np.percentile(lat_p, 99)), "seconds": t_p},
+        "batched": {"value": n_solves / t_b, "p50_s": float(np.percentile(lat_b, 50)),
+                    "p99_s": float(np.percentile(lat_b, 99)), "seconds": t_b},
+        "speedup": t_p / t_b,
+        "results_bitwise_equal": same, "max_rel_gamma_diff": diff,
+    }
+
+
+def serve_requests(n, seed=100):
+    """Mixed request stream: half 2D 256x256 disc packs (FP32-pair flow to 1e-8),
+    half 3D sphere packs n^3, n in {48, 64, 80, 96} (FP32 flow to 1e-7);
+    porosity ~U[0.4, 0.6], potential ~U[0.2, 1.2] V, 2000 transport steps."""
+    from paper_2110_13055_gb300 import serve
+    rs = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        phi = float(rs.uniform(0.4, 0.6))
+        V = float(rs.uniform(0.2, 1.2))
+        s = int(rs.integers(1, 1 << 30))
+        if rs.random() < 0.5:
+            m, _ = inputs.grain_pack((256, 256), phi, 4.0, 16.0, seed=s)
+            reqs.append(serve.Request(m, V, 1e-4, 2000, precision=cdi.FP32_SPLIT,
+                                      flow_tol=1e-8, tag=i))
+        else:
+            k = int(rs.choice([48, 64, 80, 96]))
+            m, _ = inputs.grain_pack((k, k, k), phi, 3.0, 6.0, seed=s)
+            reqs.append(serve.Request(m, V, 1e-6, 2000, precision=cdi.FP32, flow_tol=1e-7,
+                                      max_flow_steps=200_000, c0=20.0, tag=i))
+    return reqs
+
+
+def serve_bench(args):
+    """Poisson arrivals at rates around the sequential capacity, the
+    continuous-batching server against the plain sequential loop."""
+    import torch
+    from paper_2110_13055_gb300 import serve
+    torch.cuda.set_device(0)
+    n = args.serve_requests
+    serve.solve(serve_requests(1, seed=7)[0])           # warm-up
+    # capacity of the plain loop (back-to-back, no waiting)
+    probe = serve_requests(n, seed=100)
+    t0 = time.perf_counter()
+    serve.run_sequential(probe, [0.0] * n)
+    cap = n / (time.perf_counter() - t0)
+    out = {"metric": "served solves/s and p99 latency vs plain sequential loop",
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"requests_per_rate": n, "mix": serve_requests.__doc__.strip(),
+                      "sequential_capacity_solves_per_s": cap, "slots": args.serve_slots,
+                      "memory_budget_GiB": args.serve_budget_gib},
+           "rates": []}
+    rs = np.random.default_rng(5)
+    for frac in (0.5, 1.0, 1.5, 2.0):
+        rate = frac * cap
+        arrivals = list(np.cumsum(rs.exponential(1.0 / rate, size=n)))
+        seq = serve.run_sequential(serve_requests(n, seed=100), arrivals)
+        srv = serve.run_served(serve_requests(n, seed=100), arrivals, slots=args.serve_slots,
+                               memory_budget=int(args.serve_budget_gib * (1 << 30)))
+        same = all(np.array_equal(a.result["Gamma"], b.result["Gamma"])
+                   for a, b in zip(sorted(seq, key=lambda r: r.tag),
+                                   sorted(srv, key=lambda r: r.tag)))
+        out["rates"].append({"offered_fraction_of_capacity": frac, "rate_per_s": rate,
+                             "sequential": serve.latency_stats(seq),
+                             "served": serve.latency_stats(srv),
+                             "results_bitwise_equal": same})
+    best = max(r["served"]["solves_per_s"] for r in out["rates"])
+    out["value"] = best
+    return out
+
+
 def oracle_sample(mask, w, flow_steps, np_steps):
     """Time the FP64 oracle as it stands on a bounded sample of the workload:
     flow_steps LBM steps on the full flow grid, the potential solve, np_steps
@@ -375,8 +533,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d-1024x512", choices=list(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-flow-steps", type=int, default=100)
-    ap.add_argument("--ref-np-steps", type=int, default=40)
+    ap.add_argument("--ref-flow-steps", type=int, default=0,
+                    help="oracle sample: LBM steps (0: about 1e8 site updates)")
+    ap.add_argument("--ref-np-steps", type=int, default=0,
+                    help="oracle sample: transport steps (0: about 2e7 cell updates)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flow-steps", type=int, default=0,
                     help="run exactly this many flow steps (multiple of 100) instead of "
@@ -385,8 +545,20 @@ def main():
                     help="override the number of transport steps")
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-pair"], default=None,
                     help="override the workload's storage precision")
+    ap.add_argument("--sweep", action="store_true",
+                    help="batched parameter sweep against the plain loop (solves/s)")
+    ap.add_argument("--sweep-geometries", type=int, default=8)
+    ap.add_argument("--serve", action="store_true",
+                    help="continuous-batching server against the sequential loop")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     args = ap.parse_args()
     rank, world, local = dist_info()
+    if args.sweep or args.serve:
+        if rank == 0:
+            print(json.dumps(sweep_bench(args) if args.sweep else serve_bench(args)), flush=True)
+        return
     w = dict(WORKLOADS[args.workload])
     if args.precision:
         w["prec"] = {"fp64": cdi.FP64, "fp32": cdi.FP32, "fp32-pair": cdi.FP32_SPLIT}[args.precision]
@@ -398,6 +570,11 @@ def main():
         w["np_steps"] = args.np_steps
         w["desc"] += f" [override: {args.np_steps} transport steps]"
     mask = w["mask"]()
+    # bounded oracle sample (10-30 s of single-thread CPU work on any workload)
+    if not args.ref_flow_steps:
+        args.ref_flow_steps = max(2, int(round(1e8 / (2 * mask.size) / 2)) * 2)
+    if not args.ref_np_steps:
+        args.ref_np_steps = max(1, int(round(2e7 / mask.size)))
     if args.impl == "reference":
         # the oracle runs on rank 0 alone; the other ranks exit without work
         line = reference(args, w, mask)

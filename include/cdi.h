@@ -185,6 +185,36 @@ cdi_status cdi_init_transport(cdi_domain *dom, const cdi_species *sp,
 /* Advance n_steps >= 0 explicit steps (Eq. 3 with Eq. 6); asynchronous. */
 cdi_status cdi_step_transport(cdi_domain *dom, int64_t n_steps);
 
+/* One member of a transport sweep. */
+typedef struct {
+  double U_mps;     /* pore-mean velocity (the solved flow rescaled, Sec. 4) */
+  double applied_V; /* surface potential -applied_V (Eq. 4, Sec. 2) */
+} cdi_combo;
+
+/* Batched transport sweep on one geometry: the parameter studies of Sec. 4.1
+ * (velocity), Sec. 4.2 (potential) and Sec. 5 run many transport problems on
+ * one electrode image.  Every member reuses the domain's solved Stokes flow
+ * rescaled to its velocity (the flow is linear in the driving force, Eq. 2),
+ * members with equal applied_V share one potential solve, and all members
+ * advance together: one fused kernel launch per step reads the geometry once
+ * for all of them.  Each member takes its own explicit time step (the bound
+ * of cdi_init_transport) and its result equals, bit for bit, that of a single
+ * run (cdi_set_velocity, cdi_set_potential, cdi_init_transport,
+ * cdi_step_transport, queries) with the same arguments.  Every member starts
+ * from the saturated state (c0) and runs n_steps steps.
+ *   gamma_out, cout_out: host, n_combos * n_species doubles (member-major):
+ *     adsorbed amount and outlet concentration as cdi_query_adsorbed and
+ *     cdi_query_outlet report them;  dt_out: n_combos doubles or NULL.
+ * Needs a solved flow; blocks until done.  Replaces the domain's potential
+ * and transport state (set them again before cdi_step_transport).  Device
+ * memory for the members is taken from the domain's allocator for the call
+ * only: about n_combos * (dim + 8) * 4 bytes per cell in FP32. */
+cdi_status cdi_sweep_transport(cdi_domain *dom, const cdi_combo *combos, int n_combos,
+                               const cdi_elec_params *p, const cdi_species *sp,
+                               int n_species, double c0_molm3, double Ka_mps,
+                               int64_t n_steps, double *gamma_out, double *cout_out,
+                               double *dt_out);
+
 /* Adsorbed amount per species since cdi_init_transport: mol (3D) or mol per
  * metre of depth (2D).  Waits for the stream. */
 cdi_status cdi_query_adsorbed(cdi_domain *dom, double *per_species);

@@ -55,6 +55,10 @@ class cdi_species(ctypes.Structure):
     _fields_ = [("z", c_int), ("D_m2s", c_double)]
 
 
+class cdi_combo(ctypes.Structure):
+    _fields_ = [("U_mps", c_double), ("applied_V", c_double)]
+
+
 class cdi_timing(ctypes.Structure):
     _fields_ = [("flow_ms", c_double), ("flow_launches", c_int64),
                 ("flow_check_ms", c_double), ("psi_ms", c_double), ("psi_iters", c_int64),
@@ -82,6 +86,10 @@ SIGNATURES = [
     ("cdi_init_transport", c_int, [c_void_p, ctypes.POINTER(cdi_species), c_int, c_double,
                                    c_double, c_double, ctypes.POINTER(c_double)]),
     ("cdi_step_transport", c_int, [c_void_p, c_int64]),
+    ("cdi_sweep_transport", c_int, [c_void_p, ctypes.POINTER(cdi_combo), c_int,
+                                    ctypes.POINTER(cdi_elec_params),
+                                    ctypes.POINTER(cdi_species), c_int, c_double, c_double,
+                                    c_int64, c_void_p, c_void_p, c_void_p]),
     ("cdi_query_adsorbed", c_int, [c_void_p, c_void_p]),
     ("cdi_query_outlet", c_int, [c_void_p, c_void_p]),
     ("cdi_query_mass_balance", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -182,6 +190,19 @@ def init_transport(handle, z, D, c0, Ka, dt=0.0):
 
 def step_transport(handle, n_steps: int):
     _check(load().cdi_step_transport(handle, c_int64(n_steps)), handle)
+
+
+def sweep_transport(handle, combos, params: cdi_elec_params, z, D, c0, Ka, n_steps):
+    """combos: sequence of (U_mps, applied_V).  Returns (gamma, c_out, dt) with
+    gamma and c_out of shape (n_combos, n_species)."""
+    nc, ns = len(combos), len(z)
+    cb = (cdi_combo * nc)(*[cdi_combo(float(U), float(V)) for U, V in combos])
+    sp = (cdi_species * ns)(*[cdi_species(int(zz), float(dd)) for zz, dd in zip(z, D)])
+    gam, cout, dt = np.zeros((nc, ns)), np.zeros((nc, ns)), np.zeros(nc)
+    _check(load().cdi_sweep_transport(handle, cb, nc, ctypes.byref(params), sp, ns,
+                                      c_double(c0), c_double(Ka), c_int64(n_steps), _dptr(gam),
+                                      _dptr(cout), _dptr(dt)), handle)
+    return gam, cout, dt
 
 
 def query_adsorbed(handle, ns: int) -> np.ndarray:
@@ -336,6 +357,17 @@ class Domain:
 
     def step(self, n):
         step_transport(self.handle, n)
+
+    def sweep(self, combos, *, z=(1, -1), D=(1.33e-9, 2.03e-9), c0=10.0, Ka=1e-6,
+              n_steps=5000, T=298.15, eps_r=78.5, c_bulk=None, lambda_D=0.0, mode="debye",
+              tol=1e-12, max_iter=100000):
+        """Batched transport over (U_mps, applied_V) combinations on the solved
+        flow; see cdi_sweep_transport."""
+        p = cdi_elec_params(float(T), float(eps_r), float(c0 if c_bulk is None else c_bulk),
+                            float(lambda_D or 0.0), 0 if mode == "debye" else 1, float(tol),
+                            int(max_iter))
+        self.ns = 0
+        return sweep_transport(self.handle, combos, p, z, D, c0, Ka, n_steps)
 
     def adsorbed(self):
         return query_adsorbed(self.handle, self.ns)

@@ -39,6 +39,19 @@ void *cdi_dev_alloc(cdi_domain *d, size_t bytes) {
   return p;
 }
 
+// Release one block from cdi_dev_alloc (after the stream has finished with it).
+void cdi_dev_release(cdi_domain *d, void *p) {
+  for (size_t i = 0; i < d->blocks.size(); i++) {
+    if (d->blocks[i].p != p) continue;
+    if (d->has_alloc)
+      d->alloc.free(p, d->blocks[i].bytes, d->alloc.ctx);
+    else
+      cudaFree(p);
+    d->blocks.erase(d->blocks.begin() + (long)i);
+    return;
+  }
+}
+
 static void free_all(cdi_domain *d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
   for (auto &b : d->blocks) {
@@ -228,8 +241,12 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->d_flow_list = (int *)A((size_t)d->n_flow_pore * sizeof(int));
   d->d_cell_list = (int *)A((size_t)n_pore * sizeof(int));
   int *list_work = (int *)A(cdi_lists_work_ints(Nf) * sizeof(int));
-  d->d_g = A((size_t)Q * Nf * T);
-  if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A((size_t)Q * Nf * 4);
+  int *rank_work = (int *)A((size_t)Nf * sizeof(int));
+  // populations stored by pore rank: Q * n_flow_pore values
+  const size_t nq = (size_t)Q * d->n_flow_pore;
+  d->d_g = A(nq * T);
+  if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A(nq * 4);
+  d->d_nbr = (int *)A((size_t)(Q - 1) * d->n_flow_pore * sizeof(int));
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
   d->d_u = A((size_t)D.dim * N * T);
   d->d_psi = (double *)A(N * 8);
@@ -262,7 +279,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   chk(cudaMemcpyAsync(d->d_mask, mask, N, cudaMemcpyHostToDevice, d->stream), "upload mask");
   chk(cudaMemsetAsync(d->d_counter, 0, 16 * sizeof(unsigned int), d->stream), "memset");
   chk(cudaMemsetAsync(d->d_scal, 0, 64 * 8, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_g, 0, (size_t)Q * Nf * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_g, 0, nq * T, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_uflow, 0, (size_t)D.dim * Nf * 8, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_u, 0, (size_t)D.dim * N * T, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_psi, 0, N * 8, d->stream), "memset");
@@ -274,7 +291,12 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   if (s == CDI_OK) s = cdi_flow_build_flags(d);
   if (s == CDI_OK) s = cdi_np_build_flags(d);
   if (s == CDI_OK) s = cdi_build_lists(d, list_work);
+  if (s == CDI_OK) s = cdi_flow_build_links(d, rank_work);
   if (s == CDI_OK) chk(cudaStreamSynchronize(d->stream), "create domain");
+  if (s == CDI_OK) {  // the work arrays are needed at create time only
+    cdi_dev_release(d, rank_work);
+    cdi_dev_release(d, list_work);
+  }
   if (s != CDI_OK) {
     g_create_error = d->err;
     free_all(d);
@@ -381,6 +403,84 @@ cdi_status cdi_init_transport(cdi_domain *d, const cdi_species *sp, int n, doubl
   d->np_ready = false;
   cdi_status s = cdi_np_init(d, dt_s, dt_used);
   if (s == CDI_OK) d->np_ready = true;
+  return s;
+}
+
+cdi_status cdi_sweep_transport(cdi_domain *d, const cdi_combo *combos, int n_combos,
+                               const cdi_elec_params *ep, const cdi_species *sp, int n,
+                               double c0, double Ka, int64_t n_steps, double *gamma_out,
+                               double *cout_out, double *dt_out) {
+  if (!d || !combos || !ep || !sp || !gamma_out || !cout_out)
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (n_combos < 1 || n_combos > 4096)
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "1..4096 combinations");
+  if (n_steps < 0) return cdi_fail(d, CDI_ERR_INVALID_ARG, "n_steps < 0");
+  if (n < 1 || n > cdi::kMaxSpecies) return cdi_fail(d, CDI_ERR_INVALID_ARG, "1..4 species");
+  for (int k = 0; k < n; k++)
+    if (!(sp[k].D_m2s > 0) || !std::isfinite(sp[k].D_m2s) || sp[k].z < -8 || sp[k].z > 8)
+      return cdi_fail(d, CDI_ERR_INVALID_ARG, "species need D > 0 and |z| <= 8");
+  if (!(c0 >= 0) || !(Ka >= 0) || !std::isfinite(c0) || !std::isfinite(Ka))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "c0 and Ka must be finite and >= 0");
+  for (int m = 0; m < n_combos; m++)
+    if (!std::isfinite(combos[m].U_mps) || !std::isfinite(combos[m].applied_V))
+      return cdi_fail(d, CDI_ERR_INVALID_ARG, "non-finite combination");
+  if (!d->flow_done) return cdi_fail(d, CDI_ERR_STATE, "solve the flow first");
+  if (d->U_lat == 0.0) {
+    for (int m = 0; m < n_combos; m++)
+      if (combos[m].U_mps != 0.0)
+        return cdi_fail(d, CDI_ERR_INVALID_ARG, "no net flow through the pore space to scale");
+  }
+  // the sweep replaces the domain's potential and transport state
+  d->np_ready = false;
+  d->ns = n;
+  for (int k = 0; k < cdi::kMaxSpecies; k++) {
+    d->z[k] = k < n ? sp[k].z : 0;
+    d->D[k] = k < n ? sp[k].D_m2s : 1.0;
+  }
+  d->c0 = c0;
+  d->Ka = Ka;
+  // one potential per distinct applied value, each solved as by
+  // cdi_set_potential; each member's velocity scale and time step as by
+  // cdi_set_velocity and cdi_init_transport
+  std::vector<double> gv;
+  std::vector<int> group(n_combos);
+  std::vector<double> scale(n_combos), dts(n_combos);
+  std::vector<void *> phis;
+  cdi_status s = CDI_OK;
+  for (int m = 0; m < n_combos; m++) {
+    int g = -1;
+    for (size_t i = 0; i < gv.size(); i++)
+      if (gv[i] == combos[m].applied_V) g = (int)i;
+    if (g < 0) {
+      g = (int)gv.size();
+      gv.push_back(combos[m].applied_V);
+    }
+    group[m] = g;
+    scale[m] = combos[m].U_mps == 0.0 ? 0.0 : combos[m].U_mps / d->U_lat;
+  }
+  for (size_t g = 0; g < gv.size() && s == CDI_OK; g++) {
+    s = cdi_set_potential(d, gv[g], ep, nullptr, nullptr);
+    if (s != CDI_OK) break;
+    void *ph = cdi_dev_alloc(d, (size_t)d->N * 8);
+    if (!ph) {
+      s = cdi_fail(d, CDI_ERR_OOM, "sweep: potential buffer");
+      break;
+    }
+    phis.push_back(ph);
+    cudaError_t e = cudaMemcpyAsync(ph, d->d_phi, (size_t)d->N * 8, cudaMemcpyDeviceToDevice,
+                                    d->stream);
+    if (e != cudaSuccess) s = cdi_cuda_fail(d, e, "sweep: potential copy");
+    for (int m = 0; m < n_combos && s == CDI_OK; m++)
+      if (group[m] == (int)g) s = cdi_np_dt(d, scale[m], &dts[m]);
+  }
+  if (s == CDI_OK)
+    s = cdi_np_sweep(d, n_combos, scale.data(), group.data(), phis.data(), dts.data(), n_steps,
+                     gamma_out, cout_out);
+  cudaStreamSynchronize(d->stream);
+  for (void *p : phis) cdi_dev_release(d, p);
+  d->psi_done = false;  // the domain's potential is the last group's
+  if (s == CDI_OK && dt_out)
+    for (int m = 0; m < n_combos; m++) dt_out[m] = dts[m];
   return s;
 }
 

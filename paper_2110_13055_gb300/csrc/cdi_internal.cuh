@@ -229,10 +229,11 @@ struct cdi_domain {
   void *d_fflags = nullptr;     // Nf flow flags
   cdi::NFlag *d_nflags = nullptr;  // N face flags
   int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
+  int *d_nbr = nullptr;         // (Q-1)*n_flow_pore neighbour ranks (-1: solid)
   long long n_flow_pore = 0;
   int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending
-  void *d_g = nullptr;          // Q*Nf populations (shifted), precision T
-  float *d_glo = nullptr;       // Q*Nf low parts of the populations (pair storage)
+  void *d_g = nullptr;          // Q*n_flow_pore populations (shifted) by pore rank
+  float *d_glo = nullptr;       // their low parts (pair storage only)
   double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64
   void *d_u = nullptr;          // dim*N scaled velocity, precision T
   double *d_psi = nullptr;      // N potential (V), FP64
@@ -316,6 +317,7 @@ cudaError_t cdi_timing_resolve(cdi_domain *d);
 // Kernel-side entry points used by the API layer.
 cdi_status cdi_flow_build_flags(cdi_domain *d);
 size_t cdi_lists_work_ints(long long n);
+cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work);
 cdi_status cdi_build_lists(cdi_domain *d, int *work);
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
                         double *res);
@@ -325,6 +327,12 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol,
                          int max_iter, int *iters, double *relres);
 cdi_status cdi_np_build_flags(cdi_domain *d);
 cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used);
+cdi_status cdi_np_dt(cdi_domain *d, double scale, double *dt_out);
+cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *group,
+                        void *const *phi_groups, const double *dts, int64_t n_steps,
+                        double *gamma, double *cout);
+cdi_status cdi_flow_scale_to(cdi_domain *d, double scale, void *dst);
+void cdi_dev_release(cdi_domain *d, void *p);
 cdi_status cdi_np_steps(cdi_domain *d, int64_t n);
 cdi_status cdi_np_reduce(cdi_domain *d);
 cdi_status cdi_np_column_means(cdi_domain *d, int species);

@@ -124,60 +124,83 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
   fl[((size_t)z * ny + y) * NX + x] = (typename FlowFlag<DIM>::type)f;
 }
 
-// Slot read by direction i at this site (ODD: the upstream neighbour's
-// opposite slot, or the own slot after a bounce-back), and slot written by the
-// post-collision value of direction i.
+// Populations are stored compactly by pore rank k (the position of the site
+// in the ascending pore-site list): g[i * n + k].  The neighbour table
+// nbr[(i - 1) * n + k] holds the rank of the site x_k + e_i, or -1 when that
+// site is solid or lies beyond a lateral wall (halfway bounce-back).
+//
+// Slot read by direction i at rank k (ODD: the upstream neighbour's opposite
+// slot, or the own slot after a bounce-back), and slot written by the
+// post-collision value of direction i.  nb[j] caches nbr for direction j.
 template <int DIM, bool ODD>
-__device__ __forceinline__ int read_slot(const SiteIdx<DIM> &ix, unsigned f, int i, long long Nf,
-                                         size_t &base) {
+__device__ __forceinline__ size_t read_slot(const int *nb, int k, int i, long long n) {
   using L = Lat<DIM>;
-  if (!ODD) {
-    base = (size_t)i * Nf;
-    return ix.s;
-  }
-  const int o = L::opp(i);
-  if ((f >> o) & 1u) {  // the upstream site is solid: take the bounced value
-    base = (size_t)i * Nf;
-    return ix.s;
-  }
-  base = (size_t)o * Nf;
-  return ix.nb(-L::ex(i), -L::ey(i), -L::ez(i));
+  if (!ODD || i == 0) return (size_t)i * n + k;
+  const int src = nb[L::opp(i)];  // the site x - e_i
+  if (src < 0) return (size_t)i * n + k;  // upstream solid: the bounced value
+  return (size_t)L::opp(i) * n + src;
 }
 template <int DIM, bool ODD>
-__device__ __forceinline__ int write_slot(const SiteIdx<DIM> &ix, unsigned f, int i, long long Nf,
-                                          size_t &base) {
+__device__ __forceinline__ size_t write_slot(const int *nb, int k, int i, long long n) {
   using L = Lat<DIM>;
-  if (!ODD || ((f >> i) & 1u)) {  // local write, or bounce back from a solid
-    base = (size_t)L::opp(i) * Nf;
-    return ix.s;
+  if (!ODD || i == 0) return (size_t)L::opp(i) * n + k;
+  const int dst = nb[i];  // the site x + e_i
+  if (dst < 0) return (size_t)L::opp(i) * n + k;  // bounce back from a solid
+  return (size_t)i * n + dst;
+}
+
+// Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
+template <int DIM, bool ODD>
+__device__ __forceinline__ void load_links(const int *__restrict__ nbr, int k, long long n,
+                                           int (&nb)[Lat<DIM>::Q]) {
+  nb[0] = k;
+  if (ODD) {
+#pragma unroll
+    for (int i = 1; i < Lat<DIM>::Q; i++) nb[i] = nbr[(size_t)(i - 1) * n + k];
   }
-  base = (size_t)i * Nf;
-  return ix.nb(L::ex(i), L::ey(i), L::ez(i));
+}
+
+__global__ void k_rank_scatter(const int *__restrict__ list, int n, int *__restrict__ rank) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    rank[list[k]] = k;
+}
+
+template <int DIM>
+__global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
+                        const int *__restrict__ list, int n, const int *__restrict__ rank,
+                        int *__restrict__ nbr, int NX, int ny, int nz) {
+  using L = Lat<DIM>;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int s = list[k];
+    const unsigned f = fl[s];
+    const SiteIdx<DIM> ix(s, f, NX, ny, nz);
+#pragma unroll
+    for (int i = 1; i < L::Q; i++)
+      nbr[(size_t)(i - 1) * n + k] =
+          ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
+  }
 }
 
 // One full lattice Boltzmann step (stream + collide) at every pore site,
 // FP64 or FP32 storage.  Collision (Eq. 8) with the Stokes-linear
 // equilibrium g_eq_i = w_i (drho + 3 e_i.j), j = sum e_i g_i + F/2, and the
 // force source (1 - 1/(2 tau)) 3 w_i e_i.F; omega = 1/tau.
+// (more resident blocks per SM: the step is latency-bound on its scattered
+// loads, so occupancy matters more than a few spare registers; the bound is
+// chosen per variant so that nothing spills)
 template <typename T, int DIM, bool ODD>
-__global__ void __launch_bounds__(kRowBlock)
-    k_lbm_step(T *__restrict__ g, const typename FlowFlag<DIM>::type *__restrict__ fl,
-               const int *__restrict__ sites, int n_sites, int NX, int ny, int nz,
-               long long Nf, T omega, T fx_half, T fsrc) {
+__global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(T) == 4 ? 7 : 4))
+    k_lbm_step(T *__restrict__ g, const int *__restrict__ nbr, int n, T omega, T fx_half,
+               T fsrc) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n_sites) return;
-  const int site = sites[k0];
-  const unsigned f = fl[site];
-  const SiteIdx<DIM> ix(site, f, NX, ny, nz);
+  if (k0 >= n) return;
+  int nb[Q];
+  load_links<DIM, ODD>(nbr, k0, n, nb);
   T gi[Q];
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
-    size_t base;
-    const int k = read_slot<DIM, ODD>(ix, f, i, Nf, base);
-    gi[i] = g[base + k];
-  }
+  for (int i = 0; i < Q; i++) gi[i] = g[read_slot<DIM, ODD>(nb, k0, i, n)];
   T drho = T(0), jx = fx_half, jy = T(0), jz = T(0);
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -207,16 +230,13 @@ __global__ void __launch_bounds__(kRowBlock)
     go[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
   }
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
-    size_t base;
-    const int k = write_slot<DIM, ODD>(ix, f, i, Nf, base);
-    g[base + k] = go[i];
-  }
+  for (int i = 0; i < Q; i++) g[write_slot<DIM, ODD>(nb, k0, i, n)] = go[i];
 }
 
 // Constants of the pair collision, each an unevaluated FP32 pair.
 struct SplitConst {
   F2 omega;     // 1 / tau
+  F2 one_minus_omega;
   F2 fx_half;   // F / 2
   F2 src_axis;  // (1 - 1/(2 tau)) 3 F w_axis
   F2 src_diag;  // (1 - 1/(2 tau)) 3 F w_diag
@@ -224,12 +244,10 @@ struct SplitConst {
 
 // The same step with every population stored as an FP32 pair gh + gl and the
 // collision carried out in pair arithmetic.
-template <int DIM, bool ODD>
+template <int DIM, bool ODD, bool TAU1>
 __global__ void __launch_bounds__(kRowBlock)
     k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
-                     const typename FlowFlag<DIM>::type *__restrict__ fl,
-                     const int *__restrict__ sites, int n_sites, int NX, int ny, int nz,
-                     long long Nf, SplitConst c) {
+                     const int *__restrict__ nbr, int n, SplitConst c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   // lattice weights as FP32 pairs: rest, axis, diagonal
@@ -238,16 +256,14 @@ __global__ void __launch_bounds__(kRowBlock)
   constexpr F2 kWA = {(float)wa, (float)(wa - (double)(float)wa)};
   constexpr F2 kWD = {(float)wd, (float)(wd - (double)(float)wd)};
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n_sites) return;
-  const int site = sites[k0];
-  const unsigned f = fl[site];
-  const SiteIdx<DIM> ix(site, f, NX, ny, nz);
+  if (k0 >= n) return;
+  int nb[Q];
+  load_links<DIM, ODD>(nbr, k0, n, nb);
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    size_t base;
-    const int k = read_slot<DIM, ODD>(ix, f, i, Nf, base);
-    gi[i] = {gh[base + k], gl[base + k]};
+    const size_t a = read_slot<DIM, ODD>(nb, k0, i, n);
+    gi[i] = {gh[a], gl[a]};
   }
   // moments as pairs: exact sums of the high parts plus the low parts
   float rs = 0.f, rc = 0.f, xs = 0.f, xc = 0.f, ys = 0.f, yc = 0.f, zs = 0.f, zc = 0.f;
@@ -272,27 +288,35 @@ __global__ void __launch_bounds__(kRowBlock)
   const F2 jx = f2_add(fast_two_sum(xs, xc), c.fx_half);
   const F2 jy = fast_two_sum(ys, yc);
   const F2 jz = fast_two_sum(zs, zc);
+  // Equilibrium by weight class: g_eq_i = w drho + sum_a e_ia (3 w j_a), with
+  // w drho and 3 w j_a formed once per class (rest, axis, diagonal), each
+  // scaled by omega unless TAU1 (tau = 1: the collision is g* = g_eq + source).
+  const F2 om = TAU1 ? F2{1.f, 0.f} : c.omega;
+  const F2 wA3 = f2_mul(om, f2_add(kWA, f2_add(kWA, kWA)));
+  const F2 wD3 = f2_mul(om, f2_add(kWD, f2_add(kWD, kWD)));
+  const F2 r0 = f2_mul(f2_mul(om, kW0), drho);
+  const F2 rA = f2_mul(f2_mul(om, kWA), drho);
+  const F2 rD = f2_mul(f2_mul(om, kWD), drho);
+  const F2 jA[3] = {f2_mul(wA3, jx), f2_mul(wA3, jy), f2_mul(wA3, jz)};
+  const F2 jD[3] = {f2_mul(wD3, jx), f2_mul(wD3, jy), f2_mul(wD3, jz)};
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    // e_i . j (components are 0 or +-1)
-    F2 eu = {0.f, 0.f};
-    if (L::ex(i)) eu = f2_add(eu, L::ex(i) > 0 ? jx : f2_neg(jx));
-    if (L::ey(i)) eu = f2_add(eu, L::ey(i) > 0 ? jy : f2_neg(jy));
-    if (DIM == 3 && L::ez(i)) eu = f2_add(eu, L::ez(i) > 0 ? jz : f2_neg(jz));
-    const F2 eu3 = f2_add(eu, {2.f * eu.h, 2.f * eu.l});
-    const F2 w = i == 0 ? kW0 : ((L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) +
-                                  L::ez(i) * L::ez(i)) == 1 ? kWA : kWD);
-    const F2 geq = f2_mul(w, f2_add(drho, eu3));
-    F2 go = f2_add(gi[i], f2_mul(c.omega, f2_add(geq, f2_neg(gi[i]))));
+    const int n2 = L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i);
+    const F2 *jw = n2 == 1 ? jA : jD;
+    F2 geq = i == 0 ? r0 : (n2 == 1 ? rA : rD);
+    if (L::ex(i)) geq = f2_add(geq, L::ex(i) > 0 ? jw[0] : f2_neg(jw[0]));
+    if (L::ey(i)) geq = f2_add(geq, L::ey(i) > 0 ? jw[1] : f2_neg(jw[1]));
+    if (DIM == 3 && L::ez(i)) geq = f2_add(geq, L::ez(i) > 0 ? jw[2] : f2_neg(jw[2]));
+    // g* = g + omega (g_eq - g) = (1 - omega) g + [omega g_eq]
+    F2 go = TAU1 ? geq : f2_add(f2_mul(c.one_minus_omega, gi[i]), geq);
     if (L::ex(i)) {
       const bool axis = (L::ey(i) == 0 && L::ez(i) == 0);
       const F2 sv = axis ? c.src_axis : c.src_diag;
       go = f2_add(go, L::ex(i) > 0 ? sv : f2_neg(sv));
     }
-    size_t base;
-    const int k = write_slot<DIM, ODD>(ix, f, i, Nf, base);
-    gh[base + k] = go.h;
-    gl[base + k] = go.l;
+    const size_t a = write_slot<DIM, ODD>(nb, k0, i, n);
+    gh[a] = go.h;
+    gl[a] = go.l;
   }
 }
 
@@ -303,15 +327,14 @@ __global__ void __launch_bounds__(kRowBlock)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kRedThreads)
     k_flow_velocity(const T *__restrict__ g, const float *__restrict__ glo,
-                    const typename FlowFlag<DIM>::type *__restrict__ fl,
-                    double *__restrict__ uflow, long long Nf, double fx_half,
-                    double *__restrict__ part, unsigned int *counter, double *scal) {
+                    const int *__restrict__ list, int n, double *__restrict__ uflow,
+                    long long Nf, double fx_half, double *__restrict__ part,
+                    unsigned int *counter, double *scal) {
   using L = Lat<DIM>;
   __shared__ double sm[2 * 32];
   double v[2] = {0.0, 0.0};
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < Nf;
-       s += (long long)gridDim.x * blockDim.x) {
-    if (fl[s] & 1u) continue;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const long long s = list[k];  // populations by rank k, velocity by site s
     double j[3] = {fx_half, 0.0, 0.0};
     if (sizeof(T) == 4) {
       // exact sums of the FP32 values as (sum, error) pairs: the residual
@@ -320,8 +343,8 @@ __global__ void __launch_bounds__(kRedThreads)
       float ms[3] = {0.f, 0.f, 0.f}, mc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 1; i < L::Q; i++) {
-        const float gv = (float)g[(size_t)i * Nf + s];
-        const float lv = glo ? glo[(size_t)i * Nf + s] : 0.f;
+        const float gv = (float)g[(size_t)i * n + k];
+        const float lv = glo ? glo[(size_t)i * n + k] : 0.f;
         if (L::ex(i)) {
           two_sum_acc(L::ex(i) > 0 ? gv : -gv, ms[0], mc[0]);
           mc[0] = __fadd_rn(mc[0], L::ex(i) > 0 ? lv : -lv);
@@ -340,7 +363,7 @@ __global__ void __launch_bounds__(kRedThreads)
     } else {
 #pragma unroll
       for (int i = 0; i < L::Q; i++) {
-        const double gv = (double)g[(size_t)i * Nf + s];
+        const double gv = (double)g[(size_t)i * n + k];
         j[0] += L::ex(i) * gv;
         j[1] += L::ey(i) * gv;
         if (DIM == 3) j[2] += L::ez(i) * gv;
@@ -398,12 +421,13 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// u_phys = scale * u_lattice on the transport grid (0 in solid cells).
+// u_phys = scale * u_lattice on the transport grid (0 in solid cells); the
+// scale is scal[S_SCALE], or sc_arg when scal is null.
 template <typename T, int DIM>
 __global__ void k_flow_scale(const double *__restrict__ uflow, const uint8_t *__restrict__ mask,
                              T *__restrict__ u, int nx, int NX, long long N, long long Nf,
-                             const double *__restrict__ scal) {
-  const double sc = scal[S_SCALE];
+                             const double *__restrict__ scal, double sc_arg) {
+  const double sc = scal ? scal[S_SCALE] : sc_arg;
   for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
        P += (long long)gridDim.x * blockDim.x) {
     const long long row = P / nx;
@@ -421,38 +445,44 @@ template <> struct ModeT<M_F64> { using T = double; };
 
 template <int M, int DIM>
 void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
-  using FT = typename FlowFlag<DIM>::type;
   using T = typename ModeT<M>::T;
-  // one thread per pore site of the flow grid
+  // one thread per pore site of the flow grid (pore rank)
   const int n = (int)d->n_flow_pore;
   const int grid = (n + kRowBlock - 1) / kRowBlock;
-  const FT *fl = (const FT *)d->d_fflags;
+  const int *nbr = d->d_nbr;
   if (M == M_SPLIT) {
     const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
-    const SplitConst c{host_pair(1.0 / tau), host_pair(0.5 * force),
+    const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
                        host_pair(fs * Lat<DIM>::w(1)),
                        host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
-    k_lbm_step_split<DIM, false><<<grid, kRowBlock, 0, st>>>(
-        (float *)d->d_g, d->d_glo, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, c);
-    k_lbm_step_split<DIM, true><<<grid, kRowBlock, 0, st>>>(
-        (float *)d->d_g, d->d_glo, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, c);
+    if (tau == 1.0) {
+      k_lbm_step_split<DIM, false, true><<<grid, kRowBlock, 0, st>>>(
+          (float *)d->d_g, d->d_glo, nbr, n, c);
+      k_lbm_step_split<DIM, true, true><<<grid, kRowBlock, 0, st>>>(
+          (float *)d->d_g, d->d_glo, nbr, n, c);
+    } else {
+      k_lbm_step_split<DIM, false, false><<<grid, kRowBlock, 0, st>>>(
+          (float *)d->d_g, d->d_glo, nbr, n, c);
+      k_lbm_step_split<DIM, true, false><<<grid, kRowBlock, 0, st>>>(
+          (float *)d->d_g, d->d_glo, nbr, n, c);
+    }
   } else {
     const T omega = T(1.0 / tau), fxh = T(0.5 * force);
     const T fsrc = T((1.0 - 0.5 / tau) * 3.0 * force);
-    k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>(
-        (T *)d->d_g, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
-    k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>(
-        (T *)d->d_g, fl, d->d_flow_list, n, d->NX, d->ny, d->nz, d->Nf, omega, fxh, fsrc);
+    k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>((T *)d->d_g, nbr, n, omega, fxh,
+                                                           fsrc);
+    k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>((T *)d->d_g, nbr, n, omega, fxh,
+                                                          fsrc);
   }
 }
 
 template <int M, int DIM>
 cdi_status launch_velocity(cdi_domain *d) {
-  using FT = typename FlowFlag<DIM>::type;
   using T = typename ModeT<M>::T;
   k_flow_velocity<T, DIM><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-      (const T *)d->d_g, M == M_SPLIT ? d->d_glo : nullptr, (const FT *)d->d_fflags,
-      d->d_uflow, d->Nf, 0.5 * d->force, d->d_part, d->d_counter + C_RES, d->d_scal);
+      (const T *)d->d_g, M == M_SPLIT ? d->d_glo : nullptr, d->d_flow_list,
+      (int)d->n_flow_pore, d->d_uflow, d->Nf, 0.5 * d->force, d->d_part, d->d_counter + C_RES,
+      d->d_scal);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "velocity kernel");
   return CDI_OK;
@@ -467,10 +497,10 @@ cdi_status flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
   d->force = p->force_lu;
   const int Q = Lat<DIM>::Q;
   // start from rest: g = 0 (f = w), u_prev = u(0)
-  CDI_TRY(d, cudaMemsetAsync(d->d_g, 0, (size_t)Q * d->Nf * sizeof(T), d->stream), "reset g");
+  const size_t nq = (size_t)Q * d->n_flow_pore;
+  CDI_TRY(d, cudaMemsetAsync(d->d_g, 0, nq * sizeof(T), d->stream), "reset g");
   if (M == M_SPLIT)
-    CDI_TRY(d, cudaMemsetAsync(d->d_glo, 0, (size_t)Q * d->Nf * sizeof(float), d->stream),
-            "reset g low parts");
+    CDI_TRY(d, cudaMemsetAsync(d->d_glo, 0, nq * sizeof(float), d->stream), "reset g low parts");
   cdi_status s = launch_velocity<M, DIM>(d);
   if (s != CDI_OK) return s;
   // K steps captured once as a graph (parameters are baked in)
@@ -531,7 +561,7 @@ cdi_status flow_export(cdi_domain *d, double U_target) {
       d->d_uflow, d->d_mask, d->nx, d->NX, d->N, (double)d->n_pore, U_target, d->d_part,
       d->d_counter + C_ULAT, d->d_scal);
   k_flow_scale<T, DIM><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-      d->d_uflow, d->d_mask, (T *)d->d_u, d->nx, d->NX, d->N, d->Nf, d->d_scal);
+      d->d_uflow, d->d_mask, (T *)d->d_u, d->nx, d->NX, d->N, d->Nf, d->d_scal, 0.0);
   d->timing.kernel_launches += 2;
   CDI_TRY(d, cudaGetLastError(), "velocity export");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_ULAT, d->d_scal + S_ULAT, 2 * sizeof(double),
@@ -562,6 +592,27 @@ cdi_status cdi_flow_build_flags(cdi_domain *d) {
   return d->dim == 2 ? build_flags<2>(d) : build_flags<3>(d);
 }
 
+// Neighbour-rank table of the compact population layout (after the pore
+// lists): rank[site] scattered from the list (rank_work: Nf ints, -1 for
+// solid), then nbr[(i-1) n + k] for every pore rank k and direction i.
+cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work) {
+  const int n = (int)d->n_flow_pore;
+  CDI_TRY(d, cudaMemsetAsync(rank_work, 0xff, (size_t)d->Nf * sizeof(int), d->stream),
+          "rank reset");
+  k_rank_scatter<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_flow_list, n, rank_work);
+  if (d->dim == 2)
+    k_links<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
+        d->ny, d->nz);
+  else
+    k_links<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
+        d->ny, d->nz);
+  d->timing.kernel_launches += 2;
+  CDI_TRY(d, cudaGetLastError(), "neighbour table");
+  return CDI_OK;
+}
+
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps, double *res) {
   switch (d->prec) {
     case CDI_FP64:
@@ -572,6 +623,27 @@ cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
       return d->dim == 2 ? flow_run<M_SPLIT, 2>(d, p, steps, res)
                          : flow_run<M_SPLIT, 3>(d, p, steps, res);
   }
+}
+
+cdi_status cdi_flow_scale_to(cdi_domain *d, double scale, void *dst) {
+  if (d->prec == CDI_FP64) {
+    if (d->dim == 2)
+      k_flow_scale<double, 2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+          d->d_uflow, d->d_mask, (double *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+    else
+      k_flow_scale<double, 3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+          d->d_uflow, d->d_mask, (double *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+  } else {
+    if (d->dim == 2)
+      k_flow_scale<float, 2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+          d->d_uflow, d->d_mask, (float *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+    else
+      k_flow_scale<float, 3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+          d->d_uflow, d->d_mask, (float *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+  }
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "velocity scale");
+  return CDI_OK;
 }
 
 cdi_status cdi_flow_export(cdi_domain *d, double U_target) {

@@ -115,49 +115,50 @@ template <> struct FaceB<float> {
     lo = __fadd_rn(e, __fsub_rn(nb.y, p.y));
   }
   __device__ static void eval(float adv, float z, float dhi, float dlo, float &Bp, float &Bm) {
-    // P = adv - z (dhi + dlo) as ph + pl
-    const float zd = __fmul_rn(z, dhi);
-    const float zde = __fmaf_rn(z, dhi, -zd);
-    const float ph = __fsub_rn(adv, zd);
-    const float bb = __fsub_rn(ph, adv);
-    const float phe = __fadd_rn(__fsub_rn(adv, __fsub_rn(ph, bb)), __fsub_rn(-zd, bb));
-    const float pl = __fsub_rn(__fsub_rn(phe, zde), __fmul_rn(z, dlo));
-    const bool neg = ph < 0.f;
-    const float ah = neg ? -ph : ph, al = neg ? -pl : pl;
-    float Ba;
-    if (ah < 1e-3f) {
-      const float a2 = ah * ah;
-      Ba = 1.f - ah * 0.5f + a2 * (1.f / 12.f) - a2 * a2 * (1.f / 720.f);
+    const float p = __fmaf_rn(-z, dhi, adv);
+    const bool neg = p < 0.f;
+    float Ba, Bma;
+    if (fabsf(p) < 0.5f) {
+      // Almost every face: B(a) from its Taylor series (Bernoulli numbers)
+      // through a^8, truncation below 3e-11 for a < 1/2.  Dropping the low
+      // part of P shifts B by less than 4e-8 relative here.
+      const float a = fabsf(p), a2 = a * a;
+      float t = __fmaf_rn(-1.f / 1209600.f, a2, 1.f / 30240.f);
+      t = __fmaf_rn(t, a2, -1.f / 720.f);
+      t = __fmaf_rn(t, a2, 1.f / 12.f);
+      Ba = __fmaf_rn(t, a2, __fmaf_rn(-0.5f, a, 1.f));
+      Bma = Ba + a;
     } else {
-      Ba = ah / expm1f(ah);
+      // P = adv - z (dhi + dlo) as ph + pl, B at |ph| corrected for pl
+      const float zd = __fmul_rn(z, dhi);
+      const float zde = __fmaf_rn(z, dhi, -zd);
+      const float ph = __fsub_rn(adv, zd);
+      const float bb = __fsub_rn(ph, adv);
+      const float phe = __fadd_rn(__fsub_rn(adv, __fsub_rn(ph, bb)), __fsub_rn(-zd, bb));
+      const float pl = __fsub_rn(__fsub_rn(phe, zde), __fmul_rn(z, dlo));
+      const float ah = neg ? -ph : ph, al = neg ? -pl : pl;
+      // B(a) = a e^-a / (1 - e^-a) is below 1e-33 beyond a = 80
+      Ba = ah > 80.f ? 0.f : __fdividef(ah, expm1f(ah));
+      Ba = __fmaf_rn(Ba * al, __fdividef(1.f - Ba, ah) - 1.f, Ba);
+      Bma = (Ba + ah) + al;  // B(-a) = B(a) + a, no cancellation
     }
-    if (ah > 0.f) Ba = __fmaf_rn(Ba * al, (1.f - Ba) / ah - 1.f, Ba);
-    const float Bma = (Ba + ah) + al;  // B(-a) = B(a) + a, no cancellation
     Bp = neg ? Bma : Ba;
     Bm = neg ? Ba : Bma;
   }
 };
 
+// One explicit step of one pore cell P for NS species: writes the new
+// concentrations and adds the cell's adsorbed (v[k]), inflow (v[NS+k]) and
+// outflow (v[2NS+k]) fluxes.
 template <typename T, int DIM, int NS>
-__global__ void __launch_bounds__(kRowBlock)
-    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
-              const typename PhiStore<T>::type *__restrict__ phi,
-              const NFlag *__restrict__ fl, const int *__restrict__ cells, int n_cells,
-              NPConst<T> c, double *__restrict__ acc, int nx, int ny, int nz, long long N,
-              int walls) {
+__device__ __forceinline__ void np_cell(const T *__restrict__ Cin, T *__restrict__ Cout,
+                                        const T *__restrict__ u,
+                                        const typename PhiStore<T>::type *__restrict__ phi,
+                                        unsigned f, const NPConst<T> &c, int nx, int ny, int nz,
+                                        long long N, int walls, long long P, T (&v)[3 * NS]) {
   using PS = PhiStore<T>;
   using PT = typename PS::type;
-  // per-step block sums of the adsorbed / inflow / outflow fluxes in T; each
-  // block adds them to its own FP64 account (one thread per pore cell, so
-  // the block -> cells map is fixed and the totals are deterministic)
-  __shared__ T sm[3 * NS * 32];
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  T v[3 * NS];
-#pragma unroll
-  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-  if (k0 < n_cells) {
-    const long long P = cells[k0];
-    const unsigned f = fl[P];
+  {
     {
       T CP[NS], sumJ[NS];
 #pragma unroll
@@ -220,16 +221,77 @@ __global__ void __launch_bounds__(kRowBlock)
       for (int k = 0; k < NS; k++) Cout[(size_t)k * N + P] = CP[k] - c.dtdx * sumJ[k];
     }
   }
+}
+
+// Block sums of v in T, added by thread 0 to the block's own FP64 accounts
+// acc[(3*k + kind) * gridDim.x + block], kind 0 Gamma, 1 In, 2 Out (one
+// thread per pore cell, so the block -> cells map is fixed and the totals are
+// deterministic).  Every thread of the block must call it.
+template <typename T, int NS>
+__device__ __forceinline__ void np_account(T (&v)[3 * NS], T *sm, double *__restrict__ acc) {
   block_reduce<3 * NS>(v, sm, OpSum(), T(0));
   if (threadIdx.x == 0) {
     const int bid = blockIdx.x, nblocks = gridDim.x;
-    // accumulator layout: [(3*k + kind) * nblocks + block], kind 0 Gamma, 1 In, 2 Out
 #pragma unroll
     for (int k = 0; k < NS; k++) {
       acc[(size_t)(3 * k + 0) * nblocks + bid] += (double)v[k];
       acc[(size_t)(3 * k + 1) * nblocks + bid] += (double)v[NS + k];
       acc[(size_t)(3 * k + 2) * nblocks + bid] += (double)v[2 * NS + k];
     }
+  }
+}
+
+template <typename T, int DIM, int NS>
+__global__ void __launch_bounds__(kRowBlock)
+    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
+              const typename PhiStore<T>::type *__restrict__ phi,
+              const NFlag *__restrict__ fl, const int *__restrict__ cells, int n_cells,
+              NPConst<T> c, double *__restrict__ acc, int nx, int ny, int nz, long long N,
+              int walls) {
+  __shared__ T sm[3 * NS * 32];
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  T v[3 * NS];
+#pragma unroll
+  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+  if (k0 < n_cells) {
+    const long long P = cells[k0];
+    np_cell<T, DIM, NS>(Cin, Cout, u, phi, fl[P], c, nx, ny, nz, N, walls, P, v);
+  }
+  np_account<T, NS>(v, sm, acc);
+}
+
+// One member of a fused sweep: its own concentrations, velocity, potential,
+// constants (time step) and accounts.
+template <typename T> struct SweepMember {
+  T *C[2];          // concentration buffers (ping-pong)
+  const T *u;
+  const typename PhiStore<T>::type *phi;
+  double *acc;
+  NPConst<T> c;
+};
+
+// All members of a sweep advance one step in one launch: each block runs the
+// same cells for every member in turn (the block -> cells map, the arithmetic
+// and the accounts of a member are those of k_np_step, so a member's result
+// equals a single run's bit for bit).
+template <typename T, int DIM, int NS>
+__global__ void __launch_bounds__(kRowBlock)
+    k_np_sweep(const SweepMember<T> *__restrict__ members, int n_members, int in,
+               const NFlag *__restrict__ fl, const int *__restrict__ cells, int n_cells, int nx,
+               int ny, int nz, long long N, int walls) {
+  __shared__ T sm[3 * NS * 32];
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long P = k0 < n_cells ? cells[k0] : 0;
+  const unsigned f = k0 < n_cells ? fl[P] : 1u;
+  for (int m = 0; m < n_members; m++) {
+    const SweepMember<T> &mb = members[m];
+    T v[3 * NS];
+#pragma unroll
+    for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+    if (k0 < n_cells)
+      np_cell<T, DIM, NS>(mb.C[in], mb.C[1 - in], mb.u, mb.phi, f, mb.c, nx, ny, nz, N, walls,
+                          P, v);
+    np_account<T, NS>(v, sm, mb.acc);
   }
 }
 
@@ -455,8 +517,32 @@ cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
   d->np_graph = nullptr;
   double dt = dt_s;
   if (dt <= 0.0) {
+    cdi_status s = cdi_np_dt(d, d->h_scal[S_SCALE], &dt);
+    if (s != CDI_OK) return s;
+  }
+  d->dt = dt;
+  if (dt_used) *dt_used = dt;
+  if (d->prec == CDI_FP64)
+    k_np_init<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, (double *)d->d_C[0], (double *)d->d_C[1], d->N, d->ns, d->c0);
+  else
+    k_np_init<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, (float *)d->d_C[0], (float *)d->d_C[1], d->N, d->ns, (float)d->c0);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "transport init");
+  CDI_TRY(d, cudaMemsetAsync(d->d_acc, 0, (size_t)3 * kMaxSpecies * d->np_blocks * 8, d->stream),
+          "reset accumulators");
+  d->cur = 0;
+  d->np_steps = 0;
+  return CDI_OK;
+}
+
+// Explicit time step for the current potential (d_psi) and the solved flow
+// scaled by `scale` (the species set in the domain).
+cdi_status cdi_np_dt(cdi_domain *d, double scale, double *dt_out) {
+  double dt = 0.0;
+  {
     NPConst<double> c = make_const<double>(d);
-    const double scale = d->h_scal[S_SCALE];
     if (d->dim == 2)
       k_np_rate<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
           d->d_nflags, d->d_uflow, d->d_psi, c, d->ns, scale, 1.0 / d->VT, 1.0 / d->dx, 0.9,
@@ -477,21 +563,171 @@ cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
     if (!(dt > 0.0) || !std::isfinite(dt))
       return cdi_fail(d, CDI_ERR_INVALID_ARG, "no finite time step (no flux anywhere?)");
   }
-  d->dt = dt;
-  if (dt_used) *dt_used = dt;
-  if (d->prec == CDI_FP64)
-    k_np_init<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, (double *)d->d_C[0], (double *)d->d_C[1], d->N, d->ns, d->c0);
-  else
-    k_np_init<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, (float *)d->d_C[0], (float *)d->d_C[1], d->N, d->ns, (float)d->c0);
-  d->timing.kernel_launches++;
-  CDI_TRY(d, cudaGetLastError(), "transport init");
-  CDI_TRY(d, cudaMemsetAsync(d->d_acc, 0, (size_t)3 * kMaxSpecies * d->np_blocks * 8, d->stream),
-          "reset accumulators");
-  d->cur = 0;
-  d->np_steps = 0;
+  *dt_out = dt;
   return CDI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fused sweep: n members on one geometry, one launch per step for all.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T, int DIM>
+void launch_sweep_d(cdi_domain *d, cudaStream_t st, const void *members, int n, int in) {
+  const SweepMember<T> *m = (const SweepMember<T> *)members;
+  switch (d->ns) {
+    case 1:
+      k_np_sweep<T, DIM, 1><<<d->np_blocks, kRowBlock, 0, st>>>(
+          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
+          d->walls);
+      break;
+    case 2:
+      k_np_sweep<T, DIM, 2><<<d->np_blocks, kRowBlock, 0, st>>>(
+          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
+          d->walls);
+      break;
+    case 3:
+      k_np_sweep<T, DIM, 3><<<d->np_blocks, kRowBlock, 0, st>>>(
+          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
+          d->walls);
+      break;
+    default:
+      k_np_sweep<T, DIM, 4><<<d->np_blocks, kRowBlock, 0, st>>>(
+          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
+          d->walls);
+      break;
+  }
+}
+
+void launch_sweep(cdi_domain *d, cudaStream_t st, const void *members, int n, int in) {
+  if (d->prec == CDI_FP64) {
+    if (d->dim == 2) launch_sweep_d<double, 2>(d, st, members, n, in);
+    else launch_sweep_d<double, 3>(d, st, members, n, in);
+  } else {
+    if (d->dim == 2) launch_sweep_d<float, 2>(d, st, members, n, in);
+    else launch_sweep_d<float, 3>(d, st, members, n, in);
+  }
+}
+
+template <typename T>
+cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group,
+                     void *const *phi_groups, const double *dts, int64_t n_steps,
+                     double *gamma, double *cout) {
+  const size_t TN = (size_t)d->N * sizeof(T);
+  const int ns = d->ns;
+  // per-member device memory: velocity, two concentration buffers, accounts
+  std::vector<void *> blocks;
+  auto take = [&](size_t bytes) {
+    void *p = cdi_dev_alloc(d, bytes);
+    if (p) blocks.push_back(p);
+    return p;
+  };
+  std::vector<SweepMember<T>> hm(n);
+  bool ok = true;
+  for (int m = 0; m < n && ok; m++) {
+    void *u = take((size_t)d->dim * TN);
+    void *c0 = take((size_t)kMaxSpecies * TN), *c1 = take((size_t)kMaxSpecies * TN);
+    void *acc = take((size_t)3 * kMaxSpecies * d->np_blocks * 8);
+    ok = u && c0 && c1 && acc;
+    if (!ok) break;
+    d->dt = dts[m];
+    hm[m].C[0] = (T *)c0;
+    hm[m].C[1] = (T *)c1;
+    hm[m].u = (const T *)u;
+    hm[m].phi = (const typename PhiStore<T>::type *)phi_groups[group[m]];
+    hm[m].acc = (double *)acc;
+    hm[m].c = make_const<T>(d);
+  }
+  void *dmem = ok ? take(sizeof(SweepMember<T>) * n) : nullptr;
+  cdi_status s = CDI_OK;
+  if (!ok || !dmem) s = cdi_fail(d, CDI_ERR_OOM, "sweep: device allocation failed");
+  for (int m = 0; m < n && s == CDI_OK; m++) {
+    s = cdi_flow_scale_to(d, scale[m], (void *)hm[m].u);
+    if (s != CDI_OK) break;
+    k_np_init<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, hm[m].C[0], hm[m].C[1],
+                                                            d->N, ns, (T)d->c0);
+    d->timing.kernel_launches++;
+    if (cudaMemsetAsync(hm[m].acc, 0, (size_t)3 * kMaxSpecies * d->np_blocks * 8, d->stream) !=
+        cudaSuccess)
+      s = cdi_fail(d, CDI_ERR_CUDA, "sweep: memset");
+  }
+  if (s == CDI_OK &&
+      cudaMemcpyAsync(dmem, hm.data(), sizeof(SweepMember<T>) * n, cudaMemcpyHostToDevice,
+                      d->stream) != cudaSuccess)
+    s = cdi_fail(d, CDI_ERR_CUDA, "sweep: member table");
+  // steps: graphs of kGraphSteps fused launches (even, so the parity returns)
+  cudaGraphExec_t exec = nullptr;
+  int64_t done = 0;
+  if (s == CDI_OK) {
+    cudaEvent_t ev;
+    cdi_timing_begin(d, &ev);
+    if (n_steps >= kGraphSteps) {
+      cudaGraph_t graph;
+      cudaError_t e = cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int k = 0; k < kGraphSteps; k++) launch_sweep(d, d->cap_stream, dmem, n, k & 1);
+        e = cudaStreamEndCapture(d->cap_stream, &graph);
+      }
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+      }
+      if (e != cudaSuccess) s = cdi_cuda_fail(d, e, "sweep graph");
+      while (s == CDI_OK && n_steps - done >= kGraphSteps) {
+        e = cudaGraphLaunch(exec, d->stream);
+        if (e != cudaSuccess) s = cdi_cuda_fail(d, e, "sweep graph launch");
+        done += kGraphSteps;
+      }
+    }
+    for (; s == CDI_OK && done < n_steps; done++) launch_sweep(d, d->stream, dmem, n, (int)(done & 1));
+    cudaError_t e = cudaGetLastError();
+    if (s == CDI_OK && e != cudaSuccess) s = cdi_cuda_fail(d, e, "sweep step");
+    cdi_timing_end(d, ev, PH_NP, n_steps);
+    d->timing.kernel_launches += n_steps;
+  }
+  // outputs per member, through the same reductions as a single run
+  const int cur = (int)(n_steps & 1);
+  const double area = d->dim == 2 ? d->dx : d->dx * d->dx;
+  const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
+  for (int m = 0; m < n && s == CDI_OK; m++) {
+    k_np_sums<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_nflags, hm[m].C[cur], hm[m].u, d->N, d->nx, ns, vol, d->d_part,
+        d->d_counter + C_MASS, d->d_scal);
+    k_acc_total<<<1, kRedThreads, 0, d->stream>>>(hm[m].acc, d->np_blocks, d->d_scal);
+    d->timing.kernel_launches += 2;
+    cudaError_t e = cudaMemcpyAsync(d->h_scal + S_OUT, d->d_scal + S_OUT,
+                                    (S_OUTN - S_OUT + 1) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) {
+      s = cdi_cuda_fail(d, e, "sweep outputs");
+      break;
+    }
+    for (int k = 0; k < ns; k++) {
+      gamma[m * ns + k] = d->h_scal[S_ACC + 3 * k] * dts[m] * area;
+      const double num = d->h_scal[S_OUT + 2 * k], den = d->h_scal[S_OUT + 2 * k + 1];
+      const double cnt = d->h_scal[S_OUTN];
+      cout[m * ns + k] = den != 0.0 ? num / den : (cnt > 0 ? d->h_scal[S_OUTP + k] / cnt : 0.0);
+    }
+  }
+  if (s == CDI_OK) {
+    cudaError_t e = cdi_timing_resolve(d);
+    if (e != cudaSuccess) s = cdi_cuda_fail(d, e, "timing");
+  }
+  cudaStreamSynchronize(d->stream);
+  if (exec) cudaGraphExecDestroy(exec);
+  for (void *p : blocks) cdi_dev_release(d, p);
+  return s;
+}
+
+}  // namespace
+
+cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *group,
+                        void *const *phi_groups, const double *dts, int64_t n_steps,
+                        double *gamma, double *cout) {
+  if (d->prec == CDI_FP64)
+    return sweep_run<double>(d, n, scale, group, phi_groups, dts, n_steps, gamma, cout);
+  return sweep_run<float>(d, n, scale, group, phi_groups, dts, n_steps, gamma, cout);
 }
 
 cdi_status cdi_np_steps(cdi_domain *d, int64_t n) {

@@ -53,9 +53,10 @@ class PackInfo:
     sha256: str
 
 
-def _stamp(solid: np.ndarray, centre, r: float, periodic_axes) -> None:
+def _stamp(solid: np.ndarray, centre, r: float, periodic_axes) -> int:
     """Mark voxels whose centre lies within ``r`` of ``centre`` (axis order
-    matches ``solid.shape``; periodic wrap on the listed axes)."""
+    matches ``solid.shape``; periodic wrap on the listed axes).  Returns the
+    number of voxels that turned solid."""
     slices = []
     coords = []
     for ax, (c, n) in enumerate(zip(centre, solid.shape)):
@@ -74,10 +75,16 @@ def _stamp(solid: np.ndarray, centre, r: float, periodic_axes) -> None:
     hit = d2 <= r * r
     if solid.ndim == 2:
         ii, jj = np.nonzero(hit)
-        solid[slices[0][ii], slices[1][jj]] = 1
+        idx = (slices[0][ii], slices[1][jj])
     else:
         ii, jj, kk = np.nonzero(hit)
-        solid[slices[0][ii], slices[1][jj], slices[2][kk]] = 1
+        idx = (slices[0][ii], slices[1][jj], slices[2][kk])
+    # a box wider than a periodic axis visits a voxel twice: count each once
+    flat = np.unique(np.ravel_multi_index(idx, solid.shape))
+    view = solid.reshape(-1)
+    new = int(np.count_nonzero(view[flat] == 0))
+    view[flat] = 1
+    return new
 
 
 def _periodic_dist2(a, b, shape, periodic_axes) -> float:
@@ -124,8 +131,7 @@ def grain_pack(shape, porosity: float, r_min: float, r_max: float, seed: int,
                    for c, rc in placed):
                 continue
         placed.append((centre, r))
-        _stamp(solid, centre, r, periodic)
-        n_solid = int(solid.sum())
+        n_solid += _stamp(solid, centre, r, periodic)
     phi = 1.0 - n_solid / total
     return solid, PackInfo(phi, len(placed), mask_sha256(solid))
 

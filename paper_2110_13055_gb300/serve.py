@@ -1,0 +1,188 @@
+"""Continuous-batching solve server over the C ABI.
+
+Requests (one electrode image plus potential, velocity and step counts each)
+arrive at any time.  A request is admitted as soon as a slot is free and its
+device footprint fits into the remaining memory budget; admitted requests
+run concurrently, each on its own domain with its own CUDA stream, so their
+kernels overlap on the device while earlier ones are still running.  Fields
+stay resident in device memory for the whole solve; the domain (and its
+memory) is released when the request completes, which admits the next.
+
+Each request's result depends only on its own inputs: every kernel is
+deterministic and domains share no device state, so a request gives the same
+result alone and in the mix.
+
+``Server`` is host-side orchestration only; all numerical work runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import cdi
+
+
+@dataclass
+class Request:
+    mask: np.ndarray
+    applied_V: float
+    U_mps: float
+    np_steps: int
+    precision: int = cdi.FP32
+    flow_tol: float = 1e-8
+    max_flow_steps: int = 1_000_000
+    c0: float = 10.0
+    Ka: float = 1e-6
+    z: tuple = (1, -1)
+    D: tuple = (1.33e-9, 2.03e-9)
+    tag: object = None
+    # filled in by the server
+    t_arrival: float = 0.0
+    t_start: float = 0.0
+    t_done: float = 0.0
+    result: dict = field(default_factory=dict)
+    error: str = ""
+
+
+def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> int:
+    """Device memory a domain for this mask allocates (the allocations of
+    cdi_create_domain), plus one sweep-free transport state."""
+    dim = mask.ndim
+    N = int(mask.size)
+    n_pore = int((mask == 0).sum())
+    Nf = N * (2 if mirror else 1)
+    Q = 9 if dim == 2 else 19
+    T = 8 if precision == cdi.FP64 else 4
+    pop = Q * Nf * (8 if precision in (cdi.FP64, cdi.FP32_SPLIT) else 4)
+    fflag = Nf * (2 if dim == 2 else 4)
+    per_cell = (1 + 2 + dim * T + 8 + 8 + 2 * 4 * T + 4 * 8)   # mask, flags, u, psi, phi, C, CG
+    lists = 4 * (n_pore * (2 if mirror else 1) + n_pore)
+    return pop + fflag + dim * Nf * 8 + N * per_cell + lists + (4 << 20)
+
+
+class Server:
+    """Admits requests while slots and memory allow; runs them concurrently."""
+
+    def __init__(self, slots: int = 4, memory_budget: int = 16 << 30, device: int = 0,
+                 solver=None):
+        self.solver = solver or solve
+        self.slots = slots
+        self.budget = memory_budget
+        self.device = device
+        self.pending: queue.Queue = queue.Queue()
+        self.done: list = []
+        self._lock = threading.Condition()
+        self._in_use = 0
+        self._running = 0
+        self.max_running = 0
+        self.max_in_use = 0
+        self._admitter = threading.Thread(target=self._admit_loop, daemon=True)
+        self._admitter.start()
+
+    def submit(self, req: Request) -> None:
+        req.t_arrival = time.perf_counter()
+        self.pending.put(req)
+
+    def _admit_loop(self):
+        while True:
+            req = self.pending.get()
+            if req is None:
+                return
+            need = footprint_bytes(req.mask, req.precision)
+            with self._lock:
+                if need > self.budget:
+                    req.error = f"request needs {need} bytes, budget {self.budget}"
+                    req.t_done = time.perf_counter()
+                    self.done.append(req)
+                    self._lock.notify_all()
+                    continue
+                while self._running >= self.slots or self._in_use + need > self.budget:
+                    self._lock.wait()
+                self._running += 1
+                self._in_use += need
+                self.max_running = max(self.max_running, self._running)
+                self.max_in_use = max(self.max_in_use, self._in_use)
+            threading.Thread(target=self._run, args=(req, need), daemon=True).start()
+
+    def _run(self, req: Request, need: int):
+        req.t_start = time.perf_counter()
+        try:
+            req.result = self.solver(req)
+        except Exception as e:  # a failed request fails alone
+            req.error = str(e)
+        req.t_done = time.perf_counter()
+        with self._lock:
+            self._running -= 1
+            self._in_use -= need
+            self.done.append(req)
+            self._lock.notify_all()
+
+    def drain(self, n_expected: int, timeout: float = 3600.0) -> list:
+        """Wait until n_expected requests have completed; returns them."""
+        t_end = time.perf_counter() + timeout
+        with self._lock:
+            while len(self.done) < n_expected:
+                left = t_end - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError("requests still running")
+                self._lock.wait(timeout=left)
+            return list(self.done)
+
+    def close(self):
+        self.pending.put(None)
+        self._admitter.join(timeout=10)
+
+
+def solve(req: Request) -> dict:
+    """One request end to end through the C ABI (the plain single solve)."""
+    with cdi.Domain(req.mask, precision=req.precision) as d:
+        steps, res, st = d.solve_flow(tol=req.flow_tol, max_steps=req.max_flow_steps,
+                                      U_target=req.U_mps, allow_not_converged=True)
+        d.set_potential(req.applied_V, c_bulk=req.c0, tol=1e-12)
+        d.init_transport(req.z, req.D, c0=req.c0, Ka=req.Ka)
+        d.step(req.np_steps)
+        return {"Gamma": d.adsorbed(), "C_out": d.outlet(), "flow_steps": steps,
+                "flow_residual": res}
+
+
+def run_sequential(requests: list, arrivals: list) -> list:
+    """The plain loop: requests served one at a time in arrival order."""
+    t0 = time.perf_counter()
+    for req, ta in zip(requests, arrivals):
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        req.t_arrival = t0 + ta
+        req.t_start = time.perf_counter()
+        try:
+            req.result = solve(req)
+        except Exception as e:
+            req.error = str(e)
+        req.t_done = time.perf_counter()
+    return requests
+
+
+def run_served(requests: list, arrivals: list, slots: int, memory_budget: int) -> list:
+    """The same stream of requests through the continuous-batching server."""
+    srv = Server(slots=slots, memory_budget=memory_budget)
+    t0 = time.perf_counter()
+    for req, ta in zip(requests, arrivals):
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        srv.submit(req)
+    done = srv.drain(len(requests))
+    srv.close()
+    return done
+
+
+def latency_stats(reqs: list) -> dict:
+    lat = np.array([r.t_done - r.t_arrival for r in reqs if not r.error])
+    span = max(r.t_done for r in reqs) - min(r.t_arrival for r in reqs)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "solves_per_s": len(lat) / span, "failed": sum(1 for r in reqs if r.error)}

@@ -68,11 +68,14 @@ CASES = {
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("mirror,walls", [(True, False), (False, True)])
-def test_flow_fixed_steps_fp64(case, mirror, walls):
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32_SPLIT])
+def test_flow_fixed_steps(case, mirror, walls, prec):
+    """tau = 0.9 exercises the general collision (the pair kernel has a
+    separate tau = 1 path); pair storage must match like FP64."""
     m = CASES[case]()
     ref, *_ = O.lbm(m, mirror=mirror, lateral_walls=walls, tau=0.9, force=2e-6, tol=0.0,
                     check_every=100, max_steps=1200)
-    with cdi.Domain(m, precision=cdi.FP64, mirror=mirror, lateral_walls=walls) as d:
+    with cdi.Domain(m, precision=prec, mirror=mirror, lateral_walls=walls) as d:
         steps, res, _ = d.solve_flow(tau=0.9, force=2e-6, tol=0.0, check_every=100,
                                      max_steps=1200, U_target=0.0)
         u = d.u_lattice()

@@ -1,0 +1,76 @@
+"""Batched transport sweep (cdi_sweep_transport): every member of a fused
+sweep gives the single run's result bit for bit, and a member agrees with
+the oracle at the parity tolerances."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_13055_gb300 import cdi, inputs
+
+pytestmark = pytest.mark.gpu
+
+Z, D = (1, -1), (1.33e-9, 2.03e-9)
+COMBOS = [(1e-4, 1.0), (3e-4, 1.0), (1e-4, 0.6), (0.0, 0.2), (1e-3, 0.6)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def single_runs(d, combos, lam, c0, Ka, n_steps):
+    gam, cout, dts = [], [], []
+    for U, V in combos:
+        d.set_velocity(U)
+        d.set_potential(V, c_bulk=c0, lambda_D=lam, tol=1e-12)
+        dts.append(d.init_transport(Z, D, c0=c0, Ka=Ka))
+        d.step(n_steps)
+        gam.append(d.adsorbed())
+        cout.append(d.outlet())
+    return np.array(gam), np.array(cout), np.array(dts)
+
+
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("shape", [(23, 37), (9, 11, 17)])
+def test_sweep_members_equal_single_runs(prec, shape):
+    m, _ = inputs.grain_pack(shape, 0.6, 1.5, 4.0, seed=21)
+    lam, c0, Ka, n = 1.5e-7, 10.0, 1e-6, 131   # 131 = 2 graphs of 64 + 3 single steps
+    with cdi.Domain(m, precision=prec) as d:
+        d.solve_flow(tol=0.0, max_steps=600, U_target=1e-4)
+        g_sw, c_sw, dt_sw = d.sweep(COMBOS, lambda_D=lam, c0=c0, Ka=Ka, n_steps=n)
+        with pytest.raises(cdi.CDIError) as e:   # the sweep leaves no transport state
+            d.step(1)
+        assert e.value.status == 6
+        g1, c1, dt1 = single_runs(d, COMBOS, lam, c0, Ka, n)
+    assert np.array_equal(dt_sw, dt1)
+    assert np.array_equal(g_sw, g1)
+    assert np.array_equal(c_sw, c1)
+
+
+def test_sweep_member_against_oracle():
+    m, _ = inputs.grain_pack((23, 37), 0.6, 1.5, 4.0, seed=21)
+    with cdi.Domain(m, precision=cdi.FP64) as d:
+        d.solve_flow(tol=0.0, max_steps=600, U_target=1e-4)
+        g_sw, c_sw, dt_sw = d.sweep([(2e-4, 0.8), (5e-5, 0.4)], lambda_D=1.5e-7, c0=10.0,
+                                    n_steps=300)
+    for i, (U, V) in enumerate([(2e-4, 0.8), (5e-5, 0.4)]):
+        r = O.run_case(m, flow_tol=0.0, max_flow_steps=600, U_target=U, applied_V=V,
+                       lambda_D=1.5e-7, n_np_steps=300)
+        assert abs(dt_sw[i] - r["dt"]) <= 1e-11 * r["dt"]
+        np.testing.assert_allclose(g_sw[i], r["Gamma"], rtol=1e-11)
+        np.testing.assert_allclose(c_sw[i], r["C_out"], rtol=1e-11)
+
+
+def test_sweep_argument_errors():
+    m, _ = inputs.grain_pack((23, 37), 0.6, 1.5, 4.0, seed=21)
+    with cdi.Domain(m) as d:
+        with pytest.raises(cdi.CDIError) as e:     # no flow yet
+            d.sweep([(1e-4, 1.0)], n_steps=1)
+        assert e.value.status == 6
+        d.solve_flow(tol=0.0, max_steps=100)
+        with pytest.raises(cdi.CDIError) as e:
+            d.sweep([(1e-4, 1.0)], z=(1,) * 5, D=(1e-9,) * 5, n_steps=1)
+        assert e.value.status == 1
+        g, c, dt = d.sweep([(1e-4, 1.0)], n_steps=0)
+        assert np.all(g == 0)
