@@ -230,6 +230,16 @@ cdi_status cdi_query_outlet(cdi_domain *dom, double *per_species);
 cdi_status cdi_query_mass_balance(cdi_domain *dom, double *M, double *Gamma,
                                   double *In, double *Out);
 
+/* Geometry of the image (Sec. 4): porosity phi = pore cells / cells, and the
+ * specific surface s = pore-solid interface area / image volume (1/m; per
+ * metre of depth folded in for 2D, i.e. interface length / image area).
+ * Faces across the inlet and outlet planes do not count, nor, with lateral
+ * walls, faces across the lateral image boundary; with periodic lateral
+ * boundaries the wrapped neighbour decides.  With them Sec. 4 defines
+ * l_c = pi / s, Pe = U l_c / D and Da = Ka l_c / D.  Waits for the stream. */
+cdi_status cdi_query_geometry(cdi_domain *dom, double *porosity,
+                              double *specific_surface_per_m);
+
 /* Vertically averaged profile (Fig. 6, Fig. 9): the mean of species k over
  * the pore cells of each x column into out[nx] (0 for all-solid columns). */
 cdi_status cdi_query_column_means(cdi_domain *dom, int species, double *out);

@@ -94,6 +94,8 @@ SIGNATURES = [
     ("cdi_query_outlet", c_int, [c_void_p, c_void_p]),
     ("cdi_query_mass_balance", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("cdi_query_column_means", c_int, [c_void_p, c_int, c_void_p]),
+    ("cdi_query_geometry", c_int, [c_void_p, ctypes.POINTER(c_double),
+                                   ctypes.POINTER(c_double)]),
     ("cdi_copy_field", c_int, [c_void_p, c_int, c_void_p, c_size_t]),
     ("cdi_query_timing", c_int, [c_void_p, ctypes.POINTER(cdi_timing), c_int]),
     ("cdi_transport_sums_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
@@ -222,6 +224,12 @@ def query_mass_balance(handle, ns: int):
     _check(load().cdi_query_mass_balance(handle, _dptr(M), _dptr(G), _dptr(I), _dptr(O)),
            handle)
     return M, G, I, O
+
+
+def query_geometry(handle):
+    phi, s = c_double(0.0), c_double(0.0)
+    _check(load().cdi_query_geometry(handle, ctypes.byref(phi), ctypes.byref(s)), handle)
+    return phi.value, s.value
 
 
 def query_column_means(handle, species: int, nx: int) -> np.ndarray:
@@ -380,6 +388,10 @@ class Domain:
 
     def column_means(self, species):
         return query_column_means(self.handle, species, self.nx)
+
+    def geometry(self):
+        """(porosity, specific surface in 1/m)."""
+        return query_geometry(self.handle)
 
     def u_lattice(self):
         flow_shape = (self.NX,) if self.dim == 2 else (self.NX,)

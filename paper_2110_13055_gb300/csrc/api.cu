@@ -527,6 +527,16 @@ cdi_status cdi_query_outlet(cdi_domain *d, double *per_species) {
   return CDI_OK;
 }
 
+cdi_status cdi_query_geometry(cdi_domain *d, double *porosity, double *s_per_m) {
+  if (!d || !porosity || !s_per_m) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  double pores = 0.0, faces = 0.0;
+  cdi_status s = cdi_np_geometry(d, &pores, &faces);
+  if (s != CDI_OK) return s;
+  *porosity = pores / (double)d->N;
+  *s_per_m = faces / ((double)d->N * d->dx);
+  return CDI_OK;
+}
+
 cdi_status cdi_query_column_means(cdi_domain *d, int species, double *out) {
   if (!d || !out) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
   if (!d->np_ready) return cdi_fail(d, CDI_ERR_STATE, "no transport state");

@@ -292,11 +292,13 @@ enum {
   S_MASS = 32,                              // kMaxSpecies
   S_OUTP = 36,                              // kMaxSpecies: plain outlet sums
   S_ACC = 40,                               // 3*kMaxSpecies: Gamma/In/Out sums
-  S_OUTN = 52                               // pore cells in the outlet column
+  S_OUTN = 52,                              // pore cells in the outlet column
+  S_GEOM = 56                               // pore cells, pore-solid faces
 };
 
 // Counter slots in d_counter.
-enum { C_RES = 0, C_ULAT = 1, C_CG1 = 2, C_CG2 = 3, C_DT = 4, C_OUT = 5, C_MASS = 6, C_ACC = 7 };
+enum { C_RES = 0, C_ULAT = 1, C_CG1 = 2, C_CG2 = 3, C_DT = 4, C_OUT = 5, C_MASS = 6, C_ACC = 7,
+       C_GEOM = 8 };
 
 enum { PH_FLOW = 0, PH_CHECK = 1, PH_PSI = 2, PH_NP = 3 };
 
@@ -328,6 +330,7 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol,
 cdi_status cdi_np_build_flags(cdi_domain *d);
 cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used);
 cdi_status cdi_np_dt(cdi_domain *d, double scale, double *dt_out);
+cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces);
 cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *group,
                         void *const *phi_groups, const double *dts, int64_t n_steps,
                         double *gamma, double *cout);

@@ -158,69 +158,70 @@ __device__ __forceinline__ void np_cell(const T *__restrict__ Cin, T *__restrict
                                         long long N, int walls, long long P, T (&v)[3 * NS]) {
   using PS = PhiStore<T>;
   using PT = typename PS::type;
-  {
-    {
-      T CP[NS], sumJ[NS];
+  constexpr int NF = 2 * DIM;
+  // face kinds and neighbour cells first (32-bit indices: N < 2^31); a
+  // non-pore face stands in the own cell, whose values an outlet ghost copies
+  const int Pi = (int)P;
+  int kind[NF], Qi[NF];
+#pragma unroll
+  for (int fc = 0; fc < NF; fc++) {
+    long long Q = P;
+    kind[fc] = np_face<DIM>(f, fc, nx, ny, nz, walls, P, Q);
+    Qi[fc] = kind[fc] == F_PORE ? (int)Q : Pi;
+  }
+  // every load issued before any arithmetic (memory-level parallelism)
+  T CP[NS], sumJ[NS], un[NF], Cn[NF][NS];
+  PT phn[NF];
+#pragma unroll
+  for (int k = 0; k < NS; k++) {
+    CP[k] = Cin[(size_t)k * N + Pi];
+    sumJ[k] = T(0);
+  }
+  const PT phiP = phi[Pi];
+  T uP[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * N + Pi];
+#pragma unroll
+  for (int fc = 0; fc < NF; fc++) {
+    un[fc] = u[(size_t)(fc >> 1) * N + Qi[fc]];
+    phn[fc] = phi[Qi[fc]];
+#pragma unroll
+    for (int k = 0; k < NS; k++) Cn[fc][k] = Cin[(size_t)k * N + Qi[fc]];
+  }
+#pragma unroll
+  for (int fc = 0; fc < NF; fc++) {
+    const int a = fc >> 1;
+    const T sg = (fc & 1) ? T(-1) : T(1);
+    if (kind[fc] == F_WALL) continue;
+    if (kind[fc] == F_SOLID) {
 #pragma unroll
       for (int k = 0; k < NS; k++) {
-        CP[k] = Cin[(size_t)k * N + P];
-        sumJ[k] = T(0);
+        const T J = c.Keff[k] * CP[k];
+        sumJ[k] += J;
+        v[k] += J;
       }
-      const PT phiP = phi[P];
-      T uP[DIM];
+      continue;
+    }
+    if (kind[fc] == F_INLET) {  // feed ghost: C = c0, phi = 0, u = u_P
+      phn[fc] = PS::zero();
 #pragma unroll
-      for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * N + P];
+      for (int k = 0; k < NS; k++) Cn[fc][k] = c.c0;
+    }
+    const T uf = T(0.5) * (uP[a] + un[fc]) * sg;
+    T dhi, dlo;
+    FaceB<T>::dphi(phn[fc], phiP, dhi, dlo);
 #pragma unroll
-      for (int fc = 0; fc < 2 * DIM; fc++) {
-        const int a = fc >> 1;
-        const T sg = (fc & 1) ? T(-1) : T(1);
-        long long Q = 0;
-        const int kind = np_face<DIM>(f, fc, nx, ny, nz, walls, P, Q);
-        if (kind == F_WALL) continue;
-        if (kind == F_SOLID) {
-#pragma unroll
-          for (int k = 0; k < NS; k++) {
-            const T J = c.Keff[k] * CP[k];
-            sumJ[k] += J;
-            v[k] += J;
-          }
-          continue;
-        }
-        T unb, Cnb[NS];
-        PT phinb;
-        if (kind == F_PORE) {
-          unb = u[(size_t)a * N + Q];
-          phinb = phi[Q];
-#pragma unroll
-          for (int k = 0; k < NS; k++) Cnb[k] = Cin[(size_t)k * N + Q];
-        } else if (kind == F_INLET) {
-          unb = uP[a];
-          phinb = PS::zero();
-#pragma unroll
-          for (int k = 0; k < NS; k++) Cnb[k] = c.c0;
-        } else {
-          unb = uP[a];
-          phinb = phiP;
-#pragma unroll
-          for (int k = 0; k < NS; k++) Cnb[k] = CP[k];
-        }
-        const T uf = T(0.5) * (uP[a] + unb) * sg;
-        T dhi, dlo;
-        FaceB<T>::dphi(phinb, phiP, dhi, dlo);
-#pragma unroll
-        for (int k = 0; k < NS; k++) {
-          T Bp, Bm;
-          FaceB<T>::eval(uf * c.dxD[k], c.zf[k], dhi, dlo, Bp, Bm);
-          const T J = c.Ddx[k] * (Bm * CP[k] - Bp * Cnb[k]);
-          sumJ[k] += J;
-          if (kind == F_INLET) v[NS + k] -= J;
-          if (kind == F_OUTLET) v[2 * NS + k] += J;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NS; k++) Cout[(size_t)k * N + P] = CP[k] - c.dtdx * sumJ[k];
+    for (int k = 0; k < NS; k++) {
+      T Bp, Bm;
+      FaceB<T>::eval(uf * c.dxD[k], c.zf[k], dhi, dlo, Bp, Bm);
+      const T J = c.Ddx[k] * (Bm * CP[k] - Bp * Cn[fc][k]);
+      sumJ[k] += J;
+      if (kind[fc] == F_INLET) v[NS + k] -= J;
+      if (kind[fc] == F_OUTLET) v[2 * NS + k] += J;
     }
   }
+#pragma unroll
+  for (int k = 0; k < NS; k++) Cout[(size_t)k * N + Pi] = CP[k] - c.dtdx * sumJ[k];
 }
 
 // Block sums of v in T, added by thread 0 to the block's own FP64 accounts
@@ -418,6 +419,33 @@ __global__ void __launch_bounds__(kRedThreads)
         scal[S_OUTP + k] = v[9 + k];
       }
       scal[S_OUTN] = v[13];
+      *counter = 0;
+    }
+  }
+}
+
+// Pore cells and pore-solid faces inside the image (the interface the
+// specific surface of Sec. 4 measures), counted over the pore-cell list.
+__global__ void __launch_bounds__(kRedThreads)
+    k_geometry(const NFlag *__restrict__ fl, const int *__restrict__ cells, int n, int faces,
+               double *__restrict__ part, unsigned int *counter, double *scal) {
+  __shared__ double sm[2 * 32];
+  double v[2] = {0.0, 0.0};
+  const unsigned face_bits = ((1u << faces) - 1u) << kFaceBit;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    v[0] += 1.0;
+    v[1] += (double)__popc(fl[cells[k]] & face_bits);
+  }
+  block_reduce<2>(v, sm, OpSum(), 0.0);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = v[0];
+    part[gridDim.x + blockIdx.x] = v[1];
+  }
+  if (last_block(counter, gridDim.x)) {
+    combine_partials<2>(part, gridDim.x, v, sm, OpSum(), 0.0);
+    if (threadIdx.x == 0) {
+      scal[S_GEOM] = v[0];
+      scal[S_GEOM + 1] = v[1];
       *counter = 0;
     }
   }
@@ -788,6 +816,21 @@ cdi_status cdi_np_reduce(cdi_domain *d) {
           "sums copy");
   CDI_TRY(d, cudaStreamSynchronize(d->stream), "transport sums");
   CDI_TRY(d, cdi_timing_resolve(d), "timing");
+  return CDI_OK;
+}
+
+cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces) {
+  k_geometry<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list,
+                                                         (int)d->n_pore, 2 * d->dim, d->d_part,
+                                                         d->d_counter + C_GEOM, d->d_scal);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "geometry");
+  CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_GEOM, d->d_scal + S_GEOM, 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost, d->stream),
+          "geometry copy");
+  CDI_TRY(d, cudaStreamSynchronize(d->stream), "geometry");
+  *pores = d->h_scal[S_GEOM];
+  *faces = d->h_scal[S_GEOM + 1];
   return CDI_OK;
 }
 

@@ -136,6 +136,58 @@ def grain_pack(shape, porosity: float, r_min: float, r_max: float, seed: int,
     return solid, PackInfo(phi, len(placed), mask_sha256(solid))
 
 
+def fibre_pack(n: int, porosity: float, diameter_vox: float, seed: int,
+               max_fibres: int = 100000):
+    """Random straight fibres of one diameter through an n^3 box (the fibrous
+    electrodes of Sec. 5): each fibre's axis passes through a point uniform in
+    the box along a direction uniform on the sphere and extends to the box
+    faces; voxels whose centre lies within half the diameter of the axis are
+    solid; fibres overlap freely; fibres are added until the porosity first
+    drops to the target.  Returns ``(mask, PackInfo)`` with shape (n, n, n)."""
+    rng = SplitMix64(seed)
+    solid = np.zeros((n, n, n), dtype=np.uint8)        # (z, y, x)
+    flat = solid.reshape(-1)
+    r = 0.5 * diameter_vox
+    h = int(np.ceil(r * np.sqrt(3.0))) + 1             # slice window half-width
+    w = np.arange(-h, h + 1)
+    total = solid.size
+    n_solid = 0
+    count = 0
+    while 1.0 - n_solid / total > porosity and count < max_fibres:
+        p = np.array([rng.uniform() * n for _ in range(3)])          # x, y, z
+        cz = 2.0 * rng.uniform() - 1.0
+        ph = 2.0 * np.pi * rng.uniform()
+        s = np.sqrt(1.0 - cz * cz)
+        d = np.array([s * np.cos(ph), s * np.sin(ph), cz])          # unit axis
+        # walk the axis along its dominant direction: in each slice the
+        # voxels within r of the axis lie within h of the crossing point
+        m = int(np.argmax(np.abs(d)))
+        a, b = [k for k in range(3) if k != m]
+        cm = np.arange(n) + 0.5
+        t = (cm - p[m]) / d[m]
+        qa = p[a] + t * d[a]
+        qb = p[b] + t * d[b]
+        ia = np.floor(qa).astype(int)[:, None, None] + w[None, :, None]
+        ib = np.floor(qb).astype(int)[:, None, None] + w[None, None, :]
+        im = np.broadcast_to(np.arange(n)[:, None, None], (n, w.size, w.size))
+        ia = np.broadcast_to(ia, im.shape)
+        ib = np.broadcast_to(ib, im.shape)
+        inside = (ia >= 0) & (ia < n) & (ib >= 0) & (ib < n)
+        coords = [None, None, None]
+        coords[m], coords[a], coords[b] = im[inside], ia[inside], ib[inside]
+        vx = coords[0] + 0.5 - p[0]
+        vy = coords[1] + 0.5 - p[1]
+        vz = coords[2] + 0.5 - p[2]
+        tt = vx * d[0] + vy * d[1] + vz * d[2]
+        hit = vx * vx + vy * vy + vz * vz - tt * tt <= r * r
+        idx = np.unique((coords[2][hit] * n + coords[1][hit]) * n + coords[0][hit])
+        n_solid += int(np.count_nonzero(flat[idx] == 0))
+        flat[idx] = 1
+        count += 1
+    phi = 1.0 - n_solid / total
+    return solid, PackInfo(phi, count, mask_sha256(solid))
+
+
 def mask_sha256(mask: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(mask, dtype=np.uint8).tobytes()).hexdigest()
 

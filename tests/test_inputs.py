@@ -33,3 +33,31 @@ def test_sphere_pack_porosity():
     m, info = I.grain_pack((24, 24, 24), 0.5, 3.0, 5.0, seed=2)
     assert m.shape == (24, 24, 24)
     assert 0.45 < info.porosity <= 0.5
+
+
+def _fibres_brute_force(n, porosity, diameter, seed):
+    """The fibre recipe with a full-volume distance test per fibre."""
+    rng = I.SplitMix64(seed)
+    solid = np.zeros((n, n, n), np.uint8)
+    c = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r2 = (0.5 * diameter) ** 2
+    while 1.0 - solid.sum() / solid.size > porosity:
+        p = [rng.uniform() * n for _ in range(3)]
+        cz = 2.0 * rng.uniform() - 1.0
+        ph = 2.0 * np.pi * rng.uniform()
+        s = np.sqrt(1.0 - cz * cz)
+        d = (s * np.cos(ph), s * np.sin(ph), cz)
+        vx, vy, vz = X - p[0], Y - p[1], Z - p[2]
+        t = vx * d[0] + vy * d[1] + vz * d[2]
+        solid[vx * vx + vy * vy + vz * vz - t * t <= r2] = 1
+    return solid
+
+
+def test_fibre_pack_matches_brute_force():
+    """The windowed fibre stamping marks exactly the voxels a full distance
+    test marks (straight fibres through the box, Sec. 5)."""
+    for n, phi, dia, seed in ((24, 0.7, 4.0, 1), (20, 0.5, 6.0, 2)):
+        m, info = I.fibre_pack(n, phi, dia, seed)
+        assert np.array_equal(m, _fibres_brute_force(n, phi, dia, seed))
+        assert info.porosity <= phi
