@@ -151,22 +151,27 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def csrc_hash():
+KERNEL_SOURCES = {"k_lbm_step": "flow.cu", "k_np_step": "transport.cu"}
+
+
+def kernel_hash(kernel):
+    """Hash of the source file that defines the kernel and the shared header."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2110_13055_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    csrc = os.path.join(ROOT, "paper_2110_13055_gb300", "csrc")
+    for f in (KERNEL_SOURCES[kernel], "cdi_internal.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+def recorded_traffic(kernel, workload):
+    """Per-launch DRAM bytes of the kernel on this workload from a committed
+    ncu summary, if it was taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(p)).get(kernel)
-    except (OSError, ValueError):
+        rec = json.load(open(p)).get(kernel, {}).get(workload)
+    except (OSError, ValueError, AttributeError):
         return None
-    if not rec or rec.get("csrc_sha") != csrc_hash():
+    if not rec or rec.get("source_sha") != kernel_hash(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -246,13 +251,13 @@ def ours(args, w, mask):
     # FP32); odd steps also read its Q-1 neighbour ranks (4 B each), so a
     # launch averages half of that; every pore cell of the transport grid
     # reads and writes 2 species, reads d velocity components, the 8-byte
-    # potential, its list index and its 2-byte flags
-    Tp = 4 if w["prec"] == cdi.FP32 else 8
+    # potential and its 8-byte rank metadata (flags, x, row)
+    Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[w["prec"]]
     Tt = 8 if w["prec"] == cdi.FP64 else 4
     Q = 9 if dim == 2 else 19
     n_flow_pore = 2 * n_pore
     lbm_bytes = n_flow_pore * (Q * 2 * Tp + (Q - 1) * 4 // 2)
-    np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 4 + 2)
+    np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 8)
     lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
     np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3
     if tim["flow_ms"] >= tim["np_ms"]:
@@ -261,7 +266,7 @@ def ours(args, w, mask):
         kname, abytes, avg = "k_np_step", np_bytes, np_avg
     peak, peak_kind = measured_peak_gbs()
     achieved = abytes / avg / 1e9 if avg > 0 else 0.0
-    traffic = recorded_traffic(kname)
+    traffic = recorded_traffic(kname, args.workload)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -299,7 +304,8 @@ def ours(args, w, mask):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64" if w["prec"] == cdi.FP64 else "f32",
-        "storage": {cdi.FP64: "fp64", cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations"}[w["prec"]],
+        "storage": {cdi.FP64: "fp64", cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations",
+                    cdi.BF16_POP: "bf16 populations, fp32 transport"}[w["prec"]],
         "data": "synthetic",
         "config": {"workload": w["desc"], "name": args.workload,
                    "flow_sites": Nf, "cells": N, "pore_cells": n_pore,
@@ -333,38 +339,42 @@ SWEEP_V = (0.2, 0.6, 1.0, 1.2)
 SWEEP_U = (1e-5, 1e-4, 1e-3)
 
 
-def sweep_geometries(n_geom, seed0=10):
-    """The batched-sweep recipe: seeded polydisperse disc packs (r ~ U[4,16],
-    overlap allowed), porosity ~ U[0.4, 0.7] drawn from the seed."""
-    out = []
-    for k in range(n_geom):
-        rs = np.random.default_rng(seed0 + k)
-        phi = float(rs.uniform(0.4, 0.7))
-        m, _ = inputs.grain_pack((256, 256), phi, 4.0, 16.0, seed=seed0 + k)
-        out.append(m)
-    return out
-
-
 def sweep_bench(args):
     """Batched sweep against the plain one-solve-at-a-time loop, at equal
-    results: every (geometry, V, U) is one solve of flow + potential +
-    transport.  The plain loop runs each solve from scratch through the C ABI
-    (create, flow, potential, transport, queries, destroy); the batched path
-    solves each geometry's flow once, shares potentials across velocities and
-    advances all 12 combinations of a geometry in one fused launch per step."""
+    results.  Geometries: seeds 10, 11, ... of the sweep recipe (2D disc packs
+    of uneven sizes 256x256 to 1024x512, porosity ~U[0.4, 0.7]); every
+    (geometry, V, U) is one solve of flow + potential + transport.  The plain
+    loop runs each solve from scratch through the C ABI (create, flow,
+    potential, transport, queries, destroy).  The batched path solves each
+    geometry's flow once (the geometries' flows run concurrently, one stream
+    each), shares potentials across velocities, and advances all members of all
+    geometries in one fused launch per step (cdi_sweep_batch).  The BF16
+    population variant runs the batched path with the same flow step counts
+    and reports its difference from the FP32-pair results."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     torch.cuda.set_device(0)
-    geoms = sweep_geometries(args.sweep_geometries)
+    geoms = [inputs.sweep_instance(10 + k)[0] for k in range(args.sweep_geometries)]
     combos = [(U, V) for V in SWEEP_V for U in SWEEP_U]
     n_np = args.np_steps or 5000
     prec = cdi.FP32_SPLIT
-    kw = dict(tol=1e-8, max_steps=1_000_000)
+    kw = dict(tol=1e-8, max_steps=2_000_000)
 
-    def batched(m):
-        with cdi.Domain(m, precision=prec) as d:
-            d.solve_flow(U_target=1e-4, **kw)
-            g, c, _ = d.sweep(combos, n_steps=n_np)
-        return g, c
+    def batched(masks, precision=prec, flow_steps=None):
+        doms = [cdi.Domain(m, precision=precision) for m in masks]
+        try:
+            def flow(i):
+                if flow_steps is None:
+                    return doms[i].solve_flow(U_target=1e-4, **kw)[0]
+                return doms[i].solve_flow(U_target=1e-4, tol=1e-8, max_steps=flow_steps[i],
+                                          allow_not_converged=True)[0]
+            with ThreadPoolExecutor(len(doms)) as ex:
+                steps = list(ex.map(flow, range(len(doms))))
+            g, c, _ = cdi.batch(doms, combos, n_steps=n_np)
+        finally:
+            for d in doms:
+                d.close()
+        return g, c, steps
 
     def plain(m, U, V):
         with cdi.Domain(m, precision=prec) as d:
@@ -376,68 +386,74 @@ def sweep_bench(args):
             d.step(n_np)
             return d.adsorbed(), d.outlet()
 
-    batched(geoms[0])                       # warm-up (kernel loading, graphs)
+    batched([inputs.sweep_instance(9)[0]])          # warm-up (kernel loading, graphs)
     torch.cuda.synchronize()
-    lat_b, res_b = [], []
     t0 = time.perf_counter()
-    for m in geoms:
-        t = time.perf_counter()
-        res_b.append(batched(m))
-        lat_b.extend([time.perf_counter() - t] * len(combos))  # all finish together
+    g_b, c_b, steps = batched(geoms)
     t_b = time.perf_counter() - t0
-    lat_p, res_p = [], []
+    t0 = time.perf_counter()
+    g_h, c_h, _ = batched(geoms, cdi.BF16_POP, flow_steps=steps)
+    t_h = time.perf_counter() - t0
+    lat_p, g_p, c_p = [], [], []
     t0 = time.perf_counter()
     for m in geoms:
-        gs, cs = [], []
         for U, V in combos:
             t = time.perf_counter()
             g, c = plain(m, U, V)
             lat_p.append(time.perf_counter() - t)
-            gs.append(g)
-            cs.append(c)
-        res_p.append((np.array(gs), np.array(cs)))
+            g_p.append(g)
+            c_p.append(c)
     t_p = time.perf_counter() - t0
+    g_p = np.array(g_p).reshape(g_b.shape)
+    c_p = np.array(c_p).reshape(c_b.shape)
     n_solves = len(geoms) * len(combos)
-    diff = max(float(np.max(np.abs(b[0] - p[0]) / np.abs(p[0]))) for b, p in zip(res_b, res_p))
-    same = all(np.array_equal(b[0], p[0]) and np.array_equal(b[1], p[1])
-               for b, p in zip(res_b, res_p))
+    same = bool(np.array_equal(g_b, g_p) and np.array_equal(c_b, c_p))
+    lat_b = [t_b] * n_solves                       # every member finishes with the batch
     return {
         "metric": "sweep solves/s (batched vs plain loop, equal results)",
         "value": n_solves / t_b, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "storage": "fp32-pair populations", "data": "synthetic",
-        "config": {"workload": (f"{len(geoms)} 2D 256x256 polydisperse disc packs (r~U[4,16], "
-                                f"porosity ~U[0.4,0.7], seeds 10..) x V {SWEEP_V} x U {SWEEP_U}; "
-                                f"flow to 1e-8 per geometry; {n_np} Nernst-Planck steps per "
-                                "solve; wall-clock with host buffers (through the C ABI)"),
-                   "solves": n_solves},
+        "dtype": "f32", "storage": "fp32-pair populations, fp32 transport", "data": "synthetic",
+        "config": {"workload": (f"{len(geoms)} 2D disc packs of the sweep recipe (seeds 10.."
+                                f"{9 + len(geoms)}; sizes "
+                                + ", ".join(f"{m.shape[1]}x{m.shape[0]}" for m in geoms)
+                                + f") x V {SWEEP_V} x U {SWEEP_U}; flow to 1e-8 per geometry; "
+                                f"{n_np} Nernst-Planck steps per solve; wall-clock through the "
+                                "C ABI with host buffers"),
+                   "solves": n_solves, "flow_steps": steps},
         "plain": {"value": n_solves / t_p, "p50_s": float(np.percentile(lat_p, 50)),
                   "p99_s": float(np.percentile(lat_p, 99)), "seconds": t_p},
         "batched": {"value": n_solves / t_b, "p50_s": float(np.percentile(lat_b, 50)),
                     "p99_s": float(np.percentile(lat_b, 99)), "seconds": t_b},
         "speedup": t_p / t_b,
-        "results_bitwise_equal": same, "max_rel_gamma_diff": diff,
+        "results_bitwise_equal": same,
+        "max_rel_gamma_diff": float(np.max(np.abs(g_b - g_p) / np.abs(g_p))),
+        "bf16_populations": {
+            "value": n_solves / t_h, "seconds": t_h,
+            "max_rel_gamma_diff_vs_fp32_pair": float(np.max(np.abs(g_h - g_b) / np.abs(g_b))),
+            "max_rel_cout_diff_vs_fp32_pair": float(np.max(np.abs(c_h - c_b) / np.abs(c_b)))},
     }
 
 
+_SERVE_MASKS = {}
+
+
 def serve_requests(n, seed=100):
-    """Mixed request stream: half 2D 256x256 disc packs (FP32-pair flow to 1e-8),
-    half 3D sphere packs n^3, n in {48, 64, 80, 96} (FP32 flow to 1e-7);
-    porosity ~U[0.4, 0.6], potential ~U[0.2, 1.2] V, 2000 transport steps."""
+    """Mixed request stream of the serving recipe (seeds seed, seed + 1, ...):
+    half 2D 512x512 disc packs (FP32-pair flow to 1e-8, U = 1e-4 m/s), half 3D
+    sphere packs n^3, n in {64, 96, 128, 160, 192} (FP32 flow to 1e-7, U =
+    1e-6 m/s, c0 = 20 mM); porosity ~U[0.4, 0.6], potential ~U[0.2, 1.2] V,
+    2000 transport steps per request."""
     from paper_2110_13055_gb300 import serve
-    rs = np.random.default_rng(seed)
     reqs = []
     for i in range(n):
-        phi = float(rs.uniform(0.4, 0.6))
-        V = float(rs.uniform(0.2, 1.2))
-        s = int(rs.integers(1, 1 << 30))
-        if rs.random() < 0.5:
-            m, _ = inputs.grain_pack((256, 256), phi, 4.0, 16.0, seed=s)
+        if seed + i not in _SERVE_MASKS:
+            _SERVE_MASKS[seed + i] = inputs.serve_instance(seed + i)
+        m, V = _SERVE_MASKS[seed + i]
+        if m.ndim == 2:
             reqs.append(serve.Request(m, V, 1e-4, 2000, precision=cdi.FP32_SPLIT,
                                       flow_tol=1e-8, tag=i))
         else:
-            k = int(rs.choice([48, 64, 80, 96]))
-            m, _ = inputs.grain_pack((k, k, k), phi, 3.0, 6.0, seed=s)
             reqs.append(serve.Request(m, V, 1e-6, 2000, precision=cdi.FP32, flow_tol=1e-7,
                                       max_flow_steps=200_000, c0=20.0, tag=i))
     return reqs
@@ -463,7 +479,7 @@ def serve_bench(args):
                       "memory_budget_GiB": args.serve_budget_gib},
            "rates": []}
     rs = np.random.default_rng(5)
-    for frac in (0.5, 1.0, 1.5, 2.0):
+    for frac in args.serve_rates:
         rate = frac * cap
         arrivals = list(np.cumsum(rs.exponential(1.0 / rate, size=n)))
         seq = serve.run_sequential(serve_requests(n, seed=100), arrivals)
@@ -543,11 +559,13 @@ def main():
                          "converging; for short profiling runs")
     ap.add_argument("--np-steps", type=int, default=0,
                     help="override the number of transport steps")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-pair"], default=None,
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-pair", "bf16"], default=None,
                     help="override the workload's storage precision")
     ap.add_argument("--sweep", action="store_true",
                     help="batched parameter sweep against the plain loop (solves/s)")
     ap.add_argument("--sweep-geometries", type=int, default=8)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
+                    help="offered load as fractions of the sequential capacity")
     ap.add_argument("--serve", action="store_true",
                     help="continuous-batching server against the sequential loop")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -561,7 +579,8 @@ def main():
         return
     w = dict(WORKLOADS[args.workload])
     if args.precision:
-        w["prec"] = {"fp64": cdi.FP64, "fp32": cdi.FP32, "fp32-pair": cdi.FP32_SPLIT}[args.precision]
+        w["prec"] = {"fp64": cdi.FP64, "fp32": cdi.FP32, "fp32-pair": cdi.FP32_SPLIT,
+                     "bf16": cdi.BF16_POP}[args.precision]
         w["desc"] += f" [override: {args.precision} storage]"
     if args.flow_steps:
         w.update(flow_tol=0.0, max_flow=args.flow_steps)

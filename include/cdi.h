@@ -65,10 +65,15 @@ typedef enum {
   CDI_FP64 = 0,      /* populations, velocity, potential, concentrations in FP64 */
   CDI_FP32 = 1,      /* the same fields stored and updated in FP32; reductions,
                         the potential solve and all accumulators stay FP64 */
-  CDI_FP32_SPLIT = 2 /* as CDI_FP32, but every population is an unevaluated pair
-                        of FP32 words (hi + lo) updated with error-free FP32
-                        transformations: FP64-class flow accuracy at FP32
-                        arithmetic rates, twice the population memory */
+  CDI_FP32_SPLIT = 2, /* as CDI_FP32, but every population is an unevaluated pair
+                         of FP32 words (hi + lo) updated with error-free FP32
+                         transformations: FP64-class flow accuracy at FP32
+                         arithmetic rates, twice the population memory */
+  CDI_BF16_POP = 3    /* as CDI_FP32, but the populations are stored in BF16
+                         (shifted, f - w; collision in FP32): half the
+                         population bytes of FP32, about 3 significant digits;
+                         an option whose flow error is measured and reported,
+                         not held to the FP32 bounds */
 } cdi_precision;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -214,6 +219,29 @@ cdi_status cdi_sweep_transport(cdi_domain *dom, const cdi_combo *combos, int n_c
                                int n_species, double c0_molm3, double Ka_mps,
                                int64_t n_steps, double *gamma_out, double *cout_out,
                                double *dt_out);
+
+/* Batched transport over several geometries: the parameter studies of
+ * Sec. 4.1, 4.2 and Sec. 5 repeated over many electrode images.  Every
+ * (domain, combination) pair is a member (member index i * n_combos + c for
+ * domain i, combination c); each domain prepares its members exactly as
+ * cdi_sweep_transport does (rescaled flow, one potential per distinct
+ * applied_V, its own time step), and then all members of all domains advance
+ * together: one fused kernel launch per step walks the members' cell blocks,
+ * whatever their sizes.  Each member's result equals, bit for bit, that of a
+ * single run of its domain with the same arguments.
+ *   doms: n_doms >= 1 distinct domains on the current device, all of the same
+ *     dimension and precision, each with a solved flow.  doms[0] leads: its
+ *     stream runs the batch and its allocator provides the members' device
+ *     memory for the call only (about (dim + 8) * 4 bytes per pore cell per
+ *     member in FP32, plus one potential per domain and applied_V).
+ *   gamma_out, cout_out: host, n_doms * n_combos * n_species doubles;
+ *   dt_out: n_doms * n_combos doubles or NULL.
+ * Blocks until done; replaces every domain's potential and transport state.
+ * An error in a domain's preparation is reported on doms[0]. */
+cdi_status cdi_sweep_batch(cdi_domain *const *doms, int n_doms, const cdi_combo *combos,
+                           int n_combos, const cdi_elec_params *p, const cdi_species *sp,
+                           int n_species, double c0_molm3, double Ka_mps, int64_t n_steps,
+                           double *gamma_out, double *cout_out, double *dt_out);
 
 /* Adsorbed amount per species since cdi_init_transport: mol (3D) or mol per
  * metre of depth (2D).  Waits for the stream. */

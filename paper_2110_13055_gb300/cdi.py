@@ -21,7 +21,7 @@ c_int, c_double, c_size_t, c_int64, c_void_p = (ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_size_t, ctypes.c_int64,
                                                 ctypes.c_void_p)
 
-FP64, FP32, FP32_SPLIT = 0, 1, 2
+FP64, FP32, FP32_SPLIT, BF16_POP = 0, 1, 2, 3
 FIELD_U_LATTICE, FIELD_U, FIELD_PSI, FIELD_C = 0, 1, 2, 3
 STATUS = {0: "CDI_OK", 1: "CDI_ERR_INVALID_ARG", 2: "CDI_ERR_OOM", 3: "CDI_ERR_CUDA",
           4: "CDI_ERR_NOT_CONVERGED", 5: "CDI_ERR_TIMEOUT", 6: "CDI_ERR_STATE"}
@@ -90,6 +90,10 @@ SIGNATURES = [
                                     ctypes.POINTER(cdi_elec_params),
                                     ctypes.POINTER(cdi_species), c_int, c_double, c_double,
                                     c_int64, c_void_p, c_void_p, c_void_p]),
+    ("cdi_sweep_batch", c_int, [c_void_p, c_int, ctypes.POINTER(cdi_combo), c_int,
+                                ctypes.POINTER(cdi_elec_params), ctypes.POINTER(cdi_species),
+                                c_int, c_double, c_double, c_int64, c_void_p, c_void_p,
+                                c_void_p]),
     ("cdi_query_adsorbed", c_int, [c_void_p, c_void_p]),
     ("cdi_query_outlet", c_int, [c_void_p, c_void_p]),
     ("cdi_query_mass_balance", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -205,6 +209,33 @@ def sweep_transport(handle, combos, params: cdi_elec_params, z, D, c0, Ka, n_ste
                                       c_double(c0), c_double(Ka), c_int64(n_steps), _dptr(gam),
                                       _dptr(cout), _dptr(dt)), handle)
     return gam, cout, dt
+
+
+def sweep_batch(handles, combos, params: cdi_elec_params, z, D, c0, Ka, n_steps):
+    """Every (domain, combination) member in one fused launch per step.
+    Returns (gamma, c_out, dt) of shapes (n_doms, n_combos, n_species) and
+    (n_doms, n_combos)."""
+    nd, nc, ns = len(handles), len(combos), len(z)
+    hs = (c_void_p * nd)(*[h.value if isinstance(h, c_void_p) else h for h in handles])
+    cb = (cdi_combo * nc)(*[cdi_combo(float(U), float(V)) for U, V in combos])
+    sp = (cdi_species * ns)(*[cdi_species(int(zz), float(dd)) for zz, dd in zip(z, D)])
+    gam, cout, dt = np.zeros((nd, nc, ns)), np.zeros((nd, nc, ns)), np.zeros((nd, nc))
+    _check(load().cdi_sweep_batch(hs, nd, cb, nc, ctypes.byref(params), sp, ns, c_double(c0),
+                                  c_double(Ka), c_int64(n_steps), _dptr(gam), _dptr(cout),
+                                  _dptr(dt)), handles[0])
+    return gam, cout, dt
+
+
+def batch(domains, combos, *, z=(1, -1), D=(1.33e-9, 2.03e-9), c0=10.0, Ka=1e-6, n_steps=5000,
+          T=298.15, eps_r=78.5, c_bulk=None, lambda_D=0.0, mode="debye", tol=1e-12,
+          max_iter=100000):
+    """cdi_sweep_batch over Domain objects (each with a solved flow)."""
+    p = cdi_elec_params(float(T), float(eps_r), float(c0 if c_bulk is None else c_bulk),
+                        float(lambda_D or 0.0), 0 if mode == "debye" else 1, float(tol),
+                        int(max_iter))
+    for d in domains:
+        d.ns = 0
+    return sweep_batch([d.handle for d in domains], combos, p, z, D, c0, Ka, n_steps)
 
 
 def query_adsorbed(handle, ns: int) -> np.ndarray:

@@ -124,30 +124,6 @@ cudaError_t cdi_timing_resolve(cdi_domain *d) {
 }
 
 // ---------------------------------------------------------------------------
-// Conversion kernel for cdi_copy_field.
-// ---------------------------------------------------------------------------
-__global__ void k_to_double_f(const float *s, double *d, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    d[i] = (double)s[i];
-}
-
-cdi_status cdi_convert_to_double(cdi_domain *d, const void *src, int is_float, double *dst,
-                                 size_t n) {
-  if (!is_float) {
-    CDI_TRY(d, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, d->stream),
-            "copy field");
-    return CDI_OK;
-  }
-  int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
-  if (blocks < 1) blocks = 1;
-  k_to_double_f<<<blocks, 256, 0, d->stream>>>((const float *)src, dst, n);
-  d->timing.kernel_launches++;
-  CDI_TRY(d, cudaGetLastError(), "convert field");
-  return CDI_OK;
-}
-
-// ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -168,11 +144,12 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "dim must be 2 or 3");
   if (D.nx < 1 || D.ny < 1 || D.nz < 1 || (D.dim == 2 && D.nz != 1))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "bad grid size (nz must be 1 in 2D)");
-  if (D.ny > 65535 || D.nz > 65535)
-    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "ny and nz must be <= 65535");
+  if (D.nx > 65535 || D.ny > 65535 || D.nz > 65535)
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "nx, ny and nz must be <= 65535");
   if (!(D.dx_m > 0.0) || !std::isfinite(D.dx_m))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "dx_m must be positive");
-  if (D.precision != CDI_FP64 && D.precision != CDI_FP32 && D.precision != CDI_FP32_SPLIT)
+  if (D.precision != CDI_FP64 && D.precision != CDI_FP32 && D.precision != CDI_FP32_SPLIT &&
+      D.precision != CDI_BF16_POP)
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "unknown precision");
   if (alloc && (!alloc->alloc || !alloc->free))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "allocator needs alloc and free");
@@ -229,6 +206,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   const size_t fflag = D.dim == 2 ? 2 : 4;
   d->n_flow_pore = n_pore * (D.mirror_x ? 2 : 1);
   d->np_blocks = (int)((n_pore + cdi::kRowBlock - 1) / cdi::kRowBlock);
+  d->np_accs = d->np_blocks * (cdi::kRowBlock / 32);
   bool ok = true;
   auto A = [&](size_t bytes) {
     void *p = cdi_dev_alloc(d, bytes);
@@ -244,16 +222,22 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   int *rank_work = (int *)A((size_t)Nf * sizeof(int));
   // populations stored by pore rank: Q * n_flow_pore values
   const size_t nq = (size_t)Q * d->n_flow_pore;
-  d->d_g = A(nq * T);
+  const size_t Tpop = d->prec == CDI_FP64 ? 8 : d->prec == CDI_BF16_POP ? 2 : 4;
+  d->d_g = A(nq * Tpop);
   if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A(nq * 4);
   d->d_nbr = (int *)A((size_t)(Q - 1) * d->n_flow_pore * sizeof(int));
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
-  d->d_u = A((size_t)D.dim * N * T);
+  // transport fields by pore rank
+  d->W = (D.nx + 31) / 32;
+  const size_t n_words = (size_t)D.ny * D.nz * d->W;
+  d->d_cmeta = (uint2 *)A((size_t)n_pore * sizeof(uint2));
+  d->d_words = (uint2 *)A(n_words * sizeof(uint2));
+  d->d_u = A((size_t)D.dim * n_pore * T);
   d->d_psi = (double *)A(N * 8);
-  d->d_phi = A(N * 8);
-  d->d_C[0] = A((size_t)cdi::kMaxSpecies * N * T);
-  d->d_C[1] = A((size_t)cdi::kMaxSpecies * N * T);
-  d->d_acc = (double *)A((size_t)3 * cdi::kMaxSpecies * d->np_blocks * 8);
+  d->d_phi = A((size_t)n_pore * 8);
+  d->d_C[0] = A((size_t)cdi::kMaxSpecies * n_pore * T);
+  d->d_C[1] = A((size_t)cdi::kMaxSpecies * n_pore * T);
+  d->d_acc = (double *)A((size_t)3 * cdi::kMaxSpecies * d->np_accs * 8);
   d->d_part = (double *)A((size_t)16 * cdi::kRedBlocks * 8);
   d->d_counter = (unsigned int *)A(16 * sizeof(unsigned int));
   d->d_scal = (double *)A(64 * 8);
@@ -279,18 +263,19 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   chk(cudaMemcpyAsync(d->d_mask, mask, N, cudaMemcpyHostToDevice, d->stream), "upload mask");
   chk(cudaMemsetAsync(d->d_counter, 0, 16 * sizeof(unsigned int), d->stream), "memset");
   chk(cudaMemsetAsync(d->d_scal, 0, 64 * 8, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_g, 0, nq * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_g, 0, nq * Tpop, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_uflow, 0, (size_t)D.dim * Nf * 8, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_u, 0, (size_t)D.dim * N * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_u, 0, (size_t)D.dim * n_pore * T, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_psi, 0, N * 8, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_phi, 0, N * 8, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_C[0], 0, (size_t)cdi::kMaxSpecies * N * T, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_C[1], 0, (size_t)cdi::kMaxSpecies * N * T, d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_acc, 0, (size_t)3 * cdi::kMaxSpecies * d->np_blocks * 8, d->stream),
+  chk(cudaMemsetAsync(d->d_phi, 0, (size_t)n_pore * 8, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_C[0], 0, (size_t)cdi::kMaxSpecies * n_pore * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_C[1], 0, (size_t)cdi::kMaxSpecies * n_pore * T, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_acc, 0, (size_t)3 * cdi::kMaxSpecies * d->np_accs * 8, d->stream),
       "memset");
   if (s == CDI_OK) s = cdi_flow_build_flags(d);
   if (s == CDI_OK) s = cdi_np_build_flags(d);
   if (s == CDI_OK) s = cdi_build_lists(d, list_work);
+  if (s == CDI_OK) s = cdi_np_build_compact(d);
   if (s == CDI_OK) s = cdi_flow_build_links(d, rank_work);
   if (s == CDI_OK) chk(cudaStreamSynchronize(d->stream), "create domain");
   if (s == CDI_OK) {  // the work arrays are needed at create time only
@@ -406,12 +391,15 @@ cdi_status cdi_init_transport(cdi_domain *d, const cdi_species *sp, int n, doubl
   return s;
 }
 
-cdi_status cdi_sweep_transport(cdi_domain *d, const cdi_combo *combos, int n_combos,
-                               const cdi_elec_params *ep, const cdi_species *sp, int n,
-                               double c0, double Ka, int64_t n_steps, double *gamma_out,
-                               double *cout_out, double *dt_out) {
-  if (!d || !combos || !ep || !sp || !gamma_out || !cout_out)
-    return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Argument checks shared by the sweep entry points.
+cdi_status check_sweep_args(cdi_domain *d, const cdi_combo *combos, int n_combos,
+                            const cdi_elec_params *ep, const cdi_species *sp, int n, double c0,
+                            double Ka, int64_t n_steps) {
+  if (!combos || !ep || !sp) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
   if (n_combos < 1 || n_combos > 4096)
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "1..4096 combinations");
   if (n_steps < 0) return cdi_fail(d, CDI_ERR_INVALID_ARG, "n_steps < 0");
@@ -430,6 +418,17 @@ cdi_status cdi_sweep_transport(cdi_domain *d, const cdi_combo *combos, int n_com
       if (combos[m].U_mps != 0.0)
         return cdi_fail(d, CDI_ERR_INVALID_ARG, "no net flow through the pore space to scale");
   }
+  return CDI_OK;
+}
+
+// One domain's part of a sweep: the species, one potential per distinct
+// applied value (each solved as by cdi_set_potential and kept in a buffer of
+// `owner`'s, appended to phis), and each member's velocity scale, potential
+// index and time step (as cdi_set_velocity and cdi_init_transport set them).
+cdi_status prepare_sweep(cdi_domain *d, cdi_domain *owner, const cdi_combo *combos,
+                         int n_combos, const cdi_elec_params *ep, const cdi_species *sp, int n,
+                         double c0, double Ka, double *scale, int *group, double *dts,
+                         std::vector<void *> &phis) {
   // the sweep replaces the domain's potential and transport state
   d->np_ready = false;
   d->ns = n;
@@ -439,14 +438,8 @@ cdi_status cdi_sweep_transport(cdi_domain *d, const cdi_combo *combos, int n_com
   }
   d->c0 = c0;
   d->Ka = Ka;
-  // one potential per distinct applied value, each solved as by
-  // cdi_set_potential; each member's velocity scale and time step as by
-  // cdi_set_velocity and cdi_init_transport
   std::vector<double> gv;
-  std::vector<int> group(n_combos);
-  std::vector<double> scale(n_combos), dts(n_combos);
-  std::vector<void *> phis;
-  cdi_status s = CDI_OK;
+  std::vector<int> local(n_combos);
   for (int m = 0; m < n_combos; m++) {
     int g = -1;
     for (size_t i = 0; i < gv.size(); i++)
@@ -455,32 +448,98 @@ cdi_status cdi_sweep_transport(cdi_domain *d, const cdi_combo *combos, int n_com
       g = (int)gv.size();
       gv.push_back(combos[m].applied_V);
     }
-    group[m] = g;
+    local[m] = g;
     scale[m] = combos[m].U_mps == 0.0 ? 0.0 : combos[m].U_mps / d->U_lat;
   }
+  const int base = (int)phis.size();
+  cdi_status s = CDI_OK;
   for (size_t g = 0; g < gv.size() && s == CDI_OK; g++) {
     s = cdi_set_potential(d, gv[g], ep, nullptr, nullptr);
     if (s != CDI_OK) break;
-    void *ph = cdi_dev_alloc(d, (size_t)d->N * 8);
+    void *ph = cdi_dev_alloc(owner, (size_t)d->n_pore * 8);
     if (!ph) {
       s = cdi_fail(d, CDI_ERR_OOM, "sweep: potential buffer");
       break;
     }
     phis.push_back(ph);
-    cudaError_t e = cudaMemcpyAsync(ph, d->d_phi, (size_t)d->N * 8, cudaMemcpyDeviceToDevice,
-                                    d->stream);
+    cudaError_t e = cudaMemcpyAsync(ph, d->d_phi, (size_t)d->n_pore * 8,
+                                    cudaMemcpyDeviceToDevice, d->stream);
     if (e != cudaSuccess) s = cdi_cuda_fail(d, e, "sweep: potential copy");
     for (int m = 0; m < n_combos && s == CDI_OK; m++)
-      if (group[m] == (int)g) s = cdi_np_dt(d, scale[m], &dts[m]);
+      if (local[m] == (int)g) s = cdi_np_dt(d, scale[m], &dts[m]);
   }
+  for (int m = 0; m < n_combos; m++) group[m] = base + local[m];
+  d->psi_done = false;  // the domain's potential is the last group's
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+cdi_status cdi_sweep_transport(cdi_domain *d, const cdi_combo *combos, int n_combos,
+                               const cdi_elec_params *ep, const cdi_species *sp, int n,
+                               double c0, double Ka, int64_t n_steps, double *gamma_out,
+                               double *cout_out, double *dt_out) {
+  if (!d || !gamma_out || !cout_out) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  cdi_status s = check_sweep_args(d, combos, n_combos, ep, sp, n, c0, Ka, n_steps);
+  if (s != CDI_OK) return s;
+  std::vector<int> group(n_combos);
+  std::vector<double> scale(n_combos), dts(n_combos);
+  std::vector<void *> phis;
+  s = prepare_sweep(d, d, combos, n_combos, ep, sp, n, c0, Ka, scale.data(), group.data(),
+                    dts.data(), phis);
   if (s == CDI_OK)
     s = cdi_np_sweep(d, n_combos, scale.data(), group.data(), phis.data(), dts.data(), n_steps,
                      gamma_out, cout_out);
   cudaStreamSynchronize(d->stream);
   for (void *p : phis) cdi_dev_release(d, p);
-  d->psi_done = false;  // the domain's potential is the last group's
   if (s == CDI_OK && dt_out)
     for (int m = 0; m < n_combos; m++) dt_out[m] = dts[m];
+  return s;
+}
+
+cdi_status cdi_sweep_batch(cdi_domain *const *doms, int n_doms, const cdi_combo *combos,
+                           int n_combos, const cdi_elec_params *ep, const cdi_species *sp,
+                           int n, double c0, double Ka, int64_t n_steps, double *gamma_out,
+                           double *cout_out, double *dt_out) {
+  if (!doms || n_doms < 1 || !doms[0])
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "batch: no domains");
+  cdi_domain *L = doms[0];
+  if (!gamma_out || !cout_out) return cdi_fail(L, CDI_ERR_INVALID_ARG, "NULL argument");
+  if ((int64_t)n_doms * n_combos > (1 << 20))
+    return cdi_fail(L, CDI_ERR_INVALID_ARG, "batch: at most 2^20 members");
+  int64_t blocks = 0;
+  for (int i = 0; i < n_doms; i++) {
+    if (!doms[i]) return cdi_fail(L, CDI_ERR_INVALID_ARG, "batch: NULL domain");
+    if (doms[i]->dim != L->dim || doms[i]->prec != L->prec)
+      return cdi_fail(L, CDI_ERR_INVALID_ARG, "batch: domains differ in dimension or precision");
+    for (int j = 0; j < i; j++)
+      if (doms[j] == doms[i]) return cdi_fail(L, CDI_ERR_INVALID_ARG, "batch: repeated domain");
+    cdi_status s = check_sweep_args(doms[i], combos, n_combos, ep, sp, n, c0, Ka, n_steps);
+    if (s != CDI_OK) return cdi_fail(L, s, std::string("batch: ") + doms[i]->err);
+    blocks += (int64_t)doms[i]->np_blocks * n_combos;
+  }
+  if (blocks > 0x7fffffff) return cdi_fail(L, CDI_ERR_INVALID_ARG, "batch: too many blocks");
+  const int nm = n_doms * n_combos;
+  std::vector<int> group(nm);
+  std::vector<double> scale(nm), dts(nm);
+  std::vector<void *> phis;
+  cdi_status s = CDI_OK;
+  for (int i = 0; i < n_doms && s == CDI_OK; i++) {
+    s = prepare_sweep(doms[i], L, combos, n_combos, ep, sp, n, c0, Ka, scale.data() + i * n_combos,
+                      group.data() + i * n_combos, dts.data() + i * n_combos, phis);
+    if (s != CDI_OK && doms[i] != L) cdi_fail(L, s, std::string("batch: ") + doms[i]->err);
+    if (s == CDI_OK && cudaStreamSynchronize(doms[i]->stream) != cudaSuccess)
+      s = cdi_fail(L, CDI_ERR_CUDA, "batch: potential");
+  }
+  if (s == CDI_OK)
+    s = cdi_np_batch(doms, n_doms, n_combos, scale.data(), group.data(), phis.data(), dts.data(),
+                     n_steps, gamma_out, cout_out);
+  cudaStreamSynchronize(L->stream);
+  for (void *p : phis) cdi_dev_release(L, p);
+  if (s == CDI_OK && dt_out)
+    for (int m = 0; m < nm; m++) dt_out[m] = dts[m];
   return s;
 }
 
@@ -551,39 +610,39 @@ cdi_status cdi_query_column_means(cdi_domain *d, int species, double *out) {
 
 cdi_status cdi_copy_field(cdi_domain *d, int field, double *host, size_t count) {
   if (!d || !host) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
-  const int isf = d->prec != CDI_FP64;
-  const size_t T = isf ? 4 : 8;
+  const size_t T = d->prec == CDI_FP64 ? 8 : 4;
   const void *src = nullptr;
-  size_t n = 0;
+  int comps = 0;
   double *tmp = d->d_cg;  // 4*N doubles of scratch outside a potential solve
   if (field == CDI_FIELD_U_LATTICE) {
-    n = (size_t)d->dim * d->Nf;
+    const size_t n = (size_t)d->dim * d->Nf;
     if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
     CDI_TRY(d, cudaMemcpyAsync(host, d->d_uflow, n * 8, cudaMemcpyDeviceToHost, d->stream),
             "copy u lattice");
     CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");
     return CDI_OK;
-  } else if (field == CDI_FIELD_U) {
-    n = (size_t)d->dim * d->N;
-    src = d->d_u;
   } else if (field == CDI_FIELD_PSI) {
-    n = (size_t)d->N;
+    const size_t n = (size_t)d->N;
     if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
     CDI_TRY(d, cudaMemcpyAsync(host, d->d_psi, n * 8, cudaMemcpyDeviceToHost, d->stream),
             "copy psi");
     CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");
     return CDI_OK;
+  } else if (field == CDI_FIELD_U) {
+    comps = d->dim;
+    src = d->d_u;
   } else if (field >= CDI_FIELD_C && field < CDI_FIELD_C + cdi::kMaxSpecies) {
     int k = field - CDI_FIELD_C;
     if (!d->np_ready || k >= d->ns) return cdi_fail(d, CDI_ERR_STATE, "no such species state");
-    n = (size_t)d->N;
-    src = (const char *)d->d_C[d->cur] + (size_t)k * d->N * T;
+    comps = 1;
+    src = (const char *)d->d_C[d->cur] + (size_t)k * d->n_pore * T;
   } else {
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "unknown field");
   }
+  // rank-ordered transport field -> lattice order (0 in solid cells)
+  const size_t n = (size_t)comps * d->N;
   if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
-  if (n > (size_t)4 * d->N) return cdi_fail(d, CDI_ERR_INVALID_ARG, "field too large");
-  cdi_status s = cdi_convert_to_double(d, src, isf, tmp, n);
+  cdi_status s = cdi_np_scatter(d, src, comps, tmp);
   if (s != CDI_OK) return s;
   CDI_TRY(d, cudaMemcpyAsync(host, tmp, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy field");
   CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");

@@ -174,6 +174,18 @@ template <> struct PhiStore<float> {
   __device__ static float2 zero() { return make_float2(0.f, 0.f); }
 };
 
+// Arithmetic with explicit rounding (never contracted into FMAs by the
+// compiler, so two kernels that inline the same function compute the same
+// bits).
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // Bernoulli function pair B(x), B(-x) with B(x) = x / (exp(x) - 1), from one
 // expm1 of |x|: B(|x|) directly (series near 0) and B(-|x|) = B(|x|) + |x|,
 // both positive so neither loses precision.
@@ -182,12 +194,13 @@ __device__ __forceinline__ void bernoulli_pair(T x, T &Bx, T &Bmx) {
   const T a = fabs(x);
   T Ba;
   if (a < T(1e-3)) {
-    const T a2 = a * a;
-    Ba = T(1) - a * T(0.5) + a2 * (T(1) / T(12)) - a2 * a2 * (T(1) / T(720));
+    // 1 - a/2 + a^2/12 - a^4/720
+    const T a2 = r_mul(a, a);
+    Ba = r_fma(a2, r_fma(a2, T(-1) / T(720), T(1) / T(12)), r_fma(a, T(-0.5), T(1)));
   } else {
     Ba = a / expm1(a);
   }
-  const T Bma = Ba + a;
+  const T Bma = r_add(Ba, a);
   if (x >= T(0)) {
     Bx = Ba;
     Bmx = Bma;
@@ -231,16 +244,24 @@ struct cdi_domain {
   int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
   int *d_nbr = nullptr;         // (Q-1)*n_flow_pore neighbour ranks (-1: solid)
   long long n_flow_pore = 0;
-  int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending
+  int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending:
+                                // entry r is the lattice cell of pore rank r
+  uint2 *d_cmeta = nullptr;     // n_pore: {face flags | x << 16, row = z*ny + y}
+  uint2 *d_words = nullptr;     // ny*nz*W: per 32 cells of a row {rank of the
+                                // first pore cell at or after it, pore bits}
+  int W = 0;                    // words per row, ceil(nx / 32)
   void *d_g = nullptr;          // Q*n_flow_pore populations (shifted) by pore rank
   float *d_glo = nullptr;       // their low parts (pair storage only)
   double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64
-  void *d_u = nullptr;          // dim*N scaled velocity, precision T
-  double *d_psi = nullptr;      // N potential (V), FP64
-  void *d_phi = nullptr;        // N psi / V_T, 8 bytes a cell: double (FP64)
-                                // or a float2 (hi, lo) pair (FP32)
-  void *d_C[2] = {nullptr, nullptr};  // ns*N concentrations, ping-pong, T
-  double *d_acc = nullptr;      // 3*kMaxSpecies*np_blocks per-block sums
+  // transport fields by pore rank (component a / species k of rank r at
+  // a * n_pore + r)
+  void *d_u = nullptr;          // dim*n_pore scaled velocity, precision T
+  double *d_psi = nullptr;      // N potential (V), FP64, lattice order
+  void *d_phi = nullptr;        // n_pore psi / V_T, 8 bytes a cell: double
+                                // (FP64) or a float2 (hi, lo) pair (FP32)
+  void *d_C[2] = {nullptr, nullptr};  // kMaxSpecies*n_pore concentrations,
+                                      // ping-pong, T
+  double *d_acc = nullptr;      // 3*kMaxSpecies*np_accs per-warp sums
   double *d_part = nullptr;     // reduction partials (8*kRedBlocks)
   unsigned int *d_counter = nullptr;  // last-block counters (8 slots)
   double *d_scal = nullptr;     // device scalars (64)
@@ -261,7 +282,8 @@ struct cdi_domain {
   double c0 = 0.0, Ka = 0.0, dt = 0.0, VT = 0.0;
   int cur = 0;                  // which of d_C holds the current state
   int64_t np_steps = 0;
-  int np_blocks = 0;
+  int np_blocks = 0;            // blocks of a transport step launch
+  int np_accs = 0;              // their warps: one account set each
 
   // graphs
   cudaGraphExec_t flow_graph = nullptr;
@@ -328,16 +350,19 @@ cdi_status cdi_flow_velocity_lattice(cdi_domain *d);
 cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol,
                          int max_iter, int *iters, double *relres);
 cdi_status cdi_np_build_flags(cdi_domain *d);
+cdi_status cdi_np_build_compact(cdi_domain *d);
+cdi_status cdi_np_scatter(cdi_domain *d, const void *src, int comps, double *dst);
 cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used);
 cdi_status cdi_np_dt(cdi_domain *d, double scale, double *dt_out);
 cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces);
 cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *group,
                         void *const *phi_groups, const double *dts, int64_t n_steps,
                         double *gamma, double *cout);
+cdi_status cdi_np_batch(cdi_domain *const *doms, int n_doms, int n_combos, const double *scale,
+                        const int *group, void *const *phis, const double *dts, int64_t n_steps,
+                        double *gamma, double *cout);
 cdi_status cdi_flow_scale_to(cdi_domain *d, double scale, void *dst);
 void cdi_dev_release(cdi_domain *d, void *p);
 cdi_status cdi_np_steps(cdi_domain *d, int64_t n);
 cdi_status cdi_np_reduce(cdi_domain *d);
 cdi_status cdi_np_column_means(cdi_domain *d, int species);
-cdi_status cdi_convert_to_double(cdi_domain *d, const void *src, int is_float,
-                                 double *dst, size_t n);

@@ -12,10 +12,14 @@
 // would enter a solid site (or cross a lateral wall) returns to its source
 // in the opposite direction within the same step.
 //
-// Three storage modes: FP64; FP32; and FP32 pairs (hi + lo in two arrays,
+// Four storage modes: FP64; FP32; FP32 pairs (hi + lo in two arrays,
 // updated with error-free FP32 transformations: FP64-class accuracy at FP32
-// arithmetic rates, which matters on a part whose FP64 rate is low).
+// arithmetic rates, which matters on a part whose FP64 rate is low); and BF16
+// (collision in FP32, half the bytes of FP32, low accuracy).
 #include <cmath>
+#include <type_traits>
+
+#include <cuda_bf16.h>
 
 #include "cdi_internal.cuh"
 
@@ -23,7 +27,20 @@ using namespace cdi;
 
 namespace {
 
-enum Mode { M_F64 = 0, M_F32 = 1, M_SPLIT = 2 };
+enum Mode { M_F64 = 0, M_F32 = 1, M_SPLIT = 2, M_BF16 = 3 };
+
+// Arithmetic type of a population storage type (BF16 is widened to FP32).
+template <typename S> struct Arith { using type = S; };
+template <> struct Arith<__nv_bfloat16> { using type = float; };
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ double widen(double v) { return v; }
+template <typename S> __device__ __forceinline__ S narrow(typename Arith<S>::type v) {
+  return (S)v;
+}
+template <> __device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
 
 // ---------------------------------------------------------------------------
 // Error-free FP32 transformations (Knuth's two-sum, Dekker's fast two-sum,
@@ -182,16 +199,18 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 }
 
 // One full lattice Boltzmann step (stream + collide) at every pore site,
-// FP64 or FP32 storage.  Collision (Eq. 8) with the Stokes-linear
+// FP64, FP32 or BF16 storage (S), arithmetic in T = Arith<S>.  Collision (Eq. 8) with the Stokes-linear
 // equilibrium g_eq_i = w_i (drho + 3 e_i.j), j = sum e_i g_i + F/2, and the
 // force source (1 - 1/(2 tau)) 3 w_i e_i.F; omega = 1/tau.
 // (more resident blocks per SM: the step is latency-bound on its scattered
 // loads, so occupancy matters more than a few spare registers; the bound is
 // chosen per variant so that nothing spills)
-template <typename T, int DIM, bool ODD>
-__global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(T) == 4 ? 7 : 4))
-    k_lbm_step(T *__restrict__ g, const int *__restrict__ nbr, int n, T omega, T fx_half,
-               T fsrc) {
+template <typename S, int DIM, bool ODD>
+__global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7))
+    k_lbm_step(S *__restrict__ g, const int *__restrict__ nbr, int n,
+               typename Arith<S>::type omega, typename Arith<S>::type fx_half,
+               typename Arith<S>::type fsrc) {
+  using T = typename Arith<S>::type;
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,7 +219,7 @@ __global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(T) == 4 ? 7 
   load_links<DIM, ODD>(nbr, k0, n, nb);
   T gi[Q];
 #pragma unroll
-  for (int i = 0; i < Q; i++) gi[i] = g[read_slot<DIM, ODD>(nb, k0, i, n)];
+  for (int i = 0; i < Q; i++) gi[i] = widen(g[read_slot<DIM, ODD>(nb, k0, i, n)]);
   T drho = T(0), jx = fx_half, jy = T(0), jz = T(0);
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -216,7 +235,7 @@ __global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(T) == 4 ? 7 
     const T geq = T(L::w(i)) * (drho + T(3) * eu);
     go[i] = gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
   }
-  if (sizeof(T) == 4) {
+  if (std::is_same<S, float>::value) {
     // FP32 storage: the collision conserves mass exactly, but rounding the
     // stored values does not, and the leak is biased; it feeds the slowest
     // (pressure-diffusion) modes of the porous flow.  The rest population
@@ -230,7 +249,7 @@ __global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(T) == 4 ? 7 
     go[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
   }
 #pragma unroll
-  for (int i = 0; i < Q; i++) g[write_slot<DIM, ODD>(nb, k0, i, n)] = go[i];
+  for (int i = 0; i < Q; i++) g[write_slot<DIM, ODD>(nb, k0, i, n)] = narrow<S>(go[i]);
 }
 
 // Constants of the pair collision, each an unevaluated FP32 pair.
@@ -336,14 +355,14 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const long long s = list[k];  // populations by rank k, velocity by site s
     double j[3] = {fx_half, 0.0, 0.0};
-    if (sizeof(T) == 4) {
+    if (!std::is_same<T, double>::value) {
       // exact sums of the FP32 values as (sum, error) pairs: the residual
       // resolves changes far below FP32's relative precision, and FP64 adds
       // are slow on this part
       float ms[3] = {0.f, 0.f, 0.f}, mc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 1; i < L::Q; i++) {
-        const float gv = (float)g[(size_t)i * n + k];
+        const float gv = (float)widen(g[(size_t)i * n + k]);
         const float lv = glo ? glo[(size_t)i * n + k] : 0.f;
         if (L::ex(i)) {
           two_sum_acc(L::ex(i) > 0 ? gv : -gv, ms[0], mc[0]);
@@ -363,7 +382,7 @@ __global__ void __launch_bounds__(kRedThreads)
     } else {
 #pragma unroll
       for (int i = 0; i < L::Q; i++) {
-        const double gv = (double)g[(size_t)i * n + k];
+        const double gv = (double)widen(g[(size_t)i * n + k]);
         j[0] += L::ex(i) * gv;
         j[1] += L::ey(i) * gv;
         if (DIM == 3) j[2] += L::ez(i) * gv;
@@ -421,27 +440,27 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// u_phys = scale * u_lattice on the transport grid (0 in solid cells); the
-// scale is scal[S_SCALE], or sc_arg when scal is null.
+// u_phys = scale * u_lattice at every pore rank of the transport grid
+// (component a of rank r at a * n + r); the scale is scal[S_SCALE], or sc_arg
+// when scal is null.
 template <typename T, int DIM>
-__global__ void k_flow_scale(const double *__restrict__ uflow, const uint8_t *__restrict__ mask,
-                             T *__restrict__ u, int nx, int NX, long long N, long long Nf,
+__global__ void k_flow_scale(const double *__restrict__ uflow, const int *__restrict__ cells,
+                             int n, T *__restrict__ u, int nx, int NX, long long Nf,
                              const double *__restrict__ scal, double sc_arg) {
   const double sc = scal ? scal[S_SCALE] : sc_arg;
-  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
-       P += (long long)gridDim.x * blockDim.x) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const long long P = cells[r];
     const long long row = P / nx;
-    const int x = (int)(P - row * nx);
-    const long long s = row * NX + x;
+    const long long s = row * NX + (P - row * nx);
 #pragma unroll
-    for (int a = 0; a < DIM; a++)
-      u[(size_t)a * N + P] = mask[P] ? T(0) : (T)(sc * uflow[(size_t)a * Nf + s]);
+    for (int a = 0; a < DIM; a++) u[(size_t)a * n + r] = (T)(sc * uflow[(size_t)a * Nf + s]);
   }
 }
 
 // Storage type of the populations per mode.
 template <int M> struct ModeT { using T = float; };
 template <> struct ModeT<M_F64> { using T = double; };
+template <> struct ModeT<M_BF16> { using T = __nv_bfloat16; };
 
 template <int M, int DIM>
 void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
@@ -467,8 +486,9 @@ void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) 
           (float *)d->d_g, d->d_glo, nbr, n, c);
     }
   } else {
-    const T omega = T(1.0 / tau), fxh = T(0.5 * force);
-    const T fsrc = T((1.0 - 0.5 / tau) * 3.0 * force);
+    using A = typename Arith<T>::type;
+    const A omega = A(1.0 / tau), fxh = A(0.5 * force);
+    const A fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
     k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>((T *)d->d_g, nbr, n, omega, fxh,
                                                            fsrc);
     k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>((T *)d->d_g, nbr, n, omega, fxh,
@@ -561,7 +581,8 @@ cdi_status flow_export(cdi_domain *d, double U_target) {
       d->d_uflow, d->d_mask, d->nx, d->NX, d->N, (double)d->n_pore, U_target, d->d_part,
       d->d_counter + C_ULAT, d->d_scal);
   k_flow_scale<T, DIM><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-      d->d_uflow, d->d_mask, (T *)d->d_u, d->nx, d->NX, d->N, d->Nf, d->d_scal, 0.0);
+      d->d_uflow, d->d_cell_list, (int)d->n_pore, (T *)d->d_u, d->nx, d->NX, d->Nf, d->d_scal,
+      0.0);
   d->timing.kernel_launches += 2;
   CDI_TRY(d, cudaGetLastError(), "velocity export");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_ULAT, d->d_scal + S_ULAT, 2 * sizeof(double),
@@ -619,6 +640,9 @@ cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
       return d->dim == 2 ? flow_run<M_F64, 2>(d, p, steps, res) : flow_run<M_F64, 3>(d, p, steps, res);
     case CDI_FP32:
       return d->dim == 2 ? flow_run<M_F32, 2>(d, p, steps, res) : flow_run<M_F32, 3>(d, p, steps, res);
+    case CDI_BF16_POP:
+      return d->dim == 2 ? flow_run<M_BF16, 2>(d, p, steps, res)
+                         : flow_run<M_BF16, 3>(d, p, steps, res);
     default:
       return d->dim == 2 ? flow_run<M_SPLIT, 2>(d, p, steps, res)
                          : flow_run<M_SPLIT, 3>(d, p, steps, res);
@@ -629,17 +653,21 @@ cdi_status cdi_flow_scale_to(cdi_domain *d, double scale, void *dst) {
   if (d->prec == CDI_FP64) {
     if (d->dim == 2)
       k_flow_scale<double, 2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-          d->d_uflow, d->d_mask, (double *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+          d->d_uflow, d->d_cell_list, (int)d->n_pore, (double *)dst, d->nx, d->NX, d->Nf, nullptr,
+          scale);
     else
       k_flow_scale<double, 3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-          d->d_uflow, d->d_mask, (double *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+          d->d_uflow, d->d_cell_list, (int)d->n_pore, (double *)dst, d->nx, d->NX, d->Nf, nullptr,
+          scale);
   } else {
     if (d->dim == 2)
       k_flow_scale<float, 2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-          d->d_uflow, d->d_mask, (float *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+          d->d_uflow, d->d_cell_list, (int)d->n_pore, (float *)dst, d->nx, d->NX, d->Nf, nullptr,
+          scale);
     else
       k_flow_scale<float, 3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-          d->d_uflow, d->d_mask, (float *)dst, d->nx, d->NX, d->N, d->Nf, nullptr, scale);
+          d->d_uflow, d->d_cell_list, (int)d->n_pore, (float *)dst, d->nx, d->NX, d->Nf, nullptr,
+          scale);
   }
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "velocity scale");

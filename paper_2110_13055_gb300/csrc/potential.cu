@@ -204,13 +204,12 @@ __global__ void k_cg_dir(long long N, double *__restrict__ p, const double *__re
     p[P] = zq[P] + beta * p[P];
 }
 
-// phi = psi / V_T (0 in solid cells) in the transport kernel's format.
+// phi = psi / V_T of every pore rank, in the transport kernel's format.
 template <typename T>
-__global__ void k_phi(long long N, const NFlag *__restrict__ fl, const double *__restrict__ psi,
+__global__ void k_phi(int n, const int *__restrict__ cells, const double *__restrict__ psi,
                       typename PhiStore<T>::type *__restrict__ phi, double inv_vt) {
-  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
-       P += (long long)gridDim.x * blockDim.x)
-    phi[P] = (fl[P] & 1) ? PhiStore<T>::zero() : PhiStore<T>::make(psi[P] * inv_vt);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    phi[r] = PhiStore<T>::make(psi[cells[r]] * inv_vt);
 }
 
 }  // namespace
@@ -256,11 +255,11 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol, i
   // of phi into a relative error of C.
   const double inv_vt = 1.0 / d->VT;
   if (d->prec == CDI_FP64)
-    k_phi<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->N, d->d_nflags, d->d_psi,
-                                                             (double *)d->d_phi, inv_vt);
+    k_phi<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (int)d->n_pore, d->d_cell_list, d->d_psi, (double *)d->d_phi, inv_vt);
   else
-    k_phi<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->N, d->d_nflags, d->d_psi,
-                                                            (float2 *)d->d_phi, inv_vt);
+    k_phi<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (int)d->n_pore, d->d_cell_list, d->d_psi, (float2 *)d->d_phi, inv_vt);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "phi");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_CG_REL, d->d_scal + S_CG_REL, 4 * sizeof(double),

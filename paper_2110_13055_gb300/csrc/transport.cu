@@ -87,157 +87,212 @@ __device__ __forceinline__ int np_face(unsigned f, int fc, int nx, int ny, int n
   return F_PORE;
 }
 
-// B(P_f) and B(-P_f) for the face Peclet number P_f = adv - z (phi_nb - phi_P).
-template <typename T> struct FaceB;
-
-template <> struct FaceB<double> {
-  __device__ static void dphi(double nb, double p, double &hi, double &lo) {
-    hi = nb - p;
-    lo = 0.0;
-  }
-  __device__ static void eval(double adv, double z, double dhi, double, double &Bp,
-                              double &Bm) {
-    bernoulli_pair(adv - z * dhi, Bp, Bm);
-  }
-};
-
-// FP32 carries the potential difference and P_f as unevaluated pairs
-// (hi + lo): an exponent |P| rounded to FP32 costs a relative error of about
-// |P| * 6e-8 in each Boltzmann factor exp(P), which accumulates across an
-// electric double layer.  B is evaluated at hi and corrected to first order
-// in lo with B'(x) = B(x) ((1 - B(x)) / x - 1).
-template <> struct FaceB<float> {
-  __device__ static void dphi(float2 nb, float2 p, float &hi, float &lo) {
-    const float d = __fsub_rn(nb.x, p.x);
-    const float bv = __fsub_rn(d, nb.x);
-    const float e = __fadd_rn(__fsub_rn(nb.x, __fsub_rn(d, bv)), __fsub_rn(-p.x, bv));
-    hi = d;
-    lo = __fadd_rn(e, __fsub_rn(nb.y, p.y));
-  }
-  __device__ static void eval(float adv, float z, float dhi, float dlo, float &Bp, float &Bm) {
-    const float p = __fmaf_rn(-z, dhi, adv);
-    const bool neg = p < 0.f;
-    float Ba, Bma;
-    if (fabsf(p) < 0.5f) {
-      // Almost every face: B(a) from its Taylor series (Bernoulli numbers)
-      // through a^8, truncation below 3e-11 for a < 1/2.  Dropping the low
-      // part of P shifts B by less than 4e-8 relative here.
-      const float a = fabsf(p), a2 = a * a;
-      float t = __fmaf_rn(-1.f / 1209600.f, a2, 1.f / 30240.f);
-      t = __fmaf_rn(t, a2, -1.f / 720.f);
-      t = __fmaf_rn(t, a2, 1.f / 12.f);
-      Ba = __fmaf_rn(t, a2, __fmaf_rn(-0.5f, a, 1.f));
-      Bma = Ba + a;
-    } else {
-      // P = adv - z (dhi + dlo) as ph + pl, B at |ph| corrected for pl
-      const float zd = __fmul_rn(z, dhi);
-      const float zde = __fmaf_rn(z, dhi, -zd);
-      const float ph = __fsub_rn(adv, zd);
-      const float bb = __fsub_rn(ph, adv);
-      const float phe = __fadd_rn(__fsub_rn(adv, __fsub_rn(ph, bb)), __fsub_rn(-zd, bb));
-      const float pl = __fsub_rn(__fsub_rn(phe, zde), __fmul_rn(z, dlo));
-      const float ah = neg ? -ph : ph, al = neg ? -pl : pl;
-      // B(a) = a e^-a / (1 - e^-a) is below 1e-33 beyond a = 80
-      Ba = ah > 80.f ? 0.f : __fdividef(ah, expm1f(ah));
-      Ba = __fmaf_rn(Ba * al, __fdividef(1.f - Ba, ah) - 1.f, Ba);
-      Bma = (Ba + ah) + al;  // B(-a) = B(a) + a, no cancellation
-    }
-    Bp = neg ? Bma : Ba;
-    Bm = neg ? Ba : Bma;
-  }
-};
-
-// One explicit step of one pore cell P for NS species: writes the new
-// concentrations and adds the cell's adsorbed (v[k]), inflow (v[NS+k]) and
-// outflow (v[2NS+k]) fluxes.
-template <typename T, int DIM, int NS>
-__device__ __forceinline__ void np_cell(const T *__restrict__ Cin, T *__restrict__ Cout,
-                                        const T *__restrict__ u,
-                                        const typename PhiStore<T>::type *__restrict__ phi,
-                                        unsigned f, const NPConst<T> &c, int nx, int ny, int nz,
-                                        long long N, int walls, long long P, T (&v)[3 * NS]) {
-  using PS = PhiStore<T>;
-  using PT = typename PS::type;
-  constexpr int NF = 2 * DIM;
-  // face kinds and neighbour cells first (32-bit indices: N < 2^31); a
-  // non-pore face stands in the own cell, whose values an outlet ghost copies
-  const int Pi = (int)P;
-  int kind[NF], Qi[NF];
-#pragma unroll
-  for (int fc = 0; fc < NF; fc++) {
-    long long Q = P;
-    kind[fc] = np_face<DIM>(f, fc, nx, ny, nz, walls, P, Q);
-    Qi[fc] = kind[fc] == F_PORE ? (int)Q : Pi;
-  }
-  // every load issued before any arithmetic (memory-level parallelism)
-  T CP[NS], sumJ[NS], un[NF], Cn[NF][NS];
-  PT phn[NF];
-#pragma unroll
-  for (int k = 0; k < NS; k++) {
-    CP[k] = Cin[(size_t)k * N + Pi];
-    sumJ[k] = T(0);
-  }
-  const PT phiP = phi[Pi];
-  T uP[DIM];
-#pragma unroll
-  for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * N + Pi];
-#pragma unroll
-  for (int fc = 0; fc < NF; fc++) {
-    un[fc] = u[(size_t)(fc >> 1) * N + Qi[fc]];
-    phn[fc] = phi[Qi[fc]];
-#pragma unroll
-    for (int k = 0; k < NS; k++) Cn[fc][k] = Cin[(size_t)k * N + Qi[fc]];
-  }
-#pragma unroll
-  for (int fc = 0; fc < NF; fc++) {
-    const int a = fc >> 1;
-    const T sg = (fc & 1) ? T(-1) : T(1);
-    if (kind[fc] == F_WALL) continue;
-    if (kind[fc] == F_SOLID) {
-#pragma unroll
-      for (int k = 0; k < NS; k++) {
-        const T J = c.Keff[k] * CP[k];
-        sumJ[k] += J;
-        v[k] += J;
-      }
-      continue;
-    }
-    if (kind[fc] == F_INLET) {  // feed ghost: C = c0, phi = 0, u = u_P
-      phn[fc] = PS::zero();
-#pragma unroll
-      for (int k = 0; k < NS; k++) Cn[fc][k] = c.c0;
-    }
-    const T uf = T(0.5) * (uP[a] + un[fc]) * sg;
-    T dhi, dlo;
-    FaceB<T>::dphi(phn[fc], phiP, dhi, dlo);
-#pragma unroll
-    for (int k = 0; k < NS; k++) {
-      T Bp, Bm;
-      FaceB<T>::eval(uf * c.dxD[k], c.zf[k], dhi, dlo, Bp, Bm);
-      const T J = c.Ddx[k] * (Bm * CP[k] - Bp * Cn[fc][k]);
-      sumJ[k] += J;
-      if (kind[fc] == F_INLET) v[NS + k] -= J;
-      if (kind[fc] == F_OUTLET) v[2 * NS + k] += J;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NS; k++) Cout[(size_t)k * N + Pi] = CP[k] - c.dtdx * sumJ[k];
+// Pore rank of the pore lattice cell (x, row): the rank of the first pore
+// cell of its 32-cell word plus the pore cells before it in that word.
+__device__ __forceinline__ int rank_of(const uint2 *__restrict__ words, int W, int row, int x) {
+  const uint2 t = __ldg(words + (size_t)row * W + (x >> 5));
+  return (int)t.x + __popc(t.y & ((1u << (x & 31)) - 1u));
 }
 
-// Block sums of v in T, added by thread 0 to the block's own FP64 accounts
-// acc[(3*k + kind) * gridDim.x + block], kind 0 Gamma, 1 In, 2 Out (one
-// thread per pore cell, so the block -> cells map is fixed and the totals are
-// deterministic).  Every thread of the block must call it.
-template <typename T, int NS>
-__device__ __forceinline__ void np_account(T (&v)[3 * NS], T *sm, double *__restrict__ acc) {
-  block_reduce<3 * NS>(v, sm, OpSum(), T(0));
-  if (threadIdx.x == 0) {
-    const int bid = blockIdx.x, nblocks = gridDim.x;
+// Row of the lateral (y: a = 1, z: a = 2) neighbour across face fc; rows wrap
+// periodically (a wall face is never asked).  row = z * ny + y.
+__device__ __forceinline__ int lateral_row(unsigned f, int fc, int row, int ny, int nz) {
+  const int s = (fc & 1) ? -1 : 1;
+  const bool edge = (f >> (kEdgeBit + fc)) & 1u;
+  const int step = (fc >> 1) == 1 ? 1 : ny;
+  const int ext = (fc >> 1) == 1 ? ny : nz;
+  return row + (edge ? -s * (ext - 1) * step : s * step);
+}
+
+// Face flux divided by D/dx, J' = B(-P) C_P - B(P) C_nb, for the face Peclet
+// number P = adv - z (phi_nb - phi_P); dd is phi_nb - phi_P.
+__device__ __forceinline__ double face_flux(double adv, double z, double dd, double, double,
+                                            double CP, double Cn) {
+  double Bp, Bm;
+  bernoulli_pair(r_fma(-z, dd, adv), Bp, Bm);
+  return r_fma(Bm, CP, -r_mul(Bp, Cn));
+}
+
+// FP32: phi and P are carried as unevaluated pairs (hi + lo) where it
+// matters: an exponent |P| rounded to FP32 costs a relative error of about
+// |P| * 6e-8 in each Boltzmann factor exp(P), which accumulates across an
+// electric double layer.
+//  * |P| < 1/2 (almost every face): with the even function
+//      E(P) = B(P) + P/2 = (P/2) coth(P/2) = 1 + P^2/12 - P^4/720 + P^6/30240 - ...
+//    (Bernoulli numbers; the next term is below 3.3e-9 here),
+//      J' = E (C_P - C_nb) + (P/2) (C_P + C_nb),
+//    a sum of two small, accurately rounded terms.
+//  * otherwise: B at the high part of |P| from expm1, corrected to first
+//    order in the low part with B'(x) = B(x) ((1 - B(x)) / x - 1), and
+//    B(-a) = B(a) + a; J' = B(-P) C_P - B(P) C_nb, each product accurate.
+__device__ __noinline__ void bernoulli_pair_split(float adv, float z, float2 nb, float2 pp,
+                                                  float &Bp, float &Bm) {
+  // phi_nb - phi_P as dhi + dlo (two-sum of the high parts plus the lows)
+  const float d = __fsub_rn(nb.x, pp.x);
+  const float bv = __fsub_rn(d, nb.x);
+  const float e = __fadd_rn(__fsub_rn(nb.x, __fsub_rn(d, bv)), __fsub_rn(-pp.x, bv));
+  const float dhi = d, dlo = __fadd_rn(e, __fsub_rn(nb.y, pp.y));
+  // P = adv - z (dhi + dlo) as ph + pl
+  const float zd = __fmul_rn(z, dhi);
+  const float zde = __fmaf_rn(z, dhi, -zd);
+  const float ph = __fsub_rn(adv, zd);
+  const float bb = __fsub_rn(ph, adv);
+  const float phe = __fadd_rn(__fsub_rn(adv, __fsub_rn(ph, bb)), __fsub_rn(-zd, bb));
+  const float pl = __fsub_rn(__fsub_rn(phe, zde), __fmul_rn(z, dlo));
+  const bool neg = ph < 0.f;
+  const float ah = neg ? -ph : ph, al = neg ? -pl : pl;
+  // B(a) = a e^-a / (1 - e^-a) is below 1e-33 beyond a = 80
+  float Ba = ah > 80.f ? 0.f : __fdividef(ah, expm1f(ah));
+  Ba = __fmaf_rn(__fmul_rn(Ba, al), __fsub_rn(__fdividef(__fsub_rn(1.f, Ba), ah), 1.f), Ba);
+  const float Bma = __fadd_rn(__fadd_rn(Ba, ah), al);
+  Bp = neg ? Bma : Ba;
+  Bm = neg ? Ba : Bma;
+}
+
+__device__ __forceinline__ float face_flux(float adv, float z, float dd, float2 nb, float2 pp,
+                                           float CP, float Cn) {
+  const float p = __fmaf_rn(-z, dd, adv);
+  if (fabsf(p) < 0.5f) {
+    const float p2 = __fmul_rn(p, p);
+    float E = __fmaf_rn(p2, 1.f / 30240.f, -1.f / 720.f);
+    E = __fmaf_rn(E, p2, 1.f / 12.f);
+    E = __fmaf_rn(E, p2, 1.f);
+    return __fmaf_rn(E, __fsub_rn(CP, Cn), __fmul_rn(__fmul_rn(0.5f, p), __fadd_rn(CP, Cn)));
+  }
+  float Bp, Bm;
+  bernoulli_pair_split(adv, z, nb, pp, Bp, Bm);
+  return r_fma(Bm, CP, -r_mul(Bp, Cn));
+}
+
+__device__ __forceinline__ double phi_diff(double nb, double pp) { return __dsub_rn(nb, pp); }
+__device__ __forceinline__ float phi_diff(float2 nb, float2 pp) {
+  return __fadd_rn(__fsub_rn(nb.x, pp.x), __fsub_rn(nb.y, pp.y));
+}
+
+// Geometry of the compact transport layout handed to the step kernels.
+struct NPGeo {
+  const uint2 *meta;   // per rank {flags | x << 16, row}
+  const uint2 *words;  // per 32 cells of a row {first rank, pore bits}
+  int n, W, ny, nz, walls;
+};
+
+// One explicit step of the pore cell of rank r for NS species: writes the
+// new concentrations and adds the cell's adsorbed (v[k]), inflow (v[NS+k])
+// and outflow (v[2NS+k]) fluxes.  Returns whether the cell has an inlet or
+// outlet face.
+//
+// A face that does not lead to a pore cell reads the cell's own values: the
+// outlet ghost copies the cell (J = u_x C_P), the inlet ghost then takes
+// C = c0 and phi = 0, and a solid or wall face gets u_f = 0, for which the
+// flux expression is exactly 0 (C_nb = C_P, dphi = 0); the adsorption flux of
+// the n_s solid faces, n_s K_eff C_P, is added once per cell.
+template <typename T, int DIM, int NS>
+__device__ __forceinline__ bool np_cell(const T *__restrict__ Cin, T *__restrict__ Cout,
+                                        const T *__restrict__ u,
+                                        const typename PhiStore<T>::type *__restrict__ phi,
+                                        const NPGeo &g, uint2 meta, int r, const NPConst<T> &c,
+                                        T (&v)[3 * NS]) {
+  using PT = typename PhiStore<T>::type;
+  constexpr int NF = 2 * DIM;
+  const unsigned f = meta.x & 0xffffu;
+  const int x = (int)(meta.x >> 16), row = (int)meta.y;
+  const size_t n = (size_t)g.n;
+  // neighbour ranks first (x neighbours are the adjacent ranks)
+  int Q[NF];
+  bool open[NF];
+#pragma unroll
+  for (int fc = 0; fc < NF; fc++) {
+    const bool solid = (f >> (kFaceBit + fc)) & 1u;
+    const bool edge = (f >> (kEdgeBit + fc)) & 1u;
+    if (fc < 2) {
+      open[fc] = !solid;
+      Q[fc] = (solid || edge) ? r : r + ((fc & 1) ? -1 : 1);
+    } else {
+      const bool wall = edge && g.walls;
+      open[fc] = !solid && !wall;
+      Q[fc] = open[fc] ? rank_of(g.words, g.W, lateral_row(f, fc, row, g.ny, g.nz), x) : r;
+    }
+  }
+  // every load before any arithmetic (memory-level parallelism)
+  T CP[NS], Cn[NF][NS], uP[DIM], un[NF];
+  PT phn[NF];
+#pragma unroll
+  for (int k = 0; k < NS; k++) CP[k] = Cin[k * n + r];
+#pragma unroll
+  for (int a = 0; a < DIM; a++) uP[a] = u[a * n + r];
+  const PT phP = phi[r];
+#pragma unroll
+  for (int fc = 0; fc < NF; fc++) {
+    un[fc] = u[(fc >> 1) * n + Q[fc]];
+    phn[fc] = phi[Q[fc]];
+#pragma unroll
+    for (int k = 0; k < NS; k++) Cn[fc][k] = Cin[k * n + Q[fc]];
+  }
+  // the feed ghost across the inlet face (face 1 at x = 0)
+  const bool inlet = (f >> (kEdgeBit + 1)) & 1u, outlet = (f >> kEdgeBit) & 1u;
+  if (inlet) {
+    phn[1] = PhiStore<T>::zero();
+#pragma unroll
+    for (int k = 0; k < NS; k++) Cn[1][k] = c.c0;
+  }
+  // adsorption on the solid faces (Eq. 6)
+  const T ns_solid = (T)__popc(f & (((1u << NF) - 1u) << kFaceBit));
+  T sumJ[NS];
+#pragma unroll
+  for (int k = 0; k < NS; k++) {
+    const T Ja = r_mul(r_mul(ns_solid, c.Keff[k]), CP[k]);
+    sumJ[k] = Ja;
+    v[k] = r_add(v[k], Ja);
+  }
+#pragma unroll
+  for (int fc = 0; fc < NF; fc++) {
+    const T half = (fc & 1) ? T(-0.5) : T(0.5);
+    const T uf = open[fc] ? r_mul(half, r_add(uP[fc >> 1], un[fc])) : T(0);
+    const T dd = phi_diff(phn[fc], phP);
 #pragma unroll
     for (int k = 0; k < NS; k++) {
-      acc[(size_t)(3 * k + 0) * nblocks + bid] += (double)v[k];
-      acc[(size_t)(3 * k + 1) * nblocks + bid] += (double)v[NS + k];
-      acc[(size_t)(3 * k + 2) * nblocks + bid] += (double)v[2 * NS + k];
+      const T J = r_mul(c.Ddx[k], face_flux(r_mul(uf, c.dxD[k]), c.zf[k], dd, phn[fc], phP,
+                                            CP[k], Cn[fc][k]));
+      sumJ[k] = r_add(sumJ[k], J);
+      if (fc == 1 && inlet) v[NS + k] = r_sub(v[NS + k], J);
+      if (fc == 0 && outlet) v[2 * NS + k] = r_add(v[2 * NS + k], J);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NS; k++) Cout[k * n + r] = r_fma(-c.dtdx, sumJ[k], CP[k]);
+  return inlet || outlet;
+}
+
+// Warp sums of v in T, added by lane 0 to the warp's own FP64 accounts
+// acc[(3*k + kind) * nw + wid], kind 0 Gamma, 1 In, 2 Out (one thread per
+// pore cell, so the warp -> cells map is fixed and the totals are
+// deterministic).  A warp without inlet or outlet cells skips the In/Out sums
+// (its values are 0).  No block barrier: each warp retires on its own.  All
+// 32 lanes of the warp must call it.
+template <typename T, int NS>
+__device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io, double *__restrict__ acc,
+                                           int wid, int nw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NS; k++) v[k] = r_add(v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+  const bool any_io = __any_sync(0xffffffffu, io);
+  if (any_io) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = NS; k < 3 * NS; k++)
+        v[k] = r_add(v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      double *a = acc + (size_t)(3 * k) * nw + wid;
+      a[0] = __dadd_rn(a[0], (double)v[k]);
+      if (any_io) {
+        a[nw] = __dadd_rn(a[nw], (double)v[NS + k]);
+        a[2 * (size_t)nw] = __dadd_rn(a[2 * (size_t)nw], (double)v[2 * NS + k]);
+      }
     }
   }
 }
@@ -245,20 +300,15 @@ __device__ __forceinline__ void np_account(T (&v)[3 * NS], T *sm, double *__rest
 template <typename T, int DIM, int NS>
 __global__ void __launch_bounds__(kRowBlock)
     k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
-              const typename PhiStore<T>::type *__restrict__ phi,
-              const NFlag *__restrict__ fl, const int *__restrict__ cells, int n_cells,
-              NPConst<T> c, double *__restrict__ acc, int nx, int ny, int nz, long long N,
-              int walls) {
-  __shared__ T sm[3 * NS * 32];
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+              const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
+              double *__restrict__ acc) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
   T v[3 * NS];
 #pragma unroll
   for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-  if (k0 < n_cells) {
-    const long long P = cells[k0];
-    np_cell<T, DIM, NS>(Cin, Cout, u, phi, fl[P], c, nx, ny, nz, N, walls, P, v);
-  }
-  np_account<T, NS>(v, sm, acc);
+  bool io = false;
+  if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
+  np_account<T, NS>(v, io, acc, r >> 5, gridDim.x * (kRowBlock / 32));
 }
 
 // One member of a fused sweep: its own concentrations, velocity, potential,
@@ -277,23 +327,55 @@ template <typename T> struct SweepMember {
 // equals a single run's bit for bit).
 template <typename T, int DIM, int NS>
 __global__ void __launch_bounds__(kRowBlock)
-    k_np_sweep(const SweepMember<T> *__restrict__ members, int n_members, int in,
-               const NFlag *__restrict__ fl, const int *__restrict__ cells, int n_cells, int nx,
-               int ny, int nz, long long N, int walls) {
-  __shared__ T sm[3 * NS * 32];
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const long long P = k0 < n_cells ? cells[k0] : 0;
-  const unsigned f = k0 < n_cells ? fl[P] : 1u;
+    k_np_sweep(const SweepMember<T> *__restrict__ members, int n_members, int in, NPGeo g) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint2 meta = r < g.n ? g.meta[r] : make_uint2(1u, 0u);
   for (int m = 0; m < n_members; m++) {
     const SweepMember<T> &mb = members[m];
     T v[3 * NS];
 #pragma unroll
     for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-    if (k0 < n_cells)
-      np_cell<T, DIM, NS>(mb.C[in], mb.C[1 - in], mb.u, mb.phi, f, mb.c, nx, ny, nz, N, walls,
-                          P, v);
-    np_account<T, NS>(v, sm, mb.acc);
+    bool io = false;
+    if (r < g.n)
+      io = np_cell<T, DIM, NS>(mb.C[in], mb.C[1 - in], mb.u, mb.phi, g, meta, r, mb.c, v);
+    np_account<T, NS>(v, io, mb.acc, r >> 5, gridDim.x * (kRowBlock / 32));
   }
+}
+
+// One member of a batch over several geometries: a sweep member plus its
+// geometry; blocks [block0, block0 + nblocks) of the launch are its own.
+template <typename T> struct BatchMember {
+  SweepMember<T> s;
+  NPGeo g;
+  int block0, nblocks;
+};
+
+// All members of a batch over uneven geometries advance one step in one
+// launch.  Block b of the launch belongs to the member whose block range
+// holds it (binary search over the ascending block0), and runs that member's
+// local block b - block0: the same cells, arithmetic and accounts as block
+// b - block0 of the member's single-run launch, so each member equals its
+// single run bit for bit.
+template <typename T, int DIM, int NS>
+__global__ void __launch_bounds__(kRowBlock)
+    k_np_batch(const BatchMember<T> *__restrict__ members, int n_members, int in) {
+  int lo = 0, hi = n_members - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (members[mid].block0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchMember<T> &mb = members[lo];
+  const int b = (int)blockIdx.x - mb.block0;
+  const int r = b * blockDim.x + threadIdx.x;
+  T v[3 * NS];
+#pragma unroll
+  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+  bool io = false;
+  if (r < mb.g.n)
+    io = np_cell<T, DIM, NS>(mb.s.C[in], mb.s.C[1 - in], mb.s.u, mb.s.phi, mb.g, mb.g.meta[r], r,
+                             mb.s.c, v);
+  np_account<T, NS>(v, io, mb.s.acc, r >> 5, mb.nblocks * (kRowBlock / 32));
 }
 
 // Largest outflow rate over pore cells and species, in FP64 from the FP64
@@ -358,16 +440,13 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 template <typename T>
-__global__ void k_np_init(const NFlag *__restrict__ fl, T *__restrict__ C0, T *__restrict__ C1,
-                          long long N, int ns, T c0) {
-  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
-       P += (long long)gridDim.x * blockDim.x) {
-    const bool pore = !(fl[P] & 1);
+__global__ void k_np_init(T *__restrict__ C0, T *__restrict__ C1, int n, int ns, T c0) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int k = 0; k < kMaxSpecies; k++) {
-      const T v = (pore && k < ns) ? c0 : T(0);
-      C0[(size_t)k * N + P] = v;
-      C1[(size_t)k * N + P] = v;
+      const T v = k < ns ? c0 : T(0);
+      C0[(size_t)k * n + r] = v;
+      C1[(size_t)k * n + r] = v;
     }
   }
 }
@@ -377,23 +456,21 @@ __global__ void k_np_init(const NFlag *__restrict__ fl, T *__restrict__ C0, T *_
 // sum of C at the outlet, 13 pore cells in the outlet column.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_np_sums(const NFlag *__restrict__ fl, const T *__restrict__ C, const T *__restrict__ u,
-              long long N, int nx, int ns, double cell_vol, double *__restrict__ part,
-              unsigned int *counter, double *scal) {
+    k_np_sums(const uint2 *__restrict__ meta, const T *__restrict__ C, const T *__restrict__ u,
+              int n, int ns, double cell_vol, double *__restrict__ part, unsigned int *counter,
+              double *scal) {
   constexpr int NV = 14;
   __shared__ double sm[NV * 32];
   double v[NV];
 #pragma unroll
   for (int j = 0; j < NV; j++) v[j] = 0.0;
-  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
-       P += (long long)gridDim.x * blockDim.x) {
-    if (fl[P] & 1u) continue;
-    const bool outlet = (P % nx) == nx - 1;
-    const double ux = (double)u[P];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const bool outlet = (meta[r].x >> kEdgeBit) & 1u;
+    const double ux = (double)u[r];
 #pragma unroll
     for (int k = 0; k < kMaxSpecies; k++) {
       if (k >= ns) break;
-      const double ck = (double)C[(size_t)k * N + P];
+      const double ck = (double)C[(size_t)k * n + r];
       v[k] += ck;
       if (outlet) {
         v[4 + k] += ux * ck;
@@ -425,16 +502,16 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // Pore cells and pore-solid faces inside the image (the interface the
-// specific surface of Sec. 4 measures), counted over the pore-cell list.
+// specific surface of Sec. 4 measures), counted over the pore ranks.
 __global__ void __launch_bounds__(kRedThreads)
-    k_geometry(const NFlag *__restrict__ fl, const int *__restrict__ cells, int n, int faces,
-               double *__restrict__ part, unsigned int *counter, double *scal) {
+    k_geometry(const uint2 *__restrict__ meta, int n, int faces, double *__restrict__ part,
+               unsigned int *counter, double *scal) {
   __shared__ double sm[2 * 32];
   double v[2] = {0.0, 0.0};
   const unsigned face_bits = ((1u << faces) - 1u) << kFaceBit;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     v[0] += 1.0;
-    v[1] += (double)__popc(fl[cells[k]] & face_bits);
+    v[1] += (double)__popc(meta[r].x & face_bits);
   }
   block_reduce<2>(v, sm, OpSum(), 0.0);
   if (threadIdx.x == 0) {
@@ -451,7 +528,7 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// Totals of the per-block Gamma/In/Out accumulators (one block, fixed order).
+// Totals of the per-warp Gamma/In/Out accumulators (one block, fixed order).
 __global__ void __launch_bounds__(kRedThreads)
     k_acc_total(const double *__restrict__ acc, int nblocks, double *scal) {
   constexpr int NV = 3 * kMaxSpecies;
@@ -463,22 +540,66 @@ __global__ void __launch_bounds__(kRedThreads)
     for (int j = 0; j < NV; j++) scal[S_ACC + j] = v[j];
 }
 
-// Mean of species k over the pore cells of each x column.
+// Mean of species k over the pore cells of each x column (the column's
+// cells found through the row words).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_colmeans(const NFlag *__restrict__ fl, const T *__restrict__ C, int nx, long long rows,
+    k_colmeans(const uint2 *__restrict__ words, int W, const T *__restrict__ C, int rows,
                double *__restrict__ out) {
   __shared__ double sm[2 * 32];
   const int x = blockIdx.x;
   double v[2] = {0.0, 0.0};
-  for (long long r = threadIdx.x; r < rows; r += blockDim.x) {
-    const long long P = r * nx + x;
-    if (fl[P] & 1u) continue;
-    v[0] += (double)C[P];
+  for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+    const uint2 t = words[(size_t)row * W + (x >> 5)];
+    if (!((t.y >> (x & 31)) & 1u)) continue;
+    v[0] += (double)C[t.x + __popc(t.y & ((1u << (x & 31)) - 1u))];
     v[1] += 1.0;
   }
   block_reduce<2>(v, sm, OpSum(), 0.0);
   if (threadIdx.x == 0) out[x] = v[1] > 0.0 ? v[0] / v[1] : 0.0;
+}
+
+// Per pore rank: its face flags, x and row.
+__global__ void k_cmeta(const NFlag *__restrict__ fl, const int *__restrict__ cells, int n,
+                        int nx, uint2 *__restrict__ meta) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int P = cells[r];
+    const int row = P / nx, x = P - row * nx;
+    meta[r] = make_uint2((unsigned)fl[P] | ((unsigned)x << 16), (unsigned)row);
+  }
+}
+
+// Per 32 cells of a row: the pore bits and the rank of the first pore cell at
+// or after the word's first cell (binary search of the ascending cell list).
+__global__ void k_words(const NFlag *__restrict__ fl, const int *__restrict__ cells, int n,
+                        int nx, int W, long long n_words, uint2 *__restrict__ words) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n_words;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long row = w / W;
+    const int x0 = (int)(w - row * W) * 32;
+    const long long P0 = row * nx + x0;
+    unsigned bits = 0;
+    for (int b = 0; b < 32 && x0 + b < nx; b++)
+      if (!(fl[P0 + b] & 1u)) bits |= 1u << b;
+    int lo = 0, hi = n;  // first rank with cells[rank] >= P0
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((long long)cells[mid] < P0) lo = mid + 1;
+      else hi = mid;
+    }
+    words[w] = make_uint2((unsigned)lo, bits);
+  }
+}
+
+// Compact (rank-ordered) field -> FP64 lattice field, 0 in solid cells:
+// dst[a * N + cells[r]] = src[a * n + r] for comps components.
+template <typename T>
+__global__ void k_scatter(const T *__restrict__ src, int comps, const int *__restrict__ cells,
+                          int n, long long N, double *__restrict__ dst) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const long long P = cells[r];
+    for (int a = 0; a < comps; a++) dst[a * N + P] = (double)src[(size_t)a * n + r];
+  }
 }
 
 template <typename T> NPConst<T> make_const(const cdi_domain *d) {
@@ -494,13 +615,16 @@ template <typename T> NPConst<T> make_const(const cdi_domain *d) {
   return c;
 }
 
+NPGeo make_geo(const cdi_domain *d) {
+  return NPGeo{d->d_cmeta, d->d_words, (int)d->n_pore, d->W, d->ny, d->nz, d->walls};
+}
+
 template <typename T, int DIM, int NS>
 void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
-  // one thread per pore cell; np_blocks blocks, one FP64 account set each
+  // one thread per pore rank; np_blocks blocks, one FP64 account set each
   k_np_step<T, DIM, NS><<<d->np_blocks, kRowBlock, 0, st>>>(
       (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
-      (const typename PhiStore<T>::type *)d->d_phi, d->d_nflags, d->d_cell_list,
-      (int)d->n_pore, make_const<T>(d), d->d_acc, d->nx, d->ny, d->nz, d->N, d->walls);
+      (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d), d->d_acc);
 }
 
 template <typename T, int DIM>
@@ -552,13 +676,13 @@ cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
   if (dt_used) *dt_used = dt;
   if (d->prec == CDI_FP64)
     k_np_init<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, (double *)d->d_C[0], (double *)d->d_C[1], d->N, d->ns, d->c0);
+        (double *)d->d_C[0], (double *)d->d_C[1], (int)d->n_pore, d->ns, d->c0);
   else
     k_np_init<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, (float *)d->d_C[0], (float *)d->d_C[1], d->N, d->ns, (float)d->c0);
+        (float *)d->d_C[0], (float *)d->d_C[1], (int)d->n_pore, d->ns, (float)d->c0);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "transport init");
-  CDI_TRY(d, cudaMemsetAsync(d->d_acc, 0, (size_t)3 * kMaxSpecies * d->np_blocks * 8, d->stream),
+  CDI_TRY(d, cudaMemsetAsync(d->d_acc, 0, (size_t)3 * kMaxSpecies * d->np_accs * 8, d->stream),
           "reset accumulators");
   d->cur = 0;
   d->np_steps = 0;
@@ -603,27 +727,12 @@ namespace {
 template <typename T, int DIM>
 void launch_sweep_d(cdi_domain *d, cudaStream_t st, const void *members, int n, int in) {
   const SweepMember<T> *m = (const SweepMember<T> *)members;
+  const NPGeo g = make_geo(d);
   switch (d->ns) {
-    case 1:
-      k_np_sweep<T, DIM, 1><<<d->np_blocks, kRowBlock, 0, st>>>(
-          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
-          d->walls);
-      break;
-    case 2:
-      k_np_sweep<T, DIM, 2><<<d->np_blocks, kRowBlock, 0, st>>>(
-          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
-          d->walls);
-      break;
-    case 3:
-      k_np_sweep<T, DIM, 3><<<d->np_blocks, kRowBlock, 0, st>>>(
-          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
-          d->walls);
-      break;
-    default:
-      k_np_sweep<T, DIM, 4><<<d->np_blocks, kRowBlock, 0, st>>>(
-          m, n, in, d->d_nflags, d->d_cell_list, (int)d->n_pore, d->nx, d->ny, d->nz, d->N,
-          d->walls);
-      break;
+    case 1: k_np_sweep<T, DIM, 1><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    case 2: k_np_sweep<T, DIM, 2><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    case 3: k_np_sweep<T, DIM, 3><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    default: k_np_sweep<T, DIM, 4><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
   }
 }
 
@@ -641,7 +750,7 @@ template <typename T>
 cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group,
                      void *const *phi_groups, const double *dts, int64_t n_steps,
                      double *gamma, double *cout) {
-  const size_t TN = (size_t)d->N * sizeof(T);
+  const size_t TN = (size_t)d->n_pore * sizeof(T);
   const int ns = d->ns;
   // per-member device memory: velocity, two concentration buffers, accounts
   std::vector<void *> blocks;
@@ -655,7 +764,7 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
   for (int m = 0; m < n && ok; m++) {
     void *u = take((size_t)d->dim * TN);
     void *c0 = take((size_t)kMaxSpecies * TN), *c1 = take((size_t)kMaxSpecies * TN);
-    void *acc = take((size_t)3 * kMaxSpecies * d->np_blocks * 8);
+    void *acc = take((size_t)3 * kMaxSpecies * d->np_accs * 8);
     ok = u && c0 && c1 && acc;
     if (!ok) break;
     d->dt = dts[m];
@@ -672,10 +781,10 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
   for (int m = 0; m < n && s == CDI_OK; m++) {
     s = cdi_flow_scale_to(d, scale[m], (void *)hm[m].u);
     if (s != CDI_OK) break;
-    k_np_init<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, hm[m].C[0], hm[m].C[1],
-                                                            d->N, ns, (T)d->c0);
+    k_np_init<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(hm[m].C[0], hm[m].C[1],
+                                                            (int)d->n_pore, ns, (T)d->c0);
     d->timing.kernel_launches++;
-    if (cudaMemsetAsync(hm[m].acc, 0, (size_t)3 * kMaxSpecies * d->np_blocks * 8, d->stream) !=
+    if (cudaMemsetAsync(hm[m].acc, 0, (size_t)3 * kMaxSpecies * d->np_accs * 8, d->stream) !=
         cudaSuccess)
       s = cdi_fail(d, CDI_ERR_CUDA, "sweep: memset");
   }
@@ -719,9 +828,9 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
   const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
   for (int m = 0; m < n && s == CDI_OK; m++) {
     k_np_sums<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, hm[m].C[cur], hm[m].u, d->N, d->nx, ns, vol, d->d_part,
+        d->d_cmeta, hm[m].C[cur], hm[m].u, (int)d->n_pore, ns, vol, d->d_part,
         d->d_counter + C_MASS, d->d_scal);
-    k_acc_total<<<1, kRedThreads, 0, d->stream>>>(hm[m].acc, d->np_blocks, d->d_scal);
+    k_acc_total<<<1, kRedThreads, 0, d->stream>>>(hm[m].acc, d->np_accs, d->d_scal);
     d->timing.kernel_launches += 2;
     cudaError_t e = cudaMemcpyAsync(d->h_scal + S_OUT, d->d_scal + S_OUT,
                                     (S_OUTN - S_OUT + 1) * sizeof(double),
@@ -749,6 +858,165 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Batch over several geometries: every (domain, combination) member in one
+// launch per step.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T, int DIM>
+void launch_batch_d(cudaStream_t st, int ns, const void *members, int n, int blocks, int in) {
+  const BatchMember<T> *m = (const BatchMember<T> *)members;
+  switch (ns) {
+    case 1: k_np_batch<T, DIM, 1><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    case 2: k_np_batch<T, DIM, 2><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    case 3: k_np_batch<T, DIM, 3><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    default: k_np_batch<T, DIM, 4><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+  }
+}
+
+template <typename T>
+void launch_batch(const cdi_domain *lead, cudaStream_t st, const void *members, int n,
+                  int blocks, int in) {
+  if (lead->dim == 2) launch_batch_d<T, 2>(st, lead->ns, members, n, blocks, in);
+  else launch_batch_d<T, 3>(st, lead->ns, members, n, blocks, in);
+}
+
+template <typename T>
+cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const double *scale,
+                     const int *group, void *const *phis, const double *dts, int64_t n_steps,
+                     double *gamma, double *cout) {
+  cdi_domain *L = doms[0];  // the lead: its stream, allocator and scratch serve the batch
+  const int n = n_doms * n_combos, ns = L->ns;
+  std::vector<void *> blocks;
+  auto take = [&](size_t bytes) {
+    void *p = cdi_dev_alloc(L, bytes);
+    if (p) blocks.push_back(p);
+    return p;
+  };
+  std::vector<BatchMember<T>> hm(n);
+  bool ok = true;
+  int total_blocks = 0;
+  for (int m = 0; m < n && ok; m++) {
+    cdi_domain *d = doms[m / n_combos];
+    const size_t TN = (size_t)d->n_pore * sizeof(T);
+    void *u = take((size_t)d->dim * TN);
+    void *c0 = take((size_t)kMaxSpecies * TN), *c1 = take((size_t)kMaxSpecies * TN);
+    void *acc = take((size_t)3 * kMaxSpecies * d->np_accs * 8);
+    ok = u && c0 && c1 && acc;
+    if (!ok) break;
+    d->dt = dts[m];
+    hm[m].s.C[0] = (T *)c0;
+    hm[m].s.C[1] = (T *)c1;
+    hm[m].s.u = (const T *)u;
+    hm[m].s.phi = (const typename PhiStore<T>::type *)phis[group[m]];
+    hm[m].s.acc = (double *)acc;
+    hm[m].s.c = make_const<T>(d);
+    hm[m].g = make_geo(d);
+    hm[m].block0 = total_blocks;
+    hm[m].nblocks = d->np_blocks;
+    total_blocks += d->np_blocks;
+  }
+  void *dmem = ok ? take(sizeof(BatchMember<T>) * n) : nullptr;
+  cdi_status s = CDI_OK;
+  if (!ok || !dmem) s = cdi_fail(L, CDI_ERR_OOM, "batch: device allocation failed");
+  // member velocities on their domains' streams, then everything on the lead's
+  for (int m = 0; m < n && s == CDI_OK; m++)
+    s = cdi_flow_scale_to(doms[m / n_combos], scale[m], (void *)hm[m].s.u);
+  for (int i = 0; i < n_doms && s == CDI_OK; i++)
+    if (cudaStreamSynchronize(doms[i]->stream) != cudaSuccess)
+      s = cdi_fail(L, CDI_ERR_CUDA, "batch: member setup");
+  for (int m = 0; m < n && s == CDI_OK; m++) {
+    const cdi_domain *d = doms[m / n_combos];
+    k_np_init<T><<<kRedBlocks, kRedThreads, 0, L->stream>>>(hm[m].s.C[0], hm[m].s.C[1],
+                                                            (int)d->n_pore, ns, (T)d->c0);
+    L->timing.kernel_launches++;
+    if (cudaMemsetAsync(hm[m].s.acc, 0, (size_t)3 * kMaxSpecies * d->np_accs * 8,
+                        L->stream) != cudaSuccess)
+      s = cdi_fail(L, CDI_ERR_CUDA, "batch: memset");
+  }
+  if (s == CDI_OK &&
+      cudaMemcpyAsync(dmem, hm.data(), sizeof(BatchMember<T>) * n, cudaMemcpyHostToDevice,
+                      L->stream) != cudaSuccess)
+    s = cdi_fail(L, CDI_ERR_CUDA, "batch: member table");
+  cudaGraphExec_t exec = nullptr;
+  int64_t done = 0;
+  if (s == CDI_OK) {
+    cudaEvent_t ev;
+    cdi_timing_begin(L, &ev);
+    if (n_steps >= kGraphSteps) {
+      cudaGraph_t graph;
+      cudaError_t e = cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int k = 0; k < kGraphSteps; k++)
+          launch_batch<T>(L, L->cap_stream, dmem, n, total_blocks, k & 1);
+        e = cudaStreamEndCapture(L->cap_stream, &graph);
+      }
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+      }
+      if (e != cudaSuccess) s = cdi_cuda_fail(L, e, "batch graph");
+      while (s == CDI_OK && n_steps - done >= kGraphSteps) {
+        e = cudaGraphLaunch(exec, L->stream);
+        if (e != cudaSuccess) s = cdi_cuda_fail(L, e, "batch graph launch");
+        done += kGraphSteps;
+      }
+    }
+    for (; s == CDI_OK && done < n_steps; done++)
+      launch_batch<T>(L, L->stream, dmem, n, total_blocks, (int)(done & 1));
+    cudaError_t e = cudaGetLastError();
+    if (s == CDI_OK && e != cudaSuccess) s = cdi_cuda_fail(L, e, "batch step");
+    cdi_timing_end(L, ev, PH_NP, n_steps);
+    L->timing.kernel_launches += n_steps;
+  }
+  // outputs per member, through the same reductions as a single run
+  const int cur = (int)(n_steps & 1);
+  for (int m = 0; m < n && s == CDI_OK; m++) {
+    const cdi_domain *d = doms[m / n_combos];
+    const double area = d->dim == 2 ? d->dx : d->dx * d->dx;
+    const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
+    k_np_sums<T><<<kRedBlocks, kRedThreads, 0, L->stream>>>(
+        d->d_cmeta, hm[m].s.C[cur], hm[m].s.u, (int)d->n_pore, ns, vol, L->d_part,
+        L->d_counter + C_MASS, L->d_scal);
+    k_acc_total<<<1, kRedThreads, 0, L->stream>>>(hm[m].s.acc, d->np_accs, L->d_scal);
+    L->timing.kernel_launches += 2;
+    cudaError_t e = cudaMemcpyAsync(L->h_scal + S_OUT, L->d_scal + S_OUT,
+                                    (S_OUTN - S_OUT + 1) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, L->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) {
+      s = cdi_cuda_fail(L, e, "batch outputs");
+      break;
+    }
+    for (int k = 0; k < ns; k++) {
+      gamma[m * ns + k] = L->h_scal[S_ACC + 3 * k] * dts[m] * area;
+      const double num = L->h_scal[S_OUT + 2 * k], den = L->h_scal[S_OUT + 2 * k + 1];
+      const double cnt = L->h_scal[S_OUTN];
+      cout[m * ns + k] = den != 0.0 ? num / den : (cnt > 0 ? L->h_scal[S_OUTP + k] / cnt : 0.0);
+    }
+  }
+  if (s == CDI_OK) {
+    cudaError_t e = cdi_timing_resolve(L);
+    if (e != cudaSuccess) s = cdi_cuda_fail(L, e, "timing");
+  }
+  cudaStreamSynchronize(L->stream);
+  if (exec) cudaGraphExecDestroy(exec);
+  for (void *p : blocks) cdi_dev_release(L, p);
+  return s;
+}
+
+}  // namespace
+
+cdi_status cdi_np_batch(cdi_domain *const *doms, int n_doms, int n_combos, const double *scale,
+                        const int *group, void *const *phis, const double *dts, int64_t n_steps,
+                        double *gamma, double *cout) {
+  if (doms[0]->prec == CDI_FP64)
+    return batch_run<double>(doms, n_doms, n_combos, scale, group, phis, dts, n_steps, gamma,
+                             cout);
+  return batch_run<float>(doms, n_doms, n_combos, scale, group, phis, dts, n_steps, gamma, cout);
+}
 
 cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *group,
                         void *const *phi_groups, const double *dts, int64_t n_steps,
@@ -801,13 +1069,13 @@ cdi_status cdi_np_reduce(cdi_domain *d) {
   const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
   if (d->prec == CDI_FP64)
     k_np_sums<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, (const double *)d->d_C[d->cur], (const double *)d->d_u, d->N, d->nx, d->ns,
-        vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
+        d->d_cmeta, (const double *)d->d_C[d->cur], (const double *)d->d_u, (int)d->n_pore,
+        d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
   else
     k_np_sums<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_nflags, (const float *)d->d_C[d->cur], (const float *)d->d_u, d->N, d->nx, d->ns,
-        vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
-  k_acc_total<<<1, kRedThreads, 0, d->stream>>>(d->d_acc, d->np_blocks, d->d_scal);
+        d->d_cmeta, (const float *)d->d_C[d->cur], (const float *)d->d_u, (int)d->n_pore,
+        d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
+  k_acc_total<<<1, kRedThreads, 0, d->stream>>>(d->d_acc, d->np_accs, d->d_scal);
   d->timing.kernel_launches += 2;
   CDI_TRY(d, cudaGetLastError(), "transport sums");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_OUT, d->d_scal + S_OUT,
@@ -820,9 +1088,9 @@ cdi_status cdi_np_reduce(cdi_domain *d) {
 }
 
 cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces) {
-  k_geometry<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list,
-                                                         (int)d->n_pore, 2 * d->dim, d->d_part,
-                                                         d->d_counter + C_GEOM, d->d_scal);
+  k_geometry<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_cmeta, (int)d->n_pore, 2 * d->dim,
+                                                         d->d_part, d->d_counter + C_GEOM,
+                                                         d->d_scal);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "geometry");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_GEOM, d->d_scal + S_GEOM, 2 * sizeof(double),
@@ -836,15 +1104,44 @@ cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces) {
 
 cdi_status cdi_np_column_means(cdi_domain *d, int k) {
   const size_t T = d->prec == CDI_FP64 ? 8 : 4;
-  const void *C = (const char *)d->d_C[d->cur] + (size_t)k * d->N * T;
-  const long long rows = (long long)d->ny * d->nz;
+  const void *C = (const char *)d->d_C[d->cur] + (size_t)k * d->n_pore * T;
+  const int rows = d->ny * d->nz;
   if (d->prec == CDI_FP64)
-    k_colmeans<double><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_nflags, (const double *)C,
-                                                             d->nx, rows, d->d_colout);
+    k_colmeans<double><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_words, d->W, (const double *)C,
+                                                             rows, d->d_colout);
   else
-    k_colmeans<float><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_nflags, (const float *)C, d->nx,
+    k_colmeans<float><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_words, d->W, (const float *)C,
                                                             rows, d->d_colout);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "column means");
+  return CDI_OK;
+}
+
+// Rank metadata and row words of the compact transport layout (after the
+// pore lists and the face flags).
+cdi_status cdi_np_build_compact(cdi_domain *d) {
+  const int n = (int)d->n_pore;
+  const long long n_words = (long long)d->ny * d->nz * d->W;
+  k_cmeta<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list, n, d->nx,
+                                                     d->d_cmeta);
+  k_words<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list, n, d->nx, d->W,
+                                                     n_words, d->d_words);
+  d->timing.kernel_launches += 2;
+  CDI_TRY(d, cudaGetLastError(), "compact layout");
+  return CDI_OK;
+}
+
+// comps rank-ordered components of the domain's precision -> FP64 lattice
+// fields (dst: comps * N doubles, 0 in solid cells).
+cdi_status cdi_np_scatter(cdi_domain *d, const void *src, int comps, double *dst) {
+  CDI_TRY(d, cudaMemsetAsync(dst, 0, (size_t)comps * d->N * 8, d->stream), "scatter reset");
+  if (d->prec == CDI_FP64)
+    k_scatter<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const double *)src, comps, d->d_cell_list, (int)d->n_pore, d->N, dst);
+  else
+    k_scatter<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const float *)src, comps, d->d_cell_list, (int)d->n_pore, d->N, dst);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "scatter");
   return CDI_OK;
 }

@@ -221,6 +221,36 @@ def sphere_pack_256():
     return grain_pack((256, 256, 256), 0.45, 6.0, 12.0, seed=2, overlap=True)
 
 
+def sweep_instance(seed: int):
+    """One geometry of the batched parameter sweep: a 2D polydisperse disc
+    pack (overlap allowed, r ~ U[4, 16]) whose size and porosity are drawn
+    from the seed: nx = 32 k, k uniform in 8..32; ny = 32 j, j uniform in
+    8..16 (256x256 to 1024x512); porosity ~ U[0.4, 0.7].  Returns
+    ``(mask, PackInfo)``."""
+    rng = SplitMix64(seed ^ 0x5EED5EED)
+    nx = 32 * (8 + int(rng.uniform() * 25))
+    ny = 32 * (8 + int(rng.uniform() * 9))
+    phi = rng.uniform_range(0.4, 0.7)
+    return grain_pack((ny, nx), phi, 4.0, 16.0, seed=seed)
+
+
+def serve_instance(seed: int):
+    """One request geometry of the serving workload: half are 2D 512x512 disc
+    packs, half 3D n^3 sphere packs with n in {64, 96, 128, 160, 192};
+    porosity ~ U[0.4, 0.6], r ~ U[4, 16] (2D) or U[6, 12] (3D); the applied
+    potential ~ U[0.2, 1.2] V.  Returns ``(mask, applied_V)``."""
+    rng = SplitMix64(seed ^ 0x5E11E)
+    three_d = rng.uniform() < 0.5
+    phi = rng.uniform_range(0.4, 0.6)
+    V = rng.uniform_range(0.2, 1.2)
+    if three_d:
+        n = (64, 96, 128, 160, 192)[int(rng.uniform() * 5)]
+        m, _ = grain_pack((n, n, n), phi, 6.0, 12.0, seed=seed)
+    else:
+        m, _ = grain_pack((512, 512), phi, 4.0, 16.0, seed=seed)
+    return m, V
+
+
 def random_mask(shape, solid_fraction: float, seed: int) -> np.ndarray:
     """I.i.d. voxel noise (for edge-case tests): each voxel solid with the
     given probability, drawn from numpy's seeded PCG64 generator."""

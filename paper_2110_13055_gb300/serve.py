@@ -50,19 +50,24 @@ class Request:
 
 
 def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> int:
-    """Device memory a domain for this mask allocates (the allocations of
-    cdi_create_domain), plus one sweep-free transport state."""
+    """Peak device memory a domain for this mask allocates (the allocations of
+    cdi_create_domain, including its create-time work arrays), with one
+    transport state."""
     dim = mask.ndim
     N = int(mask.size)
     n_pore = int((mask == 0).sum())
+    n_fp = n_pore * (2 if mirror else 1)
     Nf = N * (2 if mirror else 1)
     Q = 9 if dim == 2 else 19
     T = 8 if precision == cdi.FP64 else 4
-    pop = Q * Nf * (8 if precision in (cdi.FP64, cdi.FP32_SPLIT) else 4)
-    fflag = Nf * (2 if dim == 2 else 4)
-    per_cell = (1 + 2 + dim * T + 8 + 8 + 2 * 4 * T + 4 * 8)   # mask, flags, u, psi, phi, C, CG
-    lists = 4 * (n_pore * (2 if mirror else 1) + n_pore)
-    return pop + fflag + dim * Nf * 8 + N * per_cell + lists + (4 << 20)
+    Tpop = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[precision]
+    nx = mask.shape[-1]
+    rows = N // nx
+    flow = (Q * Tpop + (Q - 1) * 4 + 4) * n_fp + Nf * (2 if dim == 2 else 4) + dim * Nf * 8
+    transport = n_pore * (4 + 8 + dim * T + 8 + 2 * 4 * T) + rows * ((nx + 31) // 32) * 8
+    lattice = N * (1 + 2 + 8 + 4 * 8)                 # mask, face flags, psi, CG vectors
+    work = Nf * 4 + 2 * ((Nf + 2047) // 2048) * 4     # create-time rank and list work
+    return flow + transport + lattice + work + (4 << 20)
 
 
 class Server:

@@ -74,3 +74,44 @@ def test_sweep_argument_errors():
         assert e.value.status == 1
         g, c, dt = d.sweep([(1e-4, 1.0)], n_steps=0)
         assert np.all(g == 0)
+
+
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batch_over_uneven_geometries_equals_single_runs(prec, dim):
+    """cdi_sweep_batch: members of several uneven geometries in one launch per
+    step; every member equals its domain's single run bit for bit."""
+    shapes = [(23, 37), (31, 45), (17, 70)] if dim == 2 else [(9, 11, 17), (7, 13, 21)]
+    masks = [inputs.grain_pack(s, 0.6, 1.5, 4.0, seed=30 + i)[0] for i, s in enumerate(shapes)]
+    combos = COMBOS[:3]
+    lam, c0, Ka, n = 1.5e-7, 10.0, 1e-6, 131
+    doms = [cdi.Domain(m, precision=prec) for m in masks]
+    try:
+        for d in doms:
+            d.solve_flow(tol=0.0, max_steps=600, U_target=1e-4)
+        g_b, c_b, dt_b = cdi.batch(doms, combos, lambda_D=lam, c0=c0, Ka=Ka, n_steps=n)
+        for i, d in enumerate(doms):
+            g1, c1, dt1 = single_runs(d, combos, lam, c0, Ka, n)
+            assert np.array_equal(dt_b[i], dt1)
+            assert np.array_equal(g_b[i], g1)
+            assert np.array_equal(c_b[i], c1)
+    finally:
+        for d in doms:
+            d.close()
+
+
+def test_batch_argument_errors():
+    m, _ = inputs.grain_pack((23, 37), 0.6, 1.5, 4.0, seed=21)
+    m3, _ = inputs.grain_pack((9, 11, 17), 0.6, 1.5, 4.0, seed=21)
+    with cdi.Domain(m) as a, cdi.Domain(m) as b, cdi.Domain(m3) as c:
+        with pytest.raises(cdi.CDIError) as e:       # no solved flow
+            cdi.batch([a, b], COMBOS[:1], n_steps=1)
+        assert e.value.status == 6
+        a.solve_flow(tol=0.0, max_steps=200)
+        c.solve_flow(tol=0.0, max_steps=200)
+        with pytest.raises(cdi.CDIError) as e:       # mixed dimensions
+            cdi.batch([a, c], COMBOS[:1], n_steps=1)
+        assert e.value.status == 1
+        with pytest.raises(cdi.CDIError) as e:       # the same domain twice
+            cdi.batch([a, a], COMBOS[:1], n_steps=1)
+        assert e.value.status == 1
