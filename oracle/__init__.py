@@ -73,6 +73,11 @@ def _load():
         lib.orc_np_run.argtypes = [i, i, i, i, P, i, P, P, i, P, P, d, d, d, d,
                                    d, l, P, P, P, P]
         lib.orc_np_run.restype = i
+        lib.orc_psi_src.argtypes = [i, i, i, i, P, i, d, d, P, d, i, P, P, P]
+        lib.orc_psi_src.restype = i
+        lib.orc_pnp_run.argtypes = [i, i, i, i, P, i, P, i, P, P, d, d, d, d, d, l, l, d, d,
+                                    d, P, P, P, P, P]
+        lib.orc_pnp_run.restype = i
         _lib = lib
     return _lib
 
@@ -224,6 +229,57 @@ def np_run(mask, u, psi_field, z, D, *, c0, dt, n_steps, dx=1e-7, Ka=1e-6,
     if st < 0:
         raise ValueError("orc_np_run rejected its arguments")
     return C, G, I, O
+
+
+def charge_coef(dx, eps_r=EPS_R_DEFAULT):
+    """F dx^2 / (eps_r eps_0): turns sum_i z_i C_i (mol/m^3) into the charge
+    term of the discrete Eq. 4 (volts)."""
+    return FARADAY * dx * dx / (eps_r * EPS0)
+
+
+def psi_src(mask, psi_s, src, *, lateral_walls=False, tol=1e-13, max_iter=1000000):
+    """Eq. 4 with Dirichlet psi_s at solid faces, the inlet feed at 0 and the
+    charge term ``src`` (volts, per cell: dx^2 rho_e / (eps_r eps_0)) on the
+    right-hand side; Laplace operator."""
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    out = np.zeros(m.shape, dtype=np.float64)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _load().orc_psi_src(dim, nx, ny, nz, _ptr(m), int(lateral_walls), float(psi_s),
+                             0.0, _ptr(src), float(tol), int(max_iter), _ptr(out),
+                             ctypes.byref(it), ctypes.byref(rel))
+    if st < 0:
+        raise ValueError("orc_psi_src rejected its arguments")
+    return out, it.value, rel.value
+
+
+def pnp_run(mask, u, z, D, *, c0, dt, n_steps, K, psi_s, dx=1e-7, Ka=1e-6, T=T_DEFAULT,
+            eps_r=EPS_R_DEFAULT, lateral_walls=False, psi_tol=1e-13, C=None):
+    """Coupled Poisson-Nernst-Planck (Eq. 3-5): the potential is re-solved
+    from the net charge of the current concentrations (Eq. 5) before every
+    block of K explicit steps.  Starts from C = c0 in the pore cells unless C
+    is given.  Returns ``(C, Gamma, In, Out, psi)`` with psi the last potential
+    solved."""
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    z, D = _species(z, D)
+    ns = len(z)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    if C is None:
+        C = np.where(m[None] == 0, float(c0), 0.0) * np.ones((ns,) + m.shape)
+    C = np.ascontiguousarray(C, dtype=np.float64).copy()
+    G, I, O = np.zeros(ns), np.zeros(ns), np.zeros(ns)
+    ps = np.zeros(m.shape, dtype=np.float64)
+    st = _load().orc_pnp_run(dim, nx, ny, nz, _ptr(m), int(lateral_walls), _ptr(u), ns,
+                             _ptr(z), _ptr(D), float(dx), float(Ka), float(c0),
+                             thermal_voltage(T), float(dt), int(n_steps), int(K),
+                             float(psi_s), charge_coef(dx, eps_r), float(psi_tol), _ptr(C),
+                             _ptr(G), _ptr(I), _ptr(O), _ptr(ps))
+    if st < 0:
+        raise ValueError("orc_pnp_run rejected its arguments")
+    return C, G, I, O, ps
 
 
 # --------------------------------------------------------------------------

@@ -275,10 +275,21 @@ static void psi_apply(int dim, int nx, int ny, int nz, const uint8_t *mask,
 int orc_psi(int dim, int nx, int ny, int nz, const uint8_t *mask,
             int lateral_walls, double psi_s, double kdx2, double tol,
             int max_iter, double *psi, int *iters, double *relres) {
+  return orc_psi_src(dim, nx, ny, nz, mask, lateral_walls, psi_s, kdx2, NULL, tol,
+                     max_iter, psi, iters, relres);
+}
+
+int orc_psi_src(int dim, int nx, int ny, int nz, const uint8_t *mask,
+                int lateral_walls, double psi_s, double kdx2, const double *src,
+                double tol, int max_iter, double *psi, int *iters, double *relres) {
   if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1 || kdx2 < 0.0)
     return -1;
   long N = (long)nx * ny * nz;
   double *b = (double *)calloc((size_t)N, sizeof(double));
+  /* the charge term of Eq. 4, dx^2 rho_e / (eps_r eps_0), when given */
+  if (src)
+    for (long P = 0; P < N; P++)
+      if (!mask[P]) b[P] = src[P];
   double *r = (double *)malloc(sizeof(double) * N);
   double *p = (double *)malloc(sizeof(double) * N);
   double *Ap = (double *)malloc(sizeof(double) * N);
@@ -459,4 +470,41 @@ int orc_np_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
   }
   free(Cn);
   return 0;
+}
+
+/* Coupled Poisson-Nernst-Planck (Eq. 3-5): before every block of K explicit
+ * steps, the potential is solved from Eq. 4 with the net charge density of
+ * Eq. 5 of the current concentrations (Laplace operator, Dirichlet psi_s at
+ * solid faces, psi = 0 in the inlet feed, no flux at the outlet), then the
+ * K steps run in that potential.  eps_coef = F dx^2 / (eps_r eps_0), so the
+ * source of cell P is eps_coef * sum_i z_i C_i(P).  psi (N) receives the last
+ * potential solved. */
+int orc_pnp_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
+                int lateral_walls, const double *u, int ns, const int *z,
+                const double *D, double dx, double Ka, double c0, double VT,
+                double dt, long n_steps, long K, double psi_s, double eps_coef,
+                double psi_tol, double *C, double *Gamma, double *In, double *Out,
+                double *psi) {
+  if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1 || ns < 1 || K < 1) return -1;
+  long N = (long)nx * ny * nz;
+  double *src = (double *)malloc(sizeof(double) * N);
+  int st = 0;
+  for (long s = 0; s < n_steps && st >= 0; s += K) {
+    for (long P = 0; P < N; P++) {
+      double q = 0.0;
+      if (!mask[P])
+        for (int i = 0; i < ns; i++) q += z[i] * C[(long)i * N + P];
+      src[P] = eps_coef * q;
+    }
+    int it;
+    double rel;
+    st = orc_psi_src(dim, nx, ny, nz, mask, lateral_walls, psi_s, 0.0, src, psi_tol,
+                     1000000, psi, &it, &rel);
+    if (st < 0) break;
+    long steps = n_steps - s < K ? n_steps - s : K;
+    st = orc_np_run(dim, nx, ny, nz, mask, lateral_walls, u, psi, ns, z, D, dx, Ka, c0, VT,
+                    dt, steps, C, Gamma, In, Out);
+  }
+  free(src);
+  return st < 0 ? st : 0;
 }

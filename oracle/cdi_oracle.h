@@ -41,6 +41,13 @@ int orc_psi(int dim, int nx, int ny, int nz, const uint8_t *mask,
             int lateral_walls, double psi_s, double kdx2, double tol,
             int max_iter, double *psi, int *iters, double *relres);
 
+/* The same solve with an additional right-hand side: src (N values, ignored
+ * in solid cells) is the charge term dx^2 rho_e / (eps_r eps_0) of Eq. 4
+ * (NULL: none). */
+int orc_psi_src(int dim, int nx, int ny, int nz, const uint8_t *mask,
+                int lateral_walls, double psi_s, double kdx2, const double *src,
+                double tol, int max_iter, double *psi, int *iters, double *relres);
+
 /* Explicit time step bound: safety / max over cells and species of the
  * outflow rate (the sum of the exponentially fitted outflow coefficients). */
 double orc_np_dt(int dim, int nx, int ny, int nz, const uint8_t *mask,
@@ -58,6 +65,17 @@ int orc_np_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
                const int *z, const double *D, double dx, double Ka, double c0,
                double VT, double dt, long n_steps, double *C, double *Gamma,
                double *In, double *Out);
+
+/* Coupled Poisson-Nernst-Planck (Eq. 3-5): the potential is re-solved from
+ * the charge density of the current concentrations (eps_coef = F dx^2 /
+ * (eps_r eps_0)) before every block of K steps; otherwise as orc_np_run.
+ * psi receives the last potential solved. */
+int orc_pnp_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
+                int lateral_walls, const double *u, int ns, const int *z,
+                const double *D, double dx, double Ka, double c0, double VT,
+                double dt, long n_steps, long K, double psi_s, double eps_coef,
+                double psi_tol, double *C, double *Gamma, double *In, double *Out,
+                double *psi);
 
 #ifdef __cplusplus
 }
