@@ -144,6 +144,10 @@ typedef struct {
   double np_ms;        /* device time of the Nernst-Planck step kernels */
   int64_t np_launches;
   int64_t kernel_launches; /* all kernels this domain launched */
+  int32_t lbm_block;   /* threads per block of the LBM step and of the */
+  int32_t np_block;    /* transport step, picked by the library's autotuner
+                          on the first solve (timing only: every block size
+                          computes the same bits); 0 before it ran */
 } cdi_timing;
 
 /* Create a domain from a voxel mask (Sec. 2: marker-and-cell grid, one grid

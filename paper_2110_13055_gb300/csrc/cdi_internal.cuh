@@ -242,7 +242,7 @@ struct cdi_domain {
   void *d_fflags = nullptr;     // Nf flow flags
   cdi::NFlag *d_nflags = nullptr;  // N face flags
   int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
-  int *d_nbr = nullptr;         // (Q-1)*n_flow_pore neighbour ranks (-1: solid)
+  uint2 *d_fwords = nullptr;    // ceil(Nf/32) flow-site words {first rank, pore bits}
   long long n_flow_pore = 0;
   int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending:
                                 // entry r is the lattice cell of pore rank r
@@ -261,7 +261,8 @@ struct cdi_domain {
                                 // (FP64) or a float2 (hi, lo) pair (FP32)
   void *d_C[2] = {nullptr, nullptr};  // kMaxSpecies*n_pore concentrations,
                                       // ping-pong, T
-  double *d_acc = nullptr;      // 3*kMaxSpecies*np_accs per-warp sums
+  double *d_acc = nullptr;      // 3*kMaxSpecies*np_accs per-warp sums (8 B each:
+                                // FP64, or an FP32 pair in FP32 modes)
   double *d_part = nullptr;     // reduction partials (8*kRedBlocks)
   unsigned int *d_counter = nullptr;  // last-block counters (8 slots)
   double *d_scal = nullptr;     // device scalars (64)
@@ -282,8 +283,12 @@ struct cdi_domain {
   double c0 = 0.0, Ka = 0.0, dt = 0.0, VT = 0.0;
   int cur = 0;                  // which of d_C holds the current state
   int64_t np_steps = 0;
-  int np_blocks = 0;            // blocks of a transport step launch
-  int np_accs = 0;              // their warps: one account set each
+  int np_blocks = 0;            // 128-thread blocks over the pore cells
+  int np_accs = 0;              // account sets, one per warp of 32 pore cells
+                                // (rounded up to a multiple of 8)
+  // block sizes of the step kernels, picked by the autotuners
+  int lbm_block = 128, np_block = 128;
+  bool lbm_tuned = false, np_tuned = false;
 
   // graphs
   cudaGraphExec_t flow_graph = nullptr;
@@ -341,7 +346,7 @@ cudaError_t cdi_timing_resolve(cdi_domain *d);
 // Kernel-side entry points used by the API layer.
 cdi_status cdi_flow_build_flags(cdi_domain *d);
 size_t cdi_lists_work_ints(long long n);
-cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work);
+cdi_status cdi_flow_build_links(cdi_domain *d);
 cdi_status cdi_build_lists(cdi_domain *d, int *work);
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
                         double *res);

@@ -142,13 +142,18 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
 }
 
 // Populations are stored compactly by pore rank k (the position of the site
-// in the ascending pore-site list): g[i * n + k].  The neighbour table
-// nbr[(i - 1) * n + k] holds the rank of the site x_k + e_i, or -1 when that
-// site is solid or lies beyond a lateral wall (halfway bounce-back).
+// in the ascending pore-site list): g[i * n + k].  The odd step finds the
+// rank of the site x_k + e_i from the flat site words: one uint2 per 32
+// consecutive flow sites (lattice order), {rank of the first pore site at or
+// after the word's first site, pore bits}, so rank(site) = first +
+// popc(bits below the site).  Nothing per direction is stored: a site reads
+// its list entry and its flag word instead of Q - 1 neighbour ranks, and the
+// words (Nf / 4 bytes) stay in L2.
 //
 // Slot read by direction i at rank k (ODD: the upstream neighbour's opposite
 // slot, or the own slot after a bounce-back), and slot written by the
-// post-collision value of direction i.  nb[j] caches nbr for direction j.
+// post-collision value of direction i.  nb[j] holds the rank of x_k + e_j,
+// or -1 where that site is solid or beyond a lateral wall (bounce-back).
 template <int DIM, bool ODD>
 __device__ __forceinline__ size_t read_slot(const int *nb, int k, int i, long long n) {
   using L = Lat<DIM>;
@@ -166,35 +171,57 @@ __device__ __forceinline__ size_t write_slot(const int *nb, int k, int i, long l
   return (size_t)i * n + dst;
 }
 
+// What the odd step needs to find neighbours.
+template <int DIM> struct FlowLinks {
+  const int *list;                          // rank -> flow site
+  const typename FlowFlag<DIM>::type *fl;   // flag word per flow site
+  const uint2 *words;                       // site words (see above)
+  int NX, ny, nz;
+};
+
+// Rank of the pore flow site `site`.
+__device__ __forceinline__ int site_rank(const uint2 *__restrict__ words, int site) {
+  const uint2 t = __ldg(words + (site >> 5));
+  return (int)t.x + __popc(t.y & ((1u << (site & 31)) - 1u));
+}
+
 // Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
 template <int DIM, bool ODD>
-__device__ __forceinline__ void load_links(const int *__restrict__ nbr, int k, long long n,
+__device__ __forceinline__ void load_links(const FlowLinks<DIM> &lk, int k,
                                            int (&nb)[Lat<DIM>::Q]) {
+  using L = Lat<DIM>;
   nb[0] = k;
   if (ODD) {
+    const int s = lk.list[k];
+    const unsigned f = lk.fl[s];
+    const SiteIdx<DIM> ix(s, f, lk.NX, lk.ny, lk.nz);
 #pragma unroll
-    for (int i = 1; i < Lat<DIM>::Q; i++) nb[i] = nbr[(size_t)(i - 1) * n + k];
+    for (int i = 1; i < L::Q; i++)
+      nb[i] = ((f >> i) & 1u) ? -1
+                              : site_rank(lk.words, ix.nb(L::ex(i), L::ey(i), L::ez(i)));
   }
 }
 
-__global__ void k_rank_scatter(const int *__restrict__ list, int n, int *__restrict__ rank) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    rank[list[k]] = k;
-}
-
+// Site words of the flow grid: pore bits of sites [32 w, 32 w + 32) and the
+// rank of the first pore site at or after 32 w (binary search of the
+// ascending pore-site list).
 template <int DIM>
-__global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
-                        const int *__restrict__ list, int n, const int *__restrict__ rank,
-                        int *__restrict__ nbr, int NX, int ny, int nz) {
-  using L = Lat<DIM>;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int s = list[k];
-    const unsigned f = fl[s];
-    const SiteIdx<DIM> ix(s, f, NX, ny, nz);
-#pragma unroll
-    for (int i = 1; i < L::Q; i++)
-      nbr[(size_t)(i - 1) * n + k] =
-          ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
+__global__ void k_flow_words(const typename FlowFlag<DIM>::type *__restrict__ fl,
+                             const int *__restrict__ list, int n, long long Nf,
+                             long long n_words, uint2 *__restrict__ words) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n_words;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long s0 = w * 32;
+    unsigned bits = 0;
+    for (int b = 0; b < 32 && s0 + b < Nf; b++)
+      if (!(fl[s0 + b] & 1u)) bits |= 1u << b;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((long long)list[mid] < s0) lo = mid + 1;
+      else hi = mid;
+    }
+    words[w] = make_uint2((unsigned)lo, bits);
   }
 }
 
@@ -205,9 +232,9 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 // (more resident blocks per SM: the step is latency-bound on its scattered
 // loads, so occupancy matters more than a few spare registers; the bound is
 // chosen per variant so that nothing spills)
-template <typename S, int DIM, bool ODD>
-__global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7))
-    k_lbm_step(S *__restrict__ g, const int *__restrict__ nbr, int n,
+template <typename S, int DIM, bool ODD, int BS>
+__global__ void __launch_bounds__(BS, (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128 / BS)
+    k_lbm_step(S *__restrict__ g, const FlowLinks<DIM> lk, int n,
                typename Arith<S>::type omega, typename Arith<S>::type fx_half,
                typename Arith<S>::type fsrc) {
   using T = typename Arith<S>::type;
@@ -216,7 +243,7 @@ __global__ void __launch_bounds__(kRowBlock, DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   int nb[Q];
-  load_links<DIM, ODD>(nbr, k0, n, nb);
+  load_links<DIM, ODD>(lk, k0, nb);
   T gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) gi[i] = widen(g[read_slot<DIM, ODD>(nb, k0, i, n)]);
@@ -263,10 +290,10 @@ struct SplitConst {
 
 // The same step with every population stored as an FP32 pair gh + gl and the
 // collision carried out in pair arithmetic.
-template <int DIM, bool ODD, bool TAU1>
-__global__ void __launch_bounds__(kRowBlock)
+template <int DIM, bool ODD, bool TAU1, int BS>
+__global__ void __launch_bounds__(BS)
     k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
-                     const int *__restrict__ nbr, int n, SplitConst c) {
+                     const FlowLinks<DIM> lk, int n, SplitConst c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   // lattice weights as FP32 pairs: rest, axis, diagonal
@@ -277,7 +304,7 @@ __global__ void __launch_bounds__(kRowBlock)
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   int nb[Q];
-  load_links<DIM, ODD>(nbr, k0, n, nb);
+  load_links<DIM, ODD>(lk, k0, nb);
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -462,38 +489,88 @@ template <int M> struct ModeT { using T = float; };
 template <> struct ModeT<M_F64> { using T = double; };
 template <> struct ModeT<M_BF16> { using T = __nv_bfloat16; };
 
-template <int M, int DIM>
-void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
+template <int M, int DIM, int BS>
+void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   using T = typename ModeT<M>::T;
   // one thread per pore site of the flow grid (pore rank)
   const int n = (int)d->n_flow_pore;
-  const int grid = (n + kRowBlock - 1) / kRowBlock;
-  const int *nbr = d->d_nbr;
+  const int grid = (n + BS - 1) / BS;
+  const FlowLinks<DIM> lk{d->d_flow_list, (const typename FlowFlag<DIM>::type *)d->d_fflags,
+                          d->d_fwords, d->NX, d->ny, d->nz};
   if (M == M_SPLIT) {
     const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
                        host_pair(fs * Lat<DIM>::w(1)),
                        host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
     if (tau == 1.0) {
-      k_lbm_step_split<DIM, false, true><<<grid, kRowBlock, 0, st>>>(
-          (float *)d->d_g, d->d_glo, nbr, n, c);
-      k_lbm_step_split<DIM, true, true><<<grid, kRowBlock, 0, st>>>(
-          (float *)d->d_g, d->d_glo, nbr, n, c);
+      k_lbm_step_split<DIM, false, true, BS><<<grid, BS, 0, st>>>(
+          (float *)d->d_g, d->d_glo, lk, n, c);
+      k_lbm_step_split<DIM, true, true, BS><<<grid, BS, 0, st>>>(
+          (float *)d->d_g, d->d_glo, lk, n, c);
     } else {
-      k_lbm_step_split<DIM, false, false><<<grid, kRowBlock, 0, st>>>(
-          (float *)d->d_g, d->d_glo, nbr, n, c);
-      k_lbm_step_split<DIM, true, false><<<grid, kRowBlock, 0, st>>>(
-          (float *)d->d_g, d->d_glo, nbr, n, c);
+      k_lbm_step_split<DIM, false, false, BS><<<grid, BS, 0, st>>>(
+          (float *)d->d_g, d->d_glo, lk, n, c);
+      k_lbm_step_split<DIM, true, false, BS><<<grid, BS, 0, st>>>(
+          (float *)d->d_g, d->d_glo, lk, n, c);
     }
   } else {
     using A = typename Arith<T>::type;
     const A omega = A(1.0 / tau), fxh = A(0.5 * force);
     const A fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
-    k_lbm_step<T, DIM, false><<<grid, kRowBlock, 0, st>>>((T *)d->d_g, nbr, n, omega, fxh,
-                                                           fsrc);
-    k_lbm_step<T, DIM, true><<<grid, kRowBlock, 0, st>>>((T *)d->d_g, nbr, n, omega, fxh,
-                                                          fsrc);
+    k_lbm_step<T, DIM, false, BS><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh, fsrc);
+    k_lbm_step<T, DIM, true, BS><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh, fsrc);
   }
+}
+
+// One even + one odd step with the domain's block size.
+template <int M, int DIM>
+void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
+  switch (d->lbm_block) {
+    case 64: step_pair_bs<M, DIM, 64>(d, st, tau, force); break;
+    case 256: step_pair_bs<M, DIM, 256>(d, st, tau, force); break;
+    default: step_pair_bs<M, DIM, 128>(d, st, tau, force); break;
+  }
+}
+
+// Autotuner: times a few step pairs with each candidate block size on the
+// domain's stream and keeps the fastest.  Every block size computes the same
+// bits (one thread per site, no cross-thread arithmetic), so the choice only
+// changes speed.  Runs once per domain, before its first solve resets the
+// populations.
+template <int M, int DIM>
+cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
+  static const int cand[] = {64, 128, 256};
+  cudaEvent_t a, b;
+  CDI_TRY(d, cudaEventCreate(&a), "tune event");
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cdi_cuda_fail(d, e, "tune event");
+  }
+  float best = 0.f;
+  int best_bs = 128;
+  for (int bs : cand) {
+    d->lbm_block = bs;
+    launch_step_pair<M, DIM>(d, d->stream, tau, force);  // warm-up
+    e = cudaEventRecord(a, d->stream);
+    for (int k = 0; k < 6 && e == cudaSuccess; k++) launch_step_pair<M, DIM>(d, d->stream, tau, force);
+    if (e == cudaSuccess) e = cudaEventRecord(b, d->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) break;
+    d->timing.kernel_launches += 14;
+    if (bs == cand[0] || ms < best) {
+      best = ms;
+      best_bs = bs;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  d->lbm_block = best_bs;
+  if (e != cudaSuccess) return cdi_cuda_fail(d, e, "tune flow step");
+  d->lbm_tuned = true;
+  return CDI_OK;
 }
 
 template <int M, int DIM>
@@ -516,6 +593,10 @@ cdi_status flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
   d->tau = p->tau;
   d->force = p->force_lu;
   const int Q = Lat<DIM>::Q;
+  if (!d->lbm_tuned) {
+    cdi_status ts = tune_lbm<M, DIM>(d, p->tau, p->force_lu);
+    if (ts != CDI_OK) return ts;
+  }
   // start from rest: g = 0 (f = w), u_prev = u(0)
   const size_t nq = (size_t)Q * d->n_flow_pore;
   CDI_TRY(d, cudaMemsetAsync(d->d_g, 0, nq * sizeof(T), d->stream), "reset g");
@@ -613,24 +694,19 @@ cdi_status cdi_flow_build_flags(cdi_domain *d) {
   return d->dim == 2 ? build_flags<2>(d) : build_flags<3>(d);
 }
 
-// Neighbour-rank table of the compact population layout (after the pore
-// lists): rank[site] scattered from the list (rank_work: Nf ints, -1 for
-// solid), then nbr[(i-1) n + k] for every pore rank k and direction i.
-cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work) {
-  const int n = (int)d->n_flow_pore;
-  CDI_TRY(d, cudaMemsetAsync(rank_work, 0xff, (size_t)d->Nf * sizeof(int), d->stream),
-          "rank reset");
-  k_rank_scatter<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_flow_list, n, rank_work);
+// Site words of the compact population layout (after the pore lists).
+cdi_status cdi_flow_build_links(cdi_domain *d) {
+  const long long n_words = (d->Nf + 31) / 32;
   if (d->dim == 2)
-    k_links<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
-        d->ny, d->nz);
+    k_flow_words<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, (int)d->n_flow_pore, d->Nf,
+        n_words, d->d_fwords);
   else
-    k_links<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
-        d->ny, d->nz);
-  d->timing.kernel_launches += 2;
-  CDI_TRY(d, cudaGetLastError(), "neighbour table");
+    k_flow_words<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, (int)d->n_flow_pore, d->Nf,
+        n_words, d->d_fwords);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "site words");
   return CDI_OK;
 }
 

@@ -174,6 +174,7 @@ struct NPGeo {
   const uint2 *meta;   // per rank {flags | x << 16, row}
   const uint2 *words;  // per 32 cells of a row {first rank, pore bits}
   int n, W, ny, nz, walls;
+  int naccs;           // account sets (warps of 32 ranks), the same for any launch shape
 };
 
 // One explicit step of the pore cell of rank r for NS species: writes the
@@ -263,14 +264,36 @@ __device__ __forceinline__ bool np_cell(const T *__restrict__ Cin, T *__restrict
   return inlet || outlet;
 }
 
-// Warp sums of v in T, added by lane 0 to the warp's own FP64 accounts
+// Per-warp account slot: FP64 for FP64 storage; for FP32 storage an
+// unevaluated pair of FP32 words (hi + lo, about 48 significant bits) kept
+// with the two-sum transformation, so the step issues no FP64 instruction
+// (this part's FP64 rate is a small fraction of its FP32 rate).  Both are
+// 8 bytes.
+template <typename T> struct AccSlot { using type = double; };
+template <> struct AccSlot<float> { using type = float2; };
+
+__device__ __forceinline__ void acc_add(double *a, double v) { *a = __dadd_rn(*a, v); }
+__device__ __forceinline__ void acc_add(float2 *a, float v) {
+  float2 t = *a;
+  const float s = __fadd_rn(t.x, v);
+  const float bp = __fsub_rn(s, t.x);
+  const float e = __fadd_rn(__fsub_rn(t.x, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+  t.x = s;
+  t.y = __fadd_rn(t.y, e);
+  *a = t;
+}
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(float2 a) { return (double)a.x + (double)a.y; }
+
+// Warp sums of v in T, added by lane 0 to the warp's own accounts
 // acc[(3*k + kind) * nw + wid], kind 0 Gamma, 1 In, 2 Out (one thread per
 // pore cell, so the warp -> cells map is fixed and the totals are
 // deterministic).  A warp without inlet or outlet cells skips the In/Out sums
 // (its values are 0).  No block barrier: each warp retires on its own.  All
 // 32 lanes of the warp must call it.
 template <typename T, int NS>
-__device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io, double *__restrict__ acc,
+__device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io,
+                                           typename AccSlot<T>::type *__restrict__ acc,
                                            int wid, int nw) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -287,28 +310,28 @@ __device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io, double *__re
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
     for (int k = 0; k < NS; k++) {
-      double *a = acc + (size_t)(3 * k) * nw + wid;
-      a[0] = __dadd_rn(a[0], (double)v[k]);
+      typename AccSlot<T>::type *a = acc + (size_t)(3 * k) * nw + wid;
+      acc_add(a, v[k]);
       if (any_io) {
-        a[nw] = __dadd_rn(a[nw], (double)v[NS + k]);
-        a[2 * (size_t)nw] = __dadd_rn(a[2 * (size_t)nw], (double)v[2 * NS + k]);
+        acc_add(a + nw, v[NS + k]);
+        acc_add(a + 2 * (size_t)nw, v[2 * NS + k]);
       }
     }
   }
 }
 
-template <typename T, int DIM, int NS>
-__global__ void __launch_bounds__(kRowBlock)
+template <typename T, int DIM, int NS, int BS>
+__global__ void __launch_bounds__(BS)
     k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
               const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
-              double *__restrict__ acc) {
+              typename AccSlot<T>::type *__restrict__ acc) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   T v[3 * NS];
 #pragma unroll
   for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
   bool io = false;
   if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
-  np_account<T, NS>(v, io, acc, r >> 5, gridDim.x * (kRowBlock / 32));
+  np_account<T, NS>(v, io, acc, r >> 5, g.naccs);
 }
 
 // One member of a fused sweep: its own concentrations, velocity, potential,
@@ -317,7 +340,7 @@ template <typename T> struct SweepMember {
   T *C[2];          // concentration buffers (ping-pong)
   const T *u;
   const typename PhiStore<T>::type *phi;
-  double *acc;
+  typename AccSlot<T>::type *acc;
   NPConst<T> c;
 };
 
@@ -338,7 +361,7 @@ __global__ void __launch_bounds__(kRowBlock)
     bool io = false;
     if (r < g.n)
       io = np_cell<T, DIM, NS>(mb.C[in], mb.C[1 - in], mb.u, mb.phi, g, meta, r, mb.c, v);
-    np_account<T, NS>(v, io, mb.acc, r >> 5, gridDim.x * (kRowBlock / 32));
+    np_account<T, NS>(v, io, mb.acc, r >> 5, g.naccs);
   }
 }
 
@@ -375,7 +398,7 @@ __global__ void __launch_bounds__(kRowBlock)
   if (r < mb.g.n)
     io = np_cell<T, DIM, NS>(mb.s.C[in], mb.s.C[1 - in], mb.s.u, mb.s.phi, mb.g, mb.g.meta[r], r,
                              mb.s.c, v);
-  np_account<T, NS>(v, io, mb.s.acc, r >> 5, mb.nblocks * (kRowBlock / 32));
+  np_account<T, NS>(v, io, mb.s.acc, r >> 5, mb.g.naccs);
 }
 
 // Largest outflow rate over pore cells and species, in FP64 from the FP64
@@ -528,16 +551,30 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// Totals of the per-warp Gamma/In/Out accumulators (one block, fixed order).
+// Totals of the per-warp Gamma/In/Out accounts (one block, fixed order).
+template <typename A>
 __global__ void __launch_bounds__(kRedThreads)
-    k_acc_total(const double *__restrict__ acc, int nblocks, double *scal) {
+    k_acc_total(const A *__restrict__ acc, int nw, double *scal) {
   constexpr int NV = 3 * kMaxSpecies;
   __shared__ double sm[NV * 32];
   double v[NV];
-  combine_partials<NV>(acc, nblocks, v, sm, OpSum(), 0.0);
+#pragma unroll
+  for (int k = 0; k < NV; k++) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nw; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] += acc_value(acc[(size_t)k * nw + b]);
+  block_reduce<NV>(v, sm, OpSum(), 0.0);
   if (threadIdx.x == 0)
 #pragma unroll
     for (int j = 0; j < NV; j++) scal[S_ACC + j] = v[j];
+}
+
+// Launches k_acc_total for the domain's precision.
+void acc_total(const cdi_domain *d, const void *acc, cudaStream_t st, double *scal) {
+  if (d->prec == CDI_FP64)
+    k_acc_total<double><<<1, kRedThreads, 0, st>>>((const double *)acc, d->np_accs, scal);
+  else
+    k_acc_total<float2><<<1, kRedThreads, 0, st>>>((const float2 *)acc, d->np_accs, scal);
 }
 
 // Mean of species k over the pore cells of each x column (the column's
@@ -616,15 +653,27 @@ template <typename T> NPConst<T> make_const(const cdi_domain *d) {
 }
 
 NPGeo make_geo(const cdi_domain *d) {
-  return NPGeo{d->d_cmeta, d->d_words, (int)d->n_pore, d->W, d->ny, d->nz, d->walls};
+  return NPGeo{d->d_cmeta, d->d_words, (int)d->n_pore, d->W, d->ny, d->nz, d->walls,
+               d->np_accs};
+}
+
+template <typename T, int DIM, int NS, int BS>
+void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
+  // one thread per pore rank, one account set per warp
+  const int grid = (int)((d->n_pore + BS - 1) / BS);
+  k_np_step<T, DIM, NS, BS><<<grid, BS, 0, st>>>(
+      (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
+      (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
+      (typename AccSlot<T>::type *)d->d_acc);
 }
 
 template <typename T, int DIM, int NS>
 void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
-  // one thread per pore rank; np_blocks blocks, one FP64 account set each
-  k_np_step<T, DIM, NS><<<d->np_blocks, kRowBlock, 0, st>>>(
-      (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
-      (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d), d->d_acc);
+  switch (d->np_block) {
+    case 64: launch_step_bs<T, DIM, NS, 64>(d, st, in); break;
+    case 256: launch_step_bs<T, DIM, NS, 256>(d, st, in); break;
+    default: launch_step_bs<T, DIM, NS, 128>(d, st, in); break;
+  }
 }
 
 template <typename T, int DIM>
@@ -648,6 +697,46 @@ void launch_step(cdi_domain *d, cudaStream_t st, int in) {
 }
 
 constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
+
+// Autotuner: times a few transport steps with each candidate block size on
+// the domain's stream and keeps the fastest.  Accounts are kept per warp of
+// 32 ranks whatever the block size, so every choice computes the same bits.
+// Runs once per domain, before cdi_np_init overwrites the concentrations and
+// clears the accounts.
+cdi_status tune_np(cdi_domain *d) {
+  static const int cand[] = {64, 128, 256};
+  cudaEvent_t a, b;
+  CDI_TRY(d, cudaEventCreate(&a), "tune event");
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cdi_cuda_fail(d, e, "tune event");
+  }
+  float best = 0.f;
+  int best_bs = 128;
+  for (int bs : cand) {
+    d->np_block = bs;
+    launch_step(d, d->stream, 0);  // warm-up
+    e = cudaEventRecord(a, d->stream);
+    for (int k = 0; k < 8 && e == cudaSuccess; k++) launch_step(d, d->stream, k & 1);
+    if (e == cudaSuccess) e = cudaEventRecord(b, d->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) break;
+    d->timing.kernel_launches += 9;
+    if (bs == cand[0] || ms < best) {
+      best = ms;
+      best_bs = bs;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  d->np_block = best_bs;
+  if (e != cudaSuccess) return cdi_cuda_fail(d, e, "tune transport step");
+  d->np_tuned = true;
+  return CDI_OK;
+}
 
 }  // namespace
 
@@ -674,6 +763,10 @@ cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
   }
   d->dt = dt;
   if (dt_used) *dt_used = dt;
+  if (!d->np_tuned) {
+    cdi_status s = tune_np(d);
+    if (s != CDI_OK) return s;
+  }
   if (d->prec == CDI_FP64)
     k_np_init<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
         (double *)d->d_C[0], (double *)d->d_C[1], (int)d->n_pore, d->ns, d->c0);
@@ -772,7 +865,7 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
     hm[m].C[1] = (T *)c1;
     hm[m].u = (const T *)u;
     hm[m].phi = (const typename PhiStore<T>::type *)phi_groups[group[m]];
-    hm[m].acc = (double *)acc;
+    hm[m].acc = (typename AccSlot<T>::type *)acc;
     hm[m].c = make_const<T>(d);
   }
   void *dmem = ok ? take(sizeof(SweepMember<T>) * n) : nullptr;
@@ -830,7 +923,7 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
     k_np_sums<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
         d->d_cmeta, hm[m].C[cur], hm[m].u, (int)d->n_pore, ns, vol, d->d_part,
         d->d_counter + C_MASS, d->d_scal);
-    k_acc_total<<<1, kRedThreads, 0, d->stream>>>(hm[m].acc, d->np_accs, d->d_scal);
+    acc_total(d, hm[m].acc, d->stream, d->d_scal);
     d->timing.kernel_launches += 2;
     cudaError_t e = cudaMemcpyAsync(d->h_scal + S_OUT, d->d_scal + S_OUT,
                                     (S_OUTN - S_OUT + 1) * sizeof(double),
@@ -911,7 +1004,7 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
     hm[m].s.C[1] = (T *)c1;
     hm[m].s.u = (const T *)u;
     hm[m].s.phi = (const typename PhiStore<T>::type *)phis[group[m]];
-    hm[m].s.acc = (double *)acc;
+    hm[m].s.acc = (typename AccSlot<T>::type *)acc;
     hm[m].s.c = make_const<T>(d);
     hm[m].g = make_geo(d);
     hm[m].block0 = total_blocks;
@@ -980,7 +1073,7 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
     k_np_sums<T><<<kRedBlocks, kRedThreads, 0, L->stream>>>(
         d->d_cmeta, hm[m].s.C[cur], hm[m].s.u, (int)d->n_pore, ns, vol, L->d_part,
         L->d_counter + C_MASS, L->d_scal);
-    k_acc_total<<<1, kRedThreads, 0, L->stream>>>(hm[m].s.acc, d->np_accs, L->d_scal);
+    acc_total(d, hm[m].s.acc, L->stream, L->d_scal);
     L->timing.kernel_launches += 2;
     cudaError_t e = cudaMemcpyAsync(L->h_scal + S_OUT, L->d_scal + S_OUT,
                                     (S_OUTN - S_OUT + 1) * sizeof(double),
@@ -1075,7 +1168,7 @@ cdi_status cdi_np_reduce(cdi_domain *d) {
     k_np_sums<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
         d->d_cmeta, (const float *)d->d_C[d->cur], (const float *)d->d_u, (int)d->n_pore,
         d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
-  k_acc_total<<<1, kRedThreads, 0, d->stream>>>(d->d_acc, d->np_accs, d->d_scal);
+  acc_total(d, d->d_acc, d->stream, d->d_scal);
   d->timing.kernel_launches += 2;
   CDI_TRY(d, cudaGetLastError(), "transport sums");
   CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_OUT, d->d_scal + S_OUT,

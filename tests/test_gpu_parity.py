@@ -353,3 +353,20 @@ def test_full_size_1024x512_properties():
     Cr, Gr, _, _ = O.np_run(m, u0, ps, Z, D, c0=10.0, dt=dt_ref, n_steps=200)
     assert rel(C, Cr) < TOL_C32
     assert np.max(np.abs(G - Gr) / Gr) < TOL_G32
+
+
+def test_autotuner_picks_a_block_size():
+    """The step kernels' block sizes are picked by timing on the first solve
+    and reported; the choice changes no result (the determinism test above
+    runs the tuner twice)."""
+    m = inputs.disc_pack_128x64()[0]
+    with cdi.Domain(m, precision=cdi.FP32) as d:
+        t0 = d.timing()
+        assert t0["lbm_block"] == 0 and t0["np_block"] == 0
+        d.solve_flow(tol=0.0, max_steps=200)
+        d.set_potential(1.0)
+        d.init_transport(Z, D, c0=10.0)
+        d.step(10)
+        t = d.timing()
+    assert t["lbm_block"] in (64, 128, 256)
+    assert t["np_block"] in (64, 128, 256)
