@@ -191,6 +191,22 @@ cdi_status cdi_init_transport(cdi_domain *dom, const cdi_species *sp,
                               int n_species, double c0_molm3, double Ka_mps,
                               double dt_s, double *dt_used);
 
+/* Coupled Poisson-Nernst-Planck (Eq. 3-5).  every_steps = K > 0: before
+ * every block of K transport steps (counted from cdi_init_transport),
+ * cdi_step_transport re-solves Eq. 4 with the net charge density of Eq. 5 of
+ * the current concentrations, rho_e = F sum_i z_i C_i, as its source
+ * (Laplace operator, Dirichlet -applied_V at solid faces, 0 in the inlet
+ * feed, no flux at the outlet; eps_r, tolerance and iteration limit of the
+ * last cdi_set_potential), and steps in that potential.  0 (the default):
+ * the potential stays frozen.  Needs cdi_set_potential first (CDI_ERR_STATE).
+ * The explicit scheme resolves the coupling only where the time step is
+ * well below the charge relaxation time eps_r eps_0 / conductivity (an
+ * electric double layer resolved by the grid, as in Sec. 3's validation);
+ * the caller chooses dt accordingly.  With coupling on, cdi_step_transport
+ * waits for the stream at every re-solve.  Sweeps and batches always use
+ * frozen potentials. */
+cdi_status cdi_set_coupling(cdi_domain *dom, int64_t every_steps);
+
 /* Advance n_steps >= 0 explicit steps (Eq. 3 with Eq. 6); asynchronous. */
 cdi_status cdi_step_transport(cdi_domain *dom, int64_t n_steps);
 
@@ -309,6 +325,24 @@ cdi_status cdi_transport_sums_noalloc(const double *C, const double *ux,
                                       const uint8_t *mask, int dim, int nx, int ny,
                                       int nz, int n_species, double dx_m,
                                       double *out, void *stream);
+
+/* Checkpoint of the solver state (no counterpart in the paper; its
+ * transient runs of Sec. 4-5 are long, and a run stopped and resumed gives
+ * the same result bit for bit): the solved flow (populations and lattice
+ * velocity), the potential, the scaled velocity, the transport state with
+ * its adsorbed/inflow/outflow accounts, and the solver scalars (species, c0,
+ * Ka, dt, step counts, coupling).  host_buf NULL: *bytes receives the size
+ * needed.  Otherwise *bytes is the buffer's size on entry (too small:
+ * CDI_ERR_INVALID_ARG with the size needed in *bytes) and the size written on
+ * return.  Host memory of any kind; waits for the stream. */
+cdi_status cdi_save_state(cdi_domain *dom, void *host_buf, size_t *bytes);
+
+/* Restore a state saved by cdi_save_state into a domain created from the
+ * same mask with the same grid options and precision (checked against the
+ * state's header, including a hash of the mask: CDI_ERR_INVALID_ARG if they
+ * differ).  Replaces the flow, potential and transport state; the next
+ * cdi_step_transport continues the saved run.  Waits for the stream. */
+cdi_status cdi_load_state(cdi_domain *dom, const void *host_buf, size_t bytes);
 
 /* Message for the last failed call on dom (NULL: the last failed create on
  * this thread).  Valid until the next call on the same domain. */

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("cdi_init_transport", c_int, [c_void_p, ctypes.POINTER(cdi_species), c_int, c_double,
                                    c_double, c_double, ctypes.POINTER(c_double)]),
     ("cdi_step_transport", c_int, [c_void_p, c_int64]),
+    ("cdi_set_coupling", c_int, [c_void_p, c_int64]),
     ("cdi_sweep_transport", c_int, [c_void_p, ctypes.POINTER(cdi_combo), c_int,
                                     ctypes.POINTER(cdi_elec_params),
                                     ctypes.POINTER(cdi_species), c_int, c_double, c_double,
@@ -105,6 +106,8 @@ SIGNATURES = [
     ("cdi_query_timing", c_int, [c_void_p, ctypes.POINTER(cdi_timing), c_int]),
     ("cdi_transport_sums_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
                                            c_int, c_int, c_double, c_void_p, c_void_p]),
+    ("cdi_save_state", c_int, [c_void_p, c_void_p, ctypes.POINTER(c_size_t)]),
+    ("cdi_load_state", c_int, [c_void_p, c_void_p, c_size_t]),
     ("cdi_last_error", ctypes.c_char_p, [c_void_p]),
     ("cdi_destroy_domain", None, [c_void_p]),
     ("cdi_version", c_int, []),
@@ -237,6 +240,23 @@ def batch(domains, combos, *, z=(1, -1), D=(1.33e-9, 2.03e-9), c0=10.0, Ka=1e-6,
     for d in domains:
         d.ns = 0
     return sweep_batch([d.handle for d in domains], combos, p, z, D, c0, Ka, n_steps)
+
+
+def set_coupling(handle, every_steps: int):
+    _check(load().cdi_set_coupling(handle, c_int64(every_steps)), handle)
+
+
+def save_state(handle) -> bytes:
+    n = c_size_t(0)
+    _check(load().cdi_save_state(handle, None, ctypes.byref(n)), handle)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().cdi_save_state(handle, buf, ctypes.byref(n)), handle)
+    return buf.raw[:n.value]
+
+
+def load_state(handle, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(load().cdi_load_state(handle, buf, c_size_t(len(state))), handle)
 
 
 def query_adsorbed(handle, ns: int) -> np.ndarray:
@@ -444,3 +464,16 @@ class Domain:
 
     def timing(self, reset=False):
         return query_timing(self.handle, reset)
+
+    def set_coupling(self, every_steps: int):
+        """Re-solve the potential from the net charge every ``every_steps``
+        transport steps (Eq. 3-5); 0 freezes it."""
+        set_coupling(self.handle, every_steps)
+
+    def save_state(self) -> bytes:
+        return save_state(self.handle)
+
+    def load_state(self, state: bytes):
+        load_state(self.handle, state)
+        # species count from the state's header (int32 at byte 76)
+        self.ns = int.from_bytes(state[76:80], "little", signed=True)

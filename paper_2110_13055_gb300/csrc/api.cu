@@ -159,8 +159,10 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   if (Nf > (1LL << 31) - 1)
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "grid too large (flow sites >= 2^31)");
   long long n_pore = 0, n_inlet = 0;
+  uint64_t hash = 1469598103934665603ull;
   for (long long i = 0; i < N; i++) {
     if (mask[i] > 1) return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "mask values must be 0 or 1");
+    hash = (hash ^ mask[i]) * 1099511628211ull;
     if (!mask[i]) {
       n_pore++;
       if (i % D.nx == 0) n_inlet++;
@@ -177,6 +179,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->dx = D.dx_m;
   d->NX = NX; d->N = N; d->Nf = Nf;
   d->n_pore = n_pore; d->n_pore_inlet = n_inlet;
+  d->mask_hash = hash;
   if (alloc) {
     d->alloc = *alloc;
     d->has_alloc = true;
@@ -355,13 +358,30 @@ cdi_status cdi_set_potential(cdi_domain *d, double applied_V, const cdi_elec_par
   d->psi_done = false;
   int it = 0;
   double rel = 0.0;
-  cdi_status s = cdi_psi_solve(d, -applied_V, kdx2, p->tol, p->max_iter, &it, &rel);
+  d->psi_s = -applied_V;
+  d->eps_r = p->eps_r;
+  d->psi_tol = p->tol;
+  d->psi_max_iter = p->max_iter;
+  cdi_status s = cdi_psi_solve(d, -applied_V, kdx2, nullptr, p->tol, p->max_iter, &it, &rel);
   if (iters_out) *iters_out = it;
   if (relres_out) *relres_out = rel;
   if (s == CDI_OK || s == CDI_ERR_NOT_CONVERGED) d->psi_done = true;
   if (s == CDI_ERR_NOT_CONVERGED)
     return cdi_fail(d, s, "potential solve did not reach tol within max_iter");
   return s;
+}
+
+cdi_status cdi_set_coupling(cdi_domain *d, int64_t every_steps) {
+  if (!d) return CDI_ERR_INVALID_ARG;
+  if (every_steps < 0) return cdi_fail(d, CDI_ERR_INVALID_ARG, "every_steps < 0");
+  if (every_steps > 0 && !d->psi_done)
+    return cdi_fail(d, CDI_ERR_STATE, "set the potential first (its parameters are reused)");
+  if (every_steps > 0 && !d->d_src) {
+    d->d_src = (double *)cdi_dev_alloc(d, (size_t)d->N * 8);
+    if (!d->d_src) return cdi_fail(d, CDI_ERR_OOM, "coupling: charge buffer");
+  }
+  d->couple_K = every_steps;
+  return CDI_OK;
 }
 
 cdi_status cdi_init_transport(cdi_domain *d, const cdi_species *sp, int n, double c0,

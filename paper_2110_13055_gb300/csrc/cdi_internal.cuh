@@ -223,6 +223,7 @@ struct cdi_domain {
   long long N = 0;    // transport cells nx*ny*nz
   long long Nf = 0;   // flow sites NX*ny*nz
   long long n_pore = 0, n_pore_inlet = 0;
+  uint64_t mask_hash = 0;  // FNV-1a of the mask bytes (identifies a saved state's geometry)
 
   // execution
   cudaStream_t stream = nullptr;
@@ -281,6 +282,12 @@ struct cdi_domain {
   int z[cdi::kMaxSpecies] = {0, 0, 0, 0};
   double D[cdi::kMaxSpecies] = {0, 0, 0, 0};
   double c0 = 0.0, Ka = 0.0, dt = 0.0, VT = 0.0;
+  // potential parameters of the last cdi_set_potential (for the coupled
+  // re-solve) and the coupling period (0: frozen potential)
+  double psi_s = 0.0, eps_r = 78.5, psi_tol = 1e-12;
+  int psi_max_iter = 100000;
+  int64_t couple_K = 0;
+  double *d_src = nullptr;      // N charge terms of Eq. 4 (coupled mode only)
   int cur = 0;                  // which of d_C holds the current state
   int64_t np_steps = 0;
   int np_blocks = 0;            // 128-thread blocks over the pore cells
@@ -352,8 +359,9 @@ cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
                         double *res);
 cdi_status cdi_flow_export(cdi_domain *d, double U_target);
 cdi_status cdi_flow_velocity_lattice(cdi_domain *d);
-cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol,
-                         int max_iter, int *iters, double *relres);
+cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double *src,
+                         double tol, int max_iter, int *iters, double *relres);
+cdi_status cdi_psi_coupled(cdi_domain *d);
 cdi_status cdi_np_build_flags(cdi_domain *d);
 cdi_status cdi_np_build_compact(cdi_domain *d);
 cdi_status cdi_np_scatter(cdi_domain *d, const void *src, int comps, double *dst);

@@ -6,8 +6,10 @@
 // T_f = 1 towards a pore neighbour or the inlet feed (psi = 0), 2 towards a
 // solid face (psi = psi_s at half a cell), 0 at the outlet and lateral walls;
 // kdx2 = (dx / lambda_D)^2 screens the field (Debye-Hueckel linearisation of
-// Eq. 4-5; 0 gives Laplace).  All CG scalars stay on the device; the host only
-// polls the convergence flag every few iterations.
+// Eq. 4-5; 0 gives Laplace).  With the coupling of Eq. 3-5 on, the right-hand
+// side also carries the charge term dx^2 rho_e / (eps_r eps_0) of every pore
+// cell (Eq. 5 from the current concentrations).  All CG scalars stay on the
+// device; the host only polls the convergence flag every few iterations.
 #include <cmath>
 
 #include "cdi_internal.cuh"
@@ -62,7 +64,8 @@ __device__ __forceinline__ void coords(const Geo &g, long long P, int &x, int &y
 
 // diag, right-hand side, x = 0, r = b, z = r / diag, p = z; rz and b.b.
 __global__ void __launch_bounds__(kRedThreads)
-    k_cg_setup(Geo g, const NFlag *__restrict__ fl, double kdx2, double psi_s, double tol,
+    k_cg_setup(Geo g, const NFlag *__restrict__ fl, double kdx2, double psi_s,
+               const double *__restrict__ src, double tol,
                double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
                double *__restrict__ diag, double *__restrict__ part, unsigned int *counter,
                double *scal) {
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kRedThreads)
     }
     int cx, cy, cz;
     coords(g, P, cx, cy, cz);
-    double dg = kdx2, b = 0.0;
+    double dg = kdx2, b = src ? src[P] : 0.0;
     for (int f = 0; f < 2 * g.dim; f++) {
       long long nb;
       const int k = face_kind(g, fl, P, cx, cy, cz, f, &nb);
@@ -204,6 +207,20 @@ __global__ void k_cg_dir(long long N, double *__restrict__ p, const double *__re
     p[P] = zq[P] + beta * p[P];
 }
 
+// The charge term of Eq. 4 at every pore cell from Eq. 5:
+// src = coef * sum_k z_k C_k, coef = F dx^2 / (eps_r eps_0) (lattice order;
+// solid cells keep the 0 the caller cleared).
+template <typename T>
+__global__ void k_charge(int n, int ns, const int *__restrict__ cells, const T *__restrict__ C,
+                         int4 z, double coef, double *__restrict__ src) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int zz[4] = {z.x, z.y, z.z, z.w};
+    double q = 0.0;
+    for (int k = 0; k < ns; k++) q += zz[k] * (double)C[(size_t)k * n + r];
+    src[cells[r]] = coef * q;
+  }
+}
+
 // phi = psi / V_T of every pore rank, in the transport kernel's format.
 template <typename T>
 __global__ void k_phi(int n, const int *__restrict__ cells, const double *__restrict__ psi,
@@ -214,13 +231,13 @@ __global__ void k_phi(int n, const int *__restrict__ cells, const double *__rest
 
 }  // namespace
 
-cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol, int max_iter,
-                         int *iters, double *relres) {
+cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double *src,
+                         double tol, int max_iter, int *iters, double *relres) {
   Geo g{d->nx, d->ny, d->nz, d->dim, d->walls, d->N};
   double *r = d->d_cg, *p = d->d_cg + d->N, *q = d->d_cg + 2 * d->N, *dg = d->d_cg + 3 * d->N;
   cudaEvent_t ev;
   cdi_timing_begin(d, &ev);
-  k_cg_setup<<<kRedBlocks, kRedThreads, 0, d->stream>>>(g, d->d_nflags, kdx2, psi_s, tol,
+  k_cg_setup<<<kRedBlocks, kRedThreads, 0, d->stream>>>(g, d->d_nflags, kdx2, psi_s, src, tol,
                                                          d->d_psi, r, p, dg, d->d_part,
                                                          d->d_counter + C_CG1, d->d_scal);
   d->timing.kernel_launches++;
@@ -272,4 +289,27 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, double tol, i
   if (iters) *iters = it;
   if (relres) *relres = d->h_scal[S_CG_REL];
   return (done || d->h_scal[S_CG_DONE] != 0.0) ? CDI_OK : CDI_ERR_NOT_CONVERGED;
+}
+
+// Coupled re-solve (Eq. 3-5): the charge term of the current concentrations,
+// then Eq. 4 with the Laplace operator and the domain's surface potential.
+cdi_status cdi_psi_coupled(cdi_domain *d) {
+  CDI_TRY(d, cudaMemsetAsync(d->d_src, 0, (size_t)d->N * 8, d->stream), "charge reset");
+  const double F = 96485.0, eps0 = 8.854e-12;
+  const double coef = F * d->dx * d->dx / (d->eps_r * eps0);
+  const int4 z = make_int4(d->z[0], d->z[1], d->z[2], d->z[3]);
+  if (d->prec == CDI_FP64)
+    k_charge<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (int)d->n_pore, d->ns, d->d_cell_list, (const double *)d->d_C[d->cur], z, coef, d->d_src);
+  else
+    k_charge<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (int)d->n_pore, d->ns, d->d_cell_list, (const float *)d->d_C[d->cur], z, coef, d->d_src);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "charge");
+  int it = 0;
+  double rel = 0.0;
+  cdi_status s = cdi_psi_solve(d, d->psi_s, 0.0, d->d_src, d->psi_tol, d->psi_max_iter, &it, &rel);
+  if (s == CDI_ERR_NOT_CONVERGED)
+    return cdi_fail(d, s, "coupled potential did not reach tol within max_iter");
+  return s;
 }

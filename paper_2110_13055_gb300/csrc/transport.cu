@@ -16,6 +16,7 @@
 // Adsorbed / inflow / outflow fluxes are summed per block in FP64 into
 // per-block accumulators (fixed block -> cells map, so the totals are
 // deterministic).
+#include <algorithm>
 #include <cmath>
 
 #include "cdi_internal.cuh"
@@ -1119,8 +1120,37 @@ cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *gr
   return sweep_run<float>(d, n, scale, group, phi_groups, dts, n_steps, gamma, cout);
 }
 
+// Coupled stepping (Eq. 3-5): before every block of couple_K steps (counted
+// from cdi_init_transport) the potential is re-solved from the current
+// concentrations; the steps of a block are plain launches.
+static cdi_status np_steps_coupled(cdi_domain *d, int64_t n) {
+  const int64_t K = d->couple_K;
+  while (n > 0) {
+    if (d->np_steps % K == 0) {
+      if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
+      d->np_graph = nullptr;
+      cdi_status s = cdi_psi_coupled(d);
+      if (s != CDI_OK) return s;
+    }
+    const int64_t block = std::min<int64_t>(n, K - d->np_steps % K);
+    cudaEvent_t ev;
+    cdi_timing_begin(d, &ev);
+    for (int64_t k = 0; k < block; k++) {
+      launch_step(d, d->stream, d->cur);
+      d->cur = 1 - d->cur;
+    }
+    CDI_TRY(d, cudaGetLastError(), "transport step");
+    cdi_timing_end(d, ev, PH_NP, block);
+    d->timing.kernel_launches += block;
+    d->np_steps += block;
+    n -= block;
+  }
+  return CDI_OK;
+}
+
 cdi_status cdi_np_steps(cdi_domain *d, int64_t n) {
   if (n == 0) return CDI_OK;
+  if (d->couple_K > 0) return np_steps_coupled(d, n);
   cudaEvent_t ev;
   cdi_timing_begin(d, &ev);
   int64_t left = n;

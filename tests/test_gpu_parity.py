@@ -370,3 +370,44 @@ def test_autotuner_picks_a_block_size():
         t = d.timing()
     assert t["lbm_block"] in (64, 128, 256)
     assert t["np_block"] in (64, 128, 256)
+
+
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT])
+def test_save_and_load_state_resume_bitwise(prec):
+    """A run stopped after n1 steps, saved, loaded into a fresh domain of the
+    same mask and resumed for n2 steps equals the uninterrupted n1 + n2 run."""
+    m = CASES["ragged37x23"]()
+    n1, n2 = 77, 130
+    with cdi.Domain(m, precision=prec) as a:
+        a.solve_flow(tol=0.0, max_steps=400)
+        a.set_potential(0.8, lambda_D=1.5e-7)
+        a.init_transport(Z, D, c0=10.0)
+        a.step(n1)
+        state = a.save_state()
+        a.step(n2)
+        ref = (a.adsorbed(), a.outlet(), a.mass_balance(), a.C())
+    with cdi.Domain(m, precision=prec) as b:
+        b.load_state(state)
+        b.step(n2)
+        got = (b.adsorbed(), b.outlet(), b.mass_balance(), b.C())
+    for x, y in zip(ref, got):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_load_state_rejects_another_geometry():
+    m = CASES["ragged37x23"]()
+    m2 = m.copy()   # same pore count, one pore cell moved (not in the inlet column)
+    pores = np.argwhere(m[:, 1:] == 0) + [0, 1]
+    solids = np.argwhere(m[:, 1:] == 1) + [0, 1]
+    m2[tuple(pores[0])], m2[tuple(solids[0])] = 1, 0
+    with cdi.Domain(m) as a:
+        a.solve_flow(tol=0.0, max_steps=200)
+        state = a.save_state()
+    with cdi.Domain(m, precision=cdi.FP32) as b:
+        with pytest.raises(cdi.CDIError) as e:
+            b.load_state(state)
+        assert e.value.status == 1
+    with cdi.Domain(m2) as c:
+        with pytest.raises(cdi.CDIError) as e:
+            c.load_state(state)
+        assert e.value.status == 1
