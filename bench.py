@@ -248,16 +248,16 @@ def ours(args, w, mask):
     # dominant kernel and its roofline
     # algorithmic bytes per launch: every pore site of the flow grid reads and
     # writes its Q populations (8 B each for FP64 and FP32 pairs, 4 B for
-    # FP32, 2 B for BF16); odd steps also read its list entry (4 B) and flag
-    # word (2 B in 2D, 4 B in 3D), so a launch averages half of that; every
-    # pore cell of the transport grid
+    # FP32, 2 B for BF16); odd steps also read its Q-1 neighbour ranks (4 B
+    # each), so a launch averages half of that; every pore cell of the
+    # transport grid
     # reads and writes 2 species, reads d velocity components, the 8-byte
     # potential and its 8-byte rank metadata (flags, x, row)
     Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[w["prec"]]
     Tt = 8 if w["prec"] == cdi.FP64 else 4
     Q = 9 if dim == 2 else 19
     n_flow_pore = 2 * n_pore
-    lbm_bytes = n_flow_pore * (Q * 2 * Tp + (4 + (2 if dim == 2 else 4)) / 2)
+    lbm_bytes = n_flow_pore * (Q * 2 * Tp + (Q - 1) * 4 // 2)
     np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 8)
     lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
     np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3

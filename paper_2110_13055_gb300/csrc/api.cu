@@ -222,12 +222,13 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->d_flow_list = (int *)A((size_t)d->n_flow_pore * sizeof(int));
   d->d_cell_list = (int *)A((size_t)n_pore * sizeof(int));
   int *list_work = (int *)A(cdi_lists_work_ints(Nf) * sizeof(int));
+  int *rank_work = (int *)A((size_t)Nf * sizeof(int));
   // populations stored by pore rank: Q * n_flow_pore values
   const size_t nq = (size_t)Q * d->n_flow_pore;
   const size_t Tpop = d->prec == CDI_FP64 ? 8 : d->prec == CDI_BF16_POP ? 2 : 4;
   d->d_g = A(nq * Tpop);
   if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A(nq * 4);
-  d->d_fwords = (uint2 *)A((size_t)((Nf + 31) / 32) * sizeof(uint2));
+  d->d_nbr = (int *)A((size_t)(Q - 1) * d->n_flow_pore * sizeof(int));
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
   // transport fields by pore rank
   d->W = (D.nx + 31) / 32;
@@ -278,9 +279,10 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   if (s == CDI_OK) s = cdi_np_build_flags(d);
   if (s == CDI_OK) s = cdi_build_lists(d, list_work);
   if (s == CDI_OK) s = cdi_np_build_compact(d);
-  if (s == CDI_OK) s = cdi_flow_build_links(d);
+  if (s == CDI_OK) s = cdi_flow_build_links(d, rank_work);
   if (s == CDI_OK) chk(cudaStreamSynchronize(d->stream), "create domain");
   if (s == CDI_OK) {  // the work arrays are needed at create time only
+    cdi_dev_release(d, rank_work);
     cdi_dev_release(d, list_work);
   }
   if (s != CDI_OK) {

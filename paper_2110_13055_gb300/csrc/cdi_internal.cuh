@@ -243,7 +243,7 @@ struct cdi_domain {
   void *d_fflags = nullptr;     // Nf flow flags
   cdi::NFlag *d_nflags = nullptr;  // N face flags
   int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
-  uint2 *d_fwords = nullptr;    // ceil(Nf/32) flow-site words {first rank, pore bits}
+  int *d_nbr = nullptr;         // (Q-1)*n_flow_pore neighbour ranks (-1: solid)
   long long n_flow_pore = 0;
   int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending:
                                 // entry r is the lattice cell of pore rank r
@@ -353,7 +353,7 @@ cudaError_t cdi_timing_resolve(cdi_domain *d);
 // Kernel-side entry points used by the API layer.
 cdi_status cdi_flow_build_flags(cdi_domain *d);
 size_t cdi_lists_work_ints(long long n);
-cdi_status cdi_flow_build_links(cdi_domain *d);
+cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work);
 cdi_status cdi_build_lists(cdi_domain *d, int *work);
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
                         double *res);

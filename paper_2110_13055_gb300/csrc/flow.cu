@@ -142,18 +142,13 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
 }
 
 // Populations are stored compactly by pore rank k (the position of the site
-// in the ascending pore-site list): g[i * n + k].  The odd step finds the
-// rank of the site x_k + e_i from the flat site words: one uint2 per 32
-// consecutive flow sites (lattice order), {rank of the first pore site at or
-// after the word's first site, pore bits}, so rank(site) = first +
-// popc(bits below the site).  Nothing per direction is stored: a site reads
-// its list entry and its flag word instead of Q - 1 neighbour ranks, and the
-// words (Nf / 4 bytes) stay in L2.
+// in the ascending pore-site list): g[i * n + k].  The neighbour table
+// nbr[(i - 1) * n + k] holds the rank of the site x_k + e_i, or -1 when that
+// site is solid or lies beyond a lateral wall (halfway bounce-back).
 //
 // Slot read by direction i at rank k (ODD: the upstream neighbour's opposite
 // slot, or the own slot after a bounce-back), and slot written by the
-// post-collision value of direction i.  nb[j] holds the rank of x_k + e_j,
-// or -1 where that site is solid or beyond a lateral wall (bounce-back).
+// post-collision value of direction i.  nb[j] caches nbr for direction j.
 template <int DIM, bool ODD>
 __device__ __forceinline__ size_t read_slot(const int *nb, int k, int i, long long n) {
   using L = Lat<DIM>;
@@ -171,57 +166,35 @@ __device__ __forceinline__ size_t write_slot(const int *nb, int k, int i, long l
   return (size_t)i * n + dst;
 }
 
-// What the odd step needs to find neighbours.
-template <int DIM> struct FlowLinks {
-  const int *list;                          // rank -> flow site
-  const typename FlowFlag<DIM>::type *fl;   // flag word per flow site
-  const uint2 *words;                       // site words (see above)
-  int NX, ny, nz;
-};
-
-// Rank of the pore flow site `site`.
-__device__ __forceinline__ int site_rank(const uint2 *__restrict__ words, int site) {
-  const uint2 t = __ldg(words + (site >> 5));
-  return (int)t.x + __popc(t.y & ((1u << (site & 31)) - 1u));
-}
-
 // Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
 template <int DIM, bool ODD>
-__device__ __forceinline__ void load_links(const FlowLinks<DIM> &lk, int k,
+__device__ __forceinline__ void load_links(const int *__restrict__ nbr, int k, long long n,
                                            int (&nb)[Lat<DIM>::Q]) {
-  using L = Lat<DIM>;
   nb[0] = k;
   if (ODD) {
-    const int s = lk.list[k];
-    const unsigned f = lk.fl[s];
-    const SiteIdx<DIM> ix(s, f, lk.NX, lk.ny, lk.nz);
 #pragma unroll
-    for (int i = 1; i < L::Q; i++)
-      nb[i] = ((f >> i) & 1u) ? -1
-                              : site_rank(lk.words, ix.nb(L::ex(i), L::ey(i), L::ez(i)));
+    for (int i = 1; i < Lat<DIM>::Q; i++) nb[i] = nbr[(size_t)(i - 1) * n + k];
   }
 }
 
-// Site words of the flow grid: pore bits of sites [32 w, 32 w + 32) and the
-// rank of the first pore site at or after 32 w (binary search of the
-// ascending pore-site list).
+__global__ void k_rank_scatter(const int *__restrict__ list, int n, int *__restrict__ rank) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    rank[list[k]] = k;
+}
+
 template <int DIM>
-__global__ void k_flow_words(const typename FlowFlag<DIM>::type *__restrict__ fl,
-                             const int *__restrict__ list, int n, long long Nf,
-                             long long n_words, uint2 *__restrict__ words) {
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n_words;
-       w += (long long)gridDim.x * blockDim.x) {
-    const long long s0 = w * 32;
-    unsigned bits = 0;
-    for (int b = 0; b < 32 && s0 + b < Nf; b++)
-      if (!(fl[s0 + b] & 1u)) bits |= 1u << b;
-    int lo = 0, hi = n;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((long long)list[mid] < s0) lo = mid + 1;
-      else hi = mid;
-    }
-    words[w] = make_uint2((unsigned)lo, bits);
+__global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
+                        const int *__restrict__ list, int n, const int *__restrict__ rank,
+                        int *__restrict__ nbr, int NX, int ny, int nz) {
+  using L = Lat<DIM>;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int s = list[k];
+    const unsigned f = fl[s];
+    const SiteIdx<DIM> ix(s, f, NX, ny, nz);
+#pragma unroll
+    for (int i = 1; i < L::Q; i++)
+      nbr[(size_t)(i - 1) * n + k] =
+          ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
   }
 }
 
@@ -234,7 +207,7 @@ __global__ void k_flow_words(const typename FlowFlag<DIM>::type *__restrict__ fl
 // chosen per variant so that nothing spills)
 template <typename S, int DIM, bool ODD, int BS>
 __global__ void __launch_bounds__(BS, (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128 / BS)
-    k_lbm_step(S *__restrict__ g, const FlowLinks<DIM> lk, int n,
+    k_lbm_step(S *__restrict__ g, const int *__restrict__ nbr, int n,
                typename Arith<S>::type omega, typename Arith<S>::type fx_half,
                typename Arith<S>::type fsrc) {
   using T = typename Arith<S>::type;
@@ -243,7 +216,7 @@ __global__ void __launch_bounds__(BS, (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) 
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   int nb[Q];
-  load_links<DIM, ODD>(lk, k0, nb);
+  load_links<DIM, ODD>(nbr, k0, n, nb);
   T gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) gi[i] = widen(g[read_slot<DIM, ODD>(nb, k0, i, n)]);
@@ -293,7 +266,7 @@ struct SplitConst {
 template <int DIM, bool ODD, bool TAU1, int BS>
 __global__ void __launch_bounds__(BS)
     k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
-                     const FlowLinks<DIM> lk, int n, SplitConst c) {
+                     const int *__restrict__ nbr, int n, SplitConst c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   // lattice weights as FP32 pairs: rest, axis, diagonal
@@ -304,7 +277,7 @@ __global__ void __launch_bounds__(BS)
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   int nb[Q];
-  load_links<DIM, ODD>(lk, k0, nb);
+  load_links<DIM, ODD>(nbr, k0, n, nb);
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -495,8 +468,7 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   // one thread per pore site of the flow grid (pore rank)
   const int n = (int)d->n_flow_pore;
   const int grid = (n + BS - 1) / BS;
-  const FlowLinks<DIM> lk{d->d_flow_list, (const typename FlowFlag<DIM>::type *)d->d_fflags,
-                          d->d_fwords, d->NX, d->ny, d->nz};
+  const int *lk = d->d_nbr;
   if (M == M_SPLIT) {
     const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
@@ -694,19 +666,24 @@ cdi_status cdi_flow_build_flags(cdi_domain *d) {
   return d->dim == 2 ? build_flags<2>(d) : build_flags<3>(d);
 }
 
-// Site words of the compact population layout (after the pore lists).
-cdi_status cdi_flow_build_links(cdi_domain *d) {
-  const long long n_words = (d->Nf + 31) / 32;
+// Neighbour-rank table of the compact population layout (after the pore
+// lists): rank[site] scattered from the list (rank_work: Nf ints, -1 for
+// solid), then nbr[(i-1) n + k] for every pore rank k and direction i.
+cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work) {
+  const int n = (int)d->n_flow_pore;
+  CDI_TRY(d, cudaMemsetAsync(rank_work, 0xff, (size_t)d->Nf * sizeof(int), d->stream),
+          "rank reset");
+  k_rank_scatter<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_flow_list, n, rank_work);
   if (d->dim == 2)
-    k_flow_words<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, (int)d->n_flow_pore, d->Nf,
-        n_words, d->d_fwords);
+    k_links<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
+        d->ny, d->nz);
   else
-    k_flow_words<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, (int)d->n_flow_pore, d->Nf,
-        n_words, d->d_fwords);
-  d->timing.kernel_launches++;
-  CDI_TRY(d, cudaGetLastError(), "site words");
+    k_links<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
+        d->ny, d->nz);
+  d->timing.kernel_launches += 2;
+  CDI_TRY(d, cudaGetLastError(), "neighbour table");
   return CDI_OK;
 }
 

@@ -63,10 +63,10 @@ def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> in
     Tpop = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[precision]
     nx = mask.shape[-1]
     rows = N // nx
-    flow = (Q * Tpop + 4) * n_fp + Nf * (2 if dim == 2 else 4) + Nf // 4 + dim * Nf * 8
+    flow = (Q * Tpop + (Q - 1) * 4 + 4) * n_fp + Nf * (2 if dim == 2 else 4) + dim * Nf * 8
     transport = n_pore * (4 + 8 + dim * T + 8 + 2 * 4 * T) + rows * ((nx + 31) // 32) * 8
     lattice = N * (1 + 2 + 8 + 4 * 8)                 # mask, face flags, psi, CG vectors
-    work = 2 * ((Nf + 2047) // 2048) * 4               # create-time list work
+    work = Nf * 4 + 2 * ((Nf + 2047) // 2048) * 4     # create-time rank and list work
     return flow + transport + lattice + work + (4 << 20)
 
 
