@@ -354,6 +354,21 @@ __global__ void __launch_bounds__(kRedThreads)
   double v[2] = {0.0, 0.0};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const long long s = list[k];  // populations by rank k, velocity by site s
+    // every load of the site first (the kernel is latency-bound otherwise:
+    // one site per iteration, few resident warps)
+    typename Arith<T>::type gv[L::Q];
+    float lv[L::Q];
+    double uprev[DIM];
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) gv[i] = widen(g[(size_t)i * n + k]);
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) lv[i] = 0.f;
+    if (glo) {
+#pragma unroll
+      for (int i = 1; i < L::Q; i++) lv[i] = glo[(size_t)i * n + k];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; a++) uprev[a] = uflow[(size_t)a * Nf + s];
     double j[3] = {fx_half, 0.0, 0.0};
     if (!std::is_same<T, double>::value) {
       // exact sums of the FP32 values as (sum, error) pairs: the residual
@@ -362,19 +377,18 @@ __global__ void __launch_bounds__(kRedThreads)
       float ms[3] = {0.f, 0.f, 0.f}, mc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 1; i < L::Q; i++) {
-        const float gv = (float)widen(g[(size_t)i * n + k]);
-        const float lv = glo ? glo[(size_t)i * n + k] : 0.f;
+        const float gi = (float)gv[i], li = lv[i];
         if (L::ex(i)) {
-          two_sum_acc(L::ex(i) > 0 ? gv : -gv, ms[0], mc[0]);
-          mc[0] = __fadd_rn(mc[0], L::ex(i) > 0 ? lv : -lv);
+          two_sum_acc(L::ex(i) > 0 ? gi : -gi, ms[0], mc[0]);
+          mc[0] = __fadd_rn(mc[0], L::ex(i) > 0 ? li : -li);
         }
         if (L::ey(i)) {
-          two_sum_acc(L::ey(i) > 0 ? gv : -gv, ms[1], mc[1]);
-          mc[1] = __fadd_rn(mc[1], L::ey(i) > 0 ? lv : -lv);
+          two_sum_acc(L::ey(i) > 0 ? gi : -gi, ms[1], mc[1]);
+          mc[1] = __fadd_rn(mc[1], L::ey(i) > 0 ? li : -li);
         }
         if (DIM == 3 && L::ez(i)) {
-          two_sum_acc(L::ez(i) > 0 ? gv : -gv, ms[2], mc[2]);
-          mc[2] = __fadd_rn(mc[2], L::ez(i) > 0 ? lv : -lv);
+          two_sum_acc(L::ez(i) > 0 ? gi : -gi, ms[2], mc[2]);
+          mc[2] = __fadd_rn(mc[2], L::ez(i) > 0 ? li : -li);
         }
       }
 #pragma unroll
@@ -382,15 +396,15 @@ __global__ void __launch_bounds__(kRedThreads)
     } else {
 #pragma unroll
       for (int i = 0; i < L::Q; i++) {
-        const double gv = (double)widen(g[(size_t)i * n + k]);
-        j[0] += L::ex(i) * gv;
-        j[1] += L::ey(i) * gv;
-        if (DIM == 3) j[2] += L::ez(i) * gv;
+        const double gi = (double)gv[i];
+        j[0] += L::ex(i) * gi;
+        j[1] += L::ey(i) * gi;
+        if (DIM == 3) j[2] += L::ez(i) * gi;
       }
     }
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
-      const double d = j[a] - uflow[(size_t)a * Nf + s];
+      const double d = j[a] - uprev[a];
       v[0] += d * d;
       v[1] += j[a] * j[a];
       uflow[(size_t)a * Nf + s] = j[a];
