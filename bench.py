@@ -57,8 +57,9 @@ WORKLOADS = {
         max_flow=1_000_000),
     "3d-256": dict(
         desc=("3D 256^3 sphere pack r~U[6,12] lu (overlap), porosity 0.45, seed 2; D3Q19 BGK "
-              "tau=1, body force 1e-6 lu, mirror along x; flow capped at 20000 steps (residual "
-              "reported; the 1e-7 target takes O(1e5) steps); 1.2 V, c0=20 mol/m^3, pore-mean "
+              "tau=1, body force 1e-6 lu, mirror along x; Stokes to K-lag residual 1e-7 (FP64 "
+              "residual, K=100; 11200 steps on this pack), capped at 20000; 1.2 V, "
+              "c0=20 mol/m^3, pore-mean "
               "velocity 1e-6 m/s; 20000 Nernst-Planck steps; FP32 storage"),
         mask=lambda: inputs.sphere_pack_256()[0], prec=cdi.FP32, V=1.2, U=1e-6, c0=20.0,
         np_steps=20000, flow_tol=1e-7, max_flow=20000),
