@@ -295,6 +295,7 @@ struct cdi_domain {
                                 // (rounded up to a multiple of 8)
   // block sizes of the step kernels, picked by the autotuners
   int lbm_block = 128, np_block = 128;
+  int np_variant = 1;           // transport launch shape (see tune_np)
   bool lbm_tuned = false, np_tuned = false;
 
   // graphs

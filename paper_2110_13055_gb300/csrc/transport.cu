@@ -321,8 +321,11 @@ __device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io,
   }
 }
 
-template <typename T, int DIM, int NS, int BS>
-__global__ void __launch_bounds__(BS)
+// BS threads per block; MINT > 0 asks the compiler for registers that let
+// MINT threads share an SM (more resident warps for the gathered loads, at
+// the price of a few spilled values).
+template <typename T, int DIM, int NS, int BS, int MINT>
+__global__ void __launch_bounds__(BS, MINT > 0 ? MINT / BS : 1)
     k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
               const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
               typename AccSlot<T>::type *__restrict__ acc) {
@@ -658,11 +661,11 @@ NPGeo make_geo(const cdi_domain *d) {
                d->np_accs};
 }
 
-template <typename T, int DIM, int NS, int BS>
+template <typename T, int DIM, int NS, int BS, int MINT>
 void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   // one thread per pore rank, one account set per warp
   const int grid = (int)((d->n_pore + BS - 1) / BS);
-  k_np_step<T, DIM, NS, BS><<<grid, BS, 0, st>>>(
+  k_np_step<T, DIM, NS, BS, MINT><<<grid, BS, 0, st>>>(
       (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
       (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
       (typename AccSlot<T>::type *)d->d_acc);
@@ -670,10 +673,12 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
 
 template <typename T, int DIM, int NS>
 void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
-  switch (d->np_block) {
-    case 64: launch_step_bs<T, DIM, NS, 64>(d, st, in); break;
-    case 256: launch_step_bs<T, DIM, NS, 256>(d, st, in); break;
-    default: launch_step_bs<T, DIM, NS, 128>(d, st, in); break;
+  switch (d->np_variant) {
+    case 0: launch_step_bs<T, DIM, NS, 64, 0>(d, st, in); break;
+    case 2: launch_step_bs<T, DIM, NS, 256, 0>(d, st, in); break;
+    case 3: launch_step_bs<T, DIM, NS, 64, 1280>(d, st, in); break;
+    case 4: launch_step_bs<T, DIM, NS, 128, 1280>(d, st, in); break;
+    default: launch_step_bs<T, DIM, NS, 128, 0>(d, st, in); break;
   }
 }
 
@@ -699,13 +704,16 @@ void launch_step(cdi_domain *d, cudaStream_t st, int in) {
 
 constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 
-// Autotuner: times a few transport steps with each candidate block size on
-// the domain's stream and keeps the fastest.  Accounts are kept per warp of
-// 32 ranks whatever the block size, so every choice computes the same bits.
-// Runs once per domain, before cdi_np_init overwrites the concentrations and
-// clears the accounts.
+// Autotuner: times a few transport steps with each candidate launch shape
+// (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
+// for 1280 resident threads per SM) on the domain's stream and keeps the
+// fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// the arithmetic of a thread does not depend on its register allocation, so
+// every choice computes the same bits.  Runs once per domain, before
+// cdi_np_init overwrites the concentrations and clears the accounts.
+constexpr int kNpVariantBlock[5] = {64, 128, 256, 64, 128};
 cdi_status tune_np(cdi_domain *d) {
-  static const int cand[] = {64, 128, 256};
+  static const int cand[] = {0, 1, 2, 3, 4};
   cudaEvent_t a, b;
   CDI_TRY(d, cudaEventCreate(&a), "tune event");
   cudaError_t e = cudaEventCreate(&b);
@@ -714,9 +722,9 @@ cdi_status tune_np(cdi_domain *d) {
     return cdi_cuda_fail(d, e, "tune event");
   }
   float best = 0.f;
-  int best_bs = 128;
+  int best_bs = 1;
   for (int bs : cand) {
-    d->np_block = bs;
+    d->np_variant = bs;
     launch_step(d, d->stream, 0);  // warm-up
     e = cudaEventRecord(a, d->stream);
     for (int k = 0; k < 8 && e == cudaSuccess; k++) launch_step(d, d->stream, k & 1);
@@ -733,7 +741,8 @@ cdi_status tune_np(cdi_domain *d) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  d->np_block = best_bs;
+  d->np_variant = best_bs;
+  d->np_block = kNpVariantBlock[best_bs];
   if (e != cudaSuccess) return cdi_cuda_fail(d, e, "tune transport step");
   d->np_tuned = true;
   return CDI_OK;
