@@ -4,18 +4,21 @@
 // Per pore cell P, species k, face f with outward normal n:
 //   pore or ghost neighbour:  P_f = (u_f . n) dx / D_k - z_k (phi_nb - phi_P)
 //                             J   = (D_k/dx) [B(-P_f) C_P - B(P_f) C_nb]
-// (each product is accurate on its own; the equivalent form
-// B(-P)(C_P - C_nb) + P C_nb cancels catastrophically for large |P|)
+//     evaluated for |P_f| < 1/2 as (D_k/dx) [E (C_P - C_nb) + (P_f/2)(C_P + C_nb)]
+//     with the even series E = B(P) + P/2, and otherwise as the two products
+//     (each accurate on its own; B(-P)(C_P - C_nb) + P C_nb would cancel
+//     catastrophically for large |P|)
 //   solid face (Eq. 6):       J   = K_eff C_P,  K_eff = Ka / (1 + Ka dx/(2 D_k))
 //   lateral wall:             J   = 0
 // with B(x) = x / (exp(x) - 1) (exponential fitting of advection and
 // migration against diffusion), u_f the mean of the two cell velocities,
 // phi = psi / V_T (kept to FP64 accuracy; the face difference is rounded to
-// the storage precision only after subtraction).  The inlet ghost holds C = c0,
-// phi = 0, u = u_P; the outlet ghost copies the cell (zero gradient).  Update: C_P -= (dt/dx) sum_f J.
-// Adsorbed / inflow / outflow fluxes are summed per block in FP64 into
-// per-block accumulators (fixed block -> cells map, so the totals are
-// deterministic).
+// the storage precision only after subtraction).  The inlet ghost holds
+// C = c0, phi = 0, u = u_P; the outlet ghost copies the cell (zero gradient).
+// Update: C_P -= (dt/dx) sum_f J.  Fields are stored by pore rank (see
+// NPGeo).  Adsorbed / inflow / outflow fluxes are summed per warp into
+// per-warp accounts (FP64, or FP32 pairs in FP32 storage; a fixed warp ->
+// cells map, so the totals are deterministic).
 #include <algorithm>
 #include <cmath>
 
