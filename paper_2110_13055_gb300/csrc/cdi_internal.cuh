@@ -296,6 +296,7 @@ struct cdi_domain {
   // block sizes of the step kernels, picked by the autotuners
   int lbm_block = 128, np_block = 128;
   int np_variant = 1;           // transport launch shape (see tune_np)
+  int lbm_variant = 1;          // LBM launch shape (see tune_lbm)
   bool lbm_tuned = false, np_tuned = false;
 
   // graphs

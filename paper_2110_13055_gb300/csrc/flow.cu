@@ -205,8 +205,8 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 // (more resident blocks per SM: the step is latency-bound on its scattered
 // loads, so occupancy matters more than a few spare registers; the bound is
 // chosen per variant so that nothing spills)
-template <typename S, int DIM, bool ODD, int BS>
-__global__ void __launch_bounds__(BS, (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128 / BS)
+template <typename S, int DIM, bool ODD, int BS, int MINT>
+__global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128) / BS)
     k_lbm_step(S *__restrict__ g, const int *__restrict__ nbr, int n,
                typename Arith<S>::type omega, typename Arith<S>::type fx_half,
                typename Arith<S>::type fsrc) {
@@ -263,10 +263,10 @@ struct SplitConst {
 
 // The same step with every population stored as an FP32 pair gh + gl and the
 // collision carried out in pair arithmetic.
-template <int DIM, bool ODD, bool TAU1, int BS>
-__global__ void __launch_bounds__(BS)
-    k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
-                     const int *__restrict__ nbr, int n, SplitConst c) {
+template <int DIM, bool ODD, bool TAU1>
+__device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__restrict__ gl,
+                                               const int *__restrict__ nbr, int n,
+                                               const SplitConst &c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   // lattice weights as FP32 pairs: rest, axis, diagonal
@@ -337,6 +337,22 @@ __global__ void __launch_bounds__(BS)
     gh[a] = go.h;
     gl[a] = go.l;
   }
+}
+
+// BS threads per block, registers as the compiler sees fit.
+template <int DIM, bool ODD, bool TAU1, int BS>
+__global__ void __launch_bounds__(BS)
+    k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
+                     const int *__restrict__ nbr, int n, SplitConst c) {
+  lbm_split_body<DIM, ODD, TAU1>(gh, gl, nbr, n, c);
+}
+
+// The same step with registers capped so that MINT threads share an SM.
+template <int DIM, bool ODD, bool TAU1, int BS, int MINT>
+__global__ void __launch_bounds__(BS, MINT / BS)
+    k_lbm_step_split_occ(float *__restrict__ gh, float *__restrict__ gl,
+                         const int *__restrict__ nbr, int n, SplitConst c) {
+  lbm_split_body<DIM, ODD, TAU1>(gh, gl, nbr, n, c);
 }
 
 // Velocity u = j = sum e_i g_i + F/2 from the natural layout, written to
@@ -476,7 +492,7 @@ template <int M> struct ModeT { using T = float; };
 template <> struct ModeT<M_F64> { using T = double; };
 template <> struct ModeT<M_BF16> { using T = __nv_bfloat16; };
 
-template <int M, int DIM, int BS>
+template <int M, int DIM, int BS, int MINT>
 void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   using T = typename ModeT<M>::T;
   // one thread per pore site of the flow grid (pore rank)
@@ -488,33 +504,51 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
                        host_pair(fs * Lat<DIM>::w(1)),
                        host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
-    if (tau == 1.0) {
-      k_lbm_step_split<DIM, false, true, BS><<<grid, BS, 0, st>>>(
-          (float *)d->d_g, d->d_glo, lk, n, c);
-      k_lbm_step_split<DIM, true, true, BS><<<grid, BS, 0, st>>>(
-          (float *)d->d_g, d->d_glo, lk, n, c);
+    float *gh = (float *)d->d_g;
+    if constexpr (MINT == 0) {
+      if (tau == 1.0) {
+        k_lbm_step_split<DIM, false, true, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
+        k_lbm_step_split<DIM, true, true, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
+      } else {
+        k_lbm_step_split<DIM, false, false, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
+        k_lbm_step_split<DIM, true, false, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
+      }
     } else {
-      k_lbm_step_split<DIM, false, false, BS><<<grid, BS, 0, st>>>(
-          (float *)d->d_g, d->d_glo, lk, n, c);
-      k_lbm_step_split<DIM, true, false, BS><<<grid, BS, 0, st>>>(
-          (float *)d->d_g, d->d_glo, lk, n, c);
+      if (tau == 1.0) {
+        k_lbm_step_split_occ<DIM, false, true, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
+                                                                              n, c);
+        k_lbm_step_split_occ<DIM, true, true, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
+                                                                             n, c);
+      } else {
+        k_lbm_step_split_occ<DIM, false, false, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
+                                                                               n, c);
+        k_lbm_step_split_occ<DIM, true, false, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
+                                                                              n, c);
+      }
     }
   } else {
     using A = typename Arith<T>::type;
     const A omega = A(1.0 / tau), fxh = A(0.5 * force);
     const A fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
-    k_lbm_step<T, DIM, false, BS><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh, fsrc);
-    k_lbm_step<T, DIM, true, BS><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh, fsrc);
+    k_lbm_step<T, DIM, false, BS, MINT><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh,
+                                                              fsrc);
+    k_lbm_step<T, DIM, true, BS, MINT><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh,
+                                                             fsrc);
   }
 }
 
 // One even + one odd step with the domain's block size.
 template <int M, int DIM>
 void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) {
-  switch (d->lbm_block) {
-    case 64: step_pair_bs<M, DIM, 64>(d, st, tau, force); break;
-    case 256: step_pair_bs<M, DIM, 256>(d, st, tau, force); break;
-    default: step_pair_bs<M, DIM, 128>(d, st, tau, force); break;
+  // pair storage: registers capped for 1280 threads per SM; single-word
+  // storage: for 1024 (the single-word kernels hold more live values)
+  constexpr int OCC = M == M_SPLIT ? 1280 : 1024;
+  switch (d->lbm_variant) {
+    case 0: step_pair_bs<M, DIM, 64, 0>(d, st, tau, force); break;
+    case 2: step_pair_bs<M, DIM, 256, 0>(d, st, tau, force); break;
+    case 3: step_pair_bs<M, DIM, 64, OCC>(d, st, tau, force); break;
+    case 4: step_pair_bs<M, DIM, 128, OCC>(d, st, tau, force); break;
+    default: step_pair_bs<M, DIM, 128, 0>(d, st, tau, force); break;
   }
 }
 
@@ -523,9 +557,13 @@ void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) 
 // bits (one thread per site, no cross-thread arithmetic), so the choice only
 // changes speed.  Runs once per domain, before its first solve resets the
 // populations.
+constexpr int kLbmVariantBlock[5] = {64, 128, 256, 64, 128};
 template <int M, int DIM>
 cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
-  static const int cand[] = {64, 128, 256};
+  // 64, 128 or 256 threads per block, and 64 or 128 with registers capped
+  // for more resident warps (FP64 storage skips those: too many spills)
+  static const int cand_all[] = {0, 1, 2, 3, 4};
+  const int n_cand = M == M_F64 ? 3 : 5;
   cudaEvent_t a, b;
   CDI_TRY(d, cudaEventCreate(&a), "tune event");
   cudaError_t e = cudaEventCreate(&b);
@@ -534,9 +572,10 @@ cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
     return cdi_cuda_fail(d, e, "tune event");
   }
   float best = 0.f;
-  int best_bs = 128;
-  for (int bs : cand) {
-    d->lbm_block = bs;
+  int best_bs = 1;
+  for (int ci = 0; ci < n_cand; ci++) {
+    const int bs = cand_all[ci];
+    d->lbm_variant = bs;
     launch_step_pair<M, DIM>(d, d->stream, tau, force);  // warm-up
     e = cudaEventRecord(a, d->stream);
     for (int k = 0; k < 6 && e == cudaSuccess; k++) launch_step_pair<M, DIM>(d, d->stream, tau, force);
@@ -546,14 +585,15 @@ cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
     if (e != cudaSuccess) break;
     d->timing.kernel_launches += 14;
-    if (bs == cand[0] || ms < best) {
+    if (ci == 0 || ms < best) {
       best = ms;
       best_bs = bs;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  d->lbm_block = best_bs;
+  d->lbm_variant = best_bs;
+  d->lbm_block = kLbmVariantBlock[best_bs];
   if (e != cudaSuccess) return cdi_cuda_fail(d, e, "tune flow step");
   d->lbm_tuned = true;
   return CDI_OK;

@@ -324,14 +324,12 @@ __device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io,
   }
 }
 
-// BS threads per block; MINT > 0 asks the compiler for registers that let
-// MINT threads share an SM (more resident warps for the gathered loads, at
-// the price of a few spilled values).
-template <typename T, int DIM, int NS, int BS, int MINT>
-__global__ void __launch_bounds__(BS, MINT > 0 ? MINT / BS : 1)
-    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
-              const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
-              typename AccSlot<T>::type *__restrict__ acc) {
+template <typename T, int DIM, int NS>
+__device__ __forceinline__ void np_step_body(const T *__restrict__ Cin, T *__restrict__ Cout,
+                                             const T *__restrict__ u,
+                                             const typename PhiStore<T>::type *__restrict__ phi,
+                                             const NPGeo &g, const NPConst<T> &c,
+                                             typename AccSlot<T>::type *__restrict__ acc) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   T v[3 * NS];
 #pragma unroll
@@ -339,6 +337,26 @@ __global__ void __launch_bounds__(BS, MINT > 0 ? MINT / BS : 1)
   bool io = false;
   if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
   np_account<T, NS>(v, io, acc, r >> 5, g.naccs);
+}
+
+// BS threads per block, registers as the compiler sees fit.
+template <typename T, int DIM, int NS, int BS>
+__global__ void __launch_bounds__(BS)
+    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
+              const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
+              typename AccSlot<T>::type *__restrict__ acc) {
+  np_step_body<T, DIM, NS>(Cin, Cout, u, phi, g, c, acc);
+}
+
+// The same step with registers capped so that MINT threads share an SM (more
+// resident warps for the gathered loads, at the price of a few spilled
+// values).
+template <typename T, int DIM, int NS, int BS, int MINT>
+__global__ void __launch_bounds__(BS, MINT / BS)
+    k_np_step_occ(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
+                  const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
+                  typename AccSlot<T>::type *__restrict__ acc) {
+  np_step_body<T, DIM, NS>(Cin, Cout, u, phi, g, c, acc);
 }
 
 // One member of a fused sweep: its own concentrations, velocity, potential,
@@ -668,10 +686,16 @@ template <typename T, int DIM, int NS, int BS, int MINT>
 void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   // one thread per pore rank, one account set per warp
   const int grid = (int)((d->n_pore + BS - 1) / BS);
-  k_np_step<T, DIM, NS, BS, MINT><<<grid, BS, 0, st>>>(
-      (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
-      (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
-      (typename AccSlot<T>::type *)d->d_acc);
+  if constexpr (MINT == 0)
+    k_np_step<T, DIM, NS, BS><<<grid, BS, 0, st>>>(
+        (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
+        (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
+        (typename AccSlot<T>::type *)d->d_acc);
+  else
+    k_np_step_occ<T, DIM, NS, BS, MINT><<<grid, BS, 0, st>>>(
+        (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
+        (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
+        (typename AccSlot<T>::type *)d->d_acc);
 }
 
 template <typename T, int DIM, int NS>
