@@ -251,15 +251,15 @@ def ours(args, w, mask):
     # writes its Q populations (8 B each for FP64 and FP32 pairs, 4 B for
     # FP32, 2 B for BF16); odd steps also read its Q-1 neighbour ranks (4 B
     # each), so a launch averages half of that; every pore cell of the
-    # transport grid
-    # reads and writes 2 species, reads d velocity components, the 8-byte
-    # potential and its 8-byte rank metadata (flags, x, row)
+    # transport grid reads and writes 2 species, reads d velocity components,
+    # the 8-byte potential, its 8-byte rank metadata (flags, x, row) and its
+    # 2 (d - 1) lateral neighbour ranks (4 B each)
     Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[w["prec"]]
     Tt = 8 if w["prec"] == cdi.FP64 else 4
     Q = 9 if dim == 2 else 19
     n_flow_pore = 2 * n_pore
     lbm_bytes = n_flow_pore * (Q * 2 * Tp + (Q - 1) * 4 // 2)
-    np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 8)
+    np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 8 + 2 * (dim - 1) * 4)
     lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
     np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3
     if tim["flow_ms"] >= tim["np_ms"]:

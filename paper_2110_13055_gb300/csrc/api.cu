@@ -235,6 +235,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   const size_t n_words = (size_t)D.ny * D.nz * d->W;
   d->d_cmeta = (uint2 *)A((size_t)n_pore * sizeof(uint2));
   d->d_words = (uint2 *)A(n_words * sizeof(uint2));
+  d->d_latnb = (int *)A((size_t)2 * (D.dim - 1) * n_pore * sizeof(int));
   d->d_u = A((size_t)D.dim * n_pore * T);
   d->d_psi = (double *)A(N * 8);
   d->d_phi = A((size_t)n_pore * 8);

@@ -251,6 +251,7 @@ struct cdi_domain {
   uint2 *d_words = nullptr;     // ny*nz*W: per 32 cells of a row {rank of the
                                 // first pore cell at or after it, pore bits}
   int W = 0;                    // words per row, ceil(nx / 32)
+  int *d_latnb = nullptr;       // 2*(dim-1)*n_pore lateral neighbour ranks (-1: none)
   void *d_g = nullptr;          // Q*n_flow_pore populations (shifted) by pore rank
   float *d_glo = nullptr;       // their low parts (pair storage only)
   double *d_uflow = nullptr;    // dim*Nf lattice velocity (last check), FP64

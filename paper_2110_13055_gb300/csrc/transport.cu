@@ -177,6 +177,8 @@ __device__ __forceinline__ float phi_diff(float2 nb, float2 pp) {
 struct NPGeo {
   const uint2 *meta;   // per rank {flags | x << 16, row}
   const uint2 *words;  // per 32 cells of a row {first rank, pore bits}
+  const int *lat;      // per lateral face f (y+, y-, z+, z-) and rank r, at
+                       // (f - 2) * n + r: the pore neighbour's rank, or -1
   int n, W, ny, nz, walls;
   int naccs;           // account sets (warps of 32 ranks), the same for any launch shape
 };
@@ -200,9 +202,9 @@ __device__ __forceinline__ bool np_cell(const T *__restrict__ Cin, T *__restrict
   using PT = typename PhiStore<T>::type;
   constexpr int NF = 2 * DIM;
   const unsigned f = meta.x & 0xffffu;
-  const int x = (int)(meta.x >> 16), row = (int)meta.y;
   const size_t n = (size_t)g.n;
-  // neighbour ranks first (x neighbours are the adjacent ranks)
+  // neighbour ranks first (x neighbours are the adjacent ranks, lateral ones
+  // come from the table)
   int Q[NF];
   bool open[NF];
 #pragma unroll
@@ -213,9 +215,10 @@ __device__ __forceinline__ bool np_cell(const T *__restrict__ Cin, T *__restrict
       open[fc] = !solid;
       Q[fc] = (solid || edge) ? r : r + ((fc & 1) ? -1 : 1);
     } else {
-      const bool wall = edge && g.walls;
-      open[fc] = !solid && !wall;
-      Q[fc] = open[fc] ? rank_of(g.words, g.W, lateral_row(f, fc, row, g.ny, g.nz), x) : r;
+      // the lateral neighbour's rank, found once at set-up from the row words
+      const int q = g.lat[(size_t)(fc - 2) * n + r];
+      open[fc] = q >= 0;
+      Q[fc] = q >= 0 ? q : r;
     }
   }
   // every load before any arithmetic (memory-level parallelism)
@@ -621,6 +624,26 @@ __global__ void __launch_bounds__(kRedThreads)
   if (threadIdx.x == 0) out[x] = v[1] > 0.0 ? v[0] / v[1] : 0.0;
 }
 
+// Per pore rank and lateral face (y+, y-, z+, z-): the rank of the pore
+// neighbour across it (rows wrap periodically), or -1 across a solid face or
+// a lateral wall.  The step kernels read it instead of the row words, which
+// saves them a dependent load and the rank arithmetic.
+__global__ void k_lat_nbr(const uint2 *__restrict__ meta, const uint2 *__restrict__ words,
+                          int n, int W, int ny, int nz, int walls, int faces,
+                          int *__restrict__ lat) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const uint2 m = meta[r];
+    const unsigned f = m.x & 0xffffu;
+    const int x = (int)(m.x >> 16), row = (int)m.y;
+    for (int fc = 2; fc < faces; fc++) {
+      const bool solid = (f >> (kFaceBit + fc)) & 1u;
+      const bool wall = ((f >> (kEdgeBit + fc)) & 1u) && walls;
+      lat[(size_t)(fc - 2) * n + r] =
+          (solid || wall) ? -1 : rank_of(words, W, lateral_row(f, fc, row, ny, nz), x);
+    }
+  }
+}
+
 // Per pore rank: its face flags, x and row.
 __global__ void k_cmeta(const NFlag *__restrict__ fl, const int *__restrict__ cells, int n,
                         int nx, uint2 *__restrict__ meta) {
@@ -678,8 +701,8 @@ template <typename T> NPConst<T> make_const(const cdi_domain *d) {
 }
 
 NPGeo make_geo(const cdi_domain *d) {
-  return NPGeo{d->d_cmeta, d->d_words, (int)d->n_pore, d->W, d->ny, d->nz, d->walls,
-               d->np_accs};
+  return NPGeo{d->d_cmeta, d->d_words, d->d_latnb, (int)d->n_pore, d->W, d->ny, d->nz,
+               d->walls, d->np_accs};
 }
 
 template <typename T, int DIM, int NS, int BS, int MINT>
@@ -1285,7 +1308,9 @@ cdi_status cdi_np_build_compact(cdi_domain *d) {
                                                      d->d_cmeta);
   k_words<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list, n, d->nx, d->W,
                                                      n_words, d->d_words);
-  d->timing.kernel_launches += 2;
+  k_lat_nbr<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_cmeta, d->d_words, n, d->W, d->ny,
+                                                       d->nz, d->walls, 2 * d->dim, d->d_latnb);
+  d->timing.kernel_launches += 3;
   CDI_TRY(d, cudaGetLastError(), "compact layout");
   return CDI_OK;
 }
