@@ -181,3 +181,48 @@ def test_outputs():
     C[0, 0, 2] = 7.0
     cm = O.column_means(m, C)
     assert cm[0, 2] == pytest.approx((7 + 3 + 3) / 3)
+
+
+def test_explicit_step_is_an_m_matrix_map_and_marches_to_its_fixed_point():
+    """Brute force on a tiny grid: one explicit step is the affine map
+    C' = A C + b (columns from unit states, b from the empty state).  At the
+    time-step bound A is non-negative (positivity), and every column sum is at
+    most 1 — exactly 1 for a cell with no solid, inlet or outlet face (the
+    update conserves mass).  n steps equal A^n C0 + sum_k A^k b, and a long
+    run reaches the algebraic steady state (I - A)^-1 b."""
+    m = np.zeros((3, 5), np.uint8)
+    m[1, 2] = 1
+    rng = np.random.default_rng(2)
+    u = np.zeros((2,) + m.shape)
+    u[0][m == 0] = 2e-4 * (1 + 0.3 * rng.random(int((m == 0).sum())))
+    ps = np.zeros(m.shape)
+    ps[m == 0] = 0.01 * rng.standard_normal(int((m == 0).sum()))
+    z, Dk, c0, Ka, dx = [1], [1.33e-9], 1.0, 1e-5, 1e-7
+    dt = O.np_dt(m, u, ps, z, Dk, dx=dx, Ka=Ka)
+    pores = np.argwhere(m == 0)
+    n = len(pores)
+
+    def step(Cvec, steps=1):
+        C = np.zeros((1,) + m.shape)
+        for (y, x), v in zip(pores, Cvec):
+            C[0, y, x] = v
+        Cn, *_ = O.np_run(m, u, ps, z, Dk, c0=c0, dt=dt, n_steps=steps, dx=dx, Ka=Ka, C=C)
+        return np.array([Cn[0, y, x] for (y, x) in pores])
+
+    b = step(np.zeros(n))
+    A = np.stack([step(np.eye(n)[j]) - b for j in range(n)], axis=1)
+    assert np.all(A >= -1e-15)
+    col = A.sum(axis=0)
+    assert np.all(col <= 1 + 1e-12)
+    interior = [j for j, (y, x) in enumerate(pores)
+                if 0 < x < m.shape[1] - 1 and not any(
+                    m[(y + dy) % m.shape[0], x + dxx] for dy, dxx in ((0, 1), (0, -1), (1, 0), (-1, 0)))]
+    assert interior
+    np.testing.assert_allclose(col[interior], 1.0, rtol=0, atol=1e-12)
+    C0 = rng.random(n)
+    ref = C0.copy()
+    for _ in range(7):
+        ref = A @ ref + b
+    np.testing.assert_allclose(step(C0, 7), ref, rtol=1e-12, atol=1e-14)
+    steady = np.linalg.solve(np.eye(n) - A, b)
+    np.testing.assert_allclose(step(C0, 20000), steady, rtol=1e-9)
