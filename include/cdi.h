@@ -168,8 +168,9 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
 cdi_status cdi_solve_flow(cdi_domain *dom, const cdi_flow_params *p,
                           int64_t *steps_out, double *residual_out);
 
-/* Rescale the solved Stokes field to another pore-mean velocity (the flow is
- * linear in the force, so one solve serves every velocity).  Requires a
+/* Rescale the solved Stokes field to another pore-mean velocity U = sum(u) /
+ * (N phi) of Sec. 4 (Eq. 2 is linear in the force, so one solve serves every
+ * velocity of the Pe sweeps of Sec. 4.1).  Requires a
  * solved flow; invalidates an initialised transport state. */
 cdi_status cdi_set_velocity(cdi_domain *dom, double U_target_mps);
 
@@ -263,8 +264,9 @@ cdi_status cdi_sweep_batch(cdi_domain *const *doms, int n_doms, const cdi_combo 
                            int n_species, double c0_molm3, double Ka_mps, int64_t n_steps,
                            double *gamma_out, double *cout_out, double *dt_out);
 
-/* Adsorbed amount per species since cdi_init_transport: mol (3D) or mol per
- * metre of depth (2D).  Waits for the stream. */
+/* Adsorbed amount per species since cdi_init_transport (the time integral of
+ * the Eq. 6 flux over the solid faces; the adsorbed amount of Sec. 4.1): mol
+ * (3D) or mol per metre of depth (2D).  Waits for the stream. */
 cdi_status cdi_query_adsorbed(cdi_domain *dom, double *per_species);
 
 /* Outlet concentration per species (Sec. 4.1), flux weighted over the pore
@@ -273,7 +275,8 @@ cdi_status cdi_query_adsorbed(cdi_domain *dom, double *per_species);
 cdi_status cdi_query_outlet(cdi_domain *dom, double *per_species);
 
 /* Per species: dissolved amount M = sum C dx^d, adsorbed Gamma, inflow In
- * and outflow Out (all FP64; M + Gamma + Out - In is conserved).  Any
+ * and outflow Out (all FP64; M + Gamma + Out - In is conserved, since Eq. 3
+ * is solved in conservative form with the Eq. 6 flux at solid faces).  Any
  * pointer may be NULL.  Waits for the stream. */
 cdi_status cdi_query_mass_balance(cdi_domain *dom, double *M, double *Gamma,
                                   double *In, double *Out);
@@ -292,13 +295,15 @@ cdi_status cdi_query_geometry(cdi_domain *dom, double *porosity,
  * the pore cells of each x column into out[nx] (0 for all-solid columns). */
 cdi_status cdi_query_column_means(cdi_domain *dom, int species, double *out);
 
-/* Copy a field to host memory as doubles (layouts in the CDI_FIELD_* list).
+/* Copy a field to host memory as doubles (layouts in the CDI_FIELD_* list):
+ * the fields the paper maps, e.g. the Na+ concentrations of Fig. 13-15.
  * count is the number of doubles host_dst holds; it must match exactly. */
 cdi_status cdi_copy_field(cdi_domain *dom, int field, double *host_dst,
                           size_t count);
 
 /* Device-time counters (CUDA events on the domain stream) since the last
- * reset; waits for the stream.  reset != 0 zeroes them afterwards. */
+ * reset; no counterpart in the paper.  Waits for the stream.  reset != 0
+ * zeroes them afterwards. */
 cdi_status cdi_query_timing(cdi_domain *dom, cdi_timing *out, int reset);
 
 /* Dissolved amount and outlet concentration of caller-owned FP64 device
@@ -337,7 +342,8 @@ cdi_status cdi_transport_sums_noalloc(const double *C, const double *ux,
  * return.  Host memory of any kind; waits for the stream. */
 cdi_status cdi_save_state(cdi_domain *dom, void *host_buf, size_t *bytes);
 
-/* Restore a state saved by cdi_save_state into a domain created from the
+/* Restore a state saved by cdi_save_state (no counterpart in the paper)
+ * into a domain created from the
  * same mask with the same grid options and precision (checked against the
  * state's header, including a hash of the mask: CDI_ERR_INVALID_ARG if they
  * differ).  Replaces the flow, potential and transport state; the next
@@ -345,13 +351,15 @@ cdi_status cdi_save_state(cdi_domain *dom, void *host_buf, size_t *bytes);
 cdi_status cdi_load_state(cdi_domain *dom, const void *host_buf, size_t bytes);
 
 /* Message for the last failed call on dom (NULL: the last failed create on
- * this thread).  Valid until the next call on the same domain. */
+ * this thread).  Valid until the next call on the same domain.  No
+ * counterpart in the paper. */
 const char *cdi_last_error(const cdi_domain *dom);
 
-/* Release the domain and all its device memory.  NULL is ignored. */
+/* Release the domain and all its device memory.  NULL is ignored.  No
+ * counterpart in the paper. */
 void cdi_destroy_domain(cdi_domain *dom);
 
-/* ABI version (major * 100 + minor). */
+/* ABI version (major * 100 + minor); no counterpart in the paper. */
 int cdi_version(void);
 
 #ifdef __cplusplus

@@ -75,3 +75,15 @@ def test_product_path_does_not_import_the_oracle():
             text = open(f).read()
             assert "import oracle" not in text and "from oracle" not in text, f
             assert "cdi_oracle" not in text, f
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration's comment cites the passage of the paper that defines
+    the operation, or says that the paper has no counterpart."""
+    text = open(os.path.join(ROOT, "include", "cdi.h")).read()
+    missing = []
+    for m in re.finditer(r"(/\*(?:(?!\*/).)*\*/)\s*\n(?:[^;/]*?)\b(cdi_\w+)\s*\(", text, flags=re.S):
+        comment = re.sub(r"\s*\n\s*\*\s*", " ", m.group(1))
+        if not re.search(r"Sec\. ?\d|Eq\. ?\d|Fig\. ?\d|no counterpart", comment):
+            missing.append(m.group(2))
+    assert not missing, missing
