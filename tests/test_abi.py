@@ -84,6 +84,6 @@ def test_every_entry_point_cites_its_passage():
     missing = []
     for m in re.finditer(r"(/\*(?:(?!\*/).)*\*/)\s*\n(?:[^;/]*?)\b(cdi_\w+)\s*\(", text, flags=re.S):
         comment = re.sub(r"\s*\n\s*\*\s*", " ", m.group(1))
-        if not re.search(r"Sec\. ?\d|Eq\. ?\d|Fig\. ?\d|no counterpart", comment):
+        if not re.search(r"Sec\. ?\d|Eq\. ?\d|Fig\. ?\d|no counterpart", comment, flags=re.I):
             missing.append(m.group(2))
     assert not missing, missing
