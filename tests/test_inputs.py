@@ -61,3 +61,28 @@ def test_fibre_pack_matches_brute_force():
         m, info = I.fibre_pack(n, phi, dia, seed)
         assert np.array_equal(m, _fibres_brute_force(n, phi, dia, seed))
         assert info.porosity <= phi
+
+
+def test_sweep_and_serve_recipes():
+    """The batched-sweep geometries span 256x256..1024x512 in multiples of 32
+    with porosity in [0.4, 0.7]; the serving requests are half 2D 512^2, half
+    3D n^3 with n in {64, ..., 192}, porosity in [0.4, 0.6], V in [0.2, 1.2];
+    both are reproducible from their seeds."""
+    for seed in range(10, 16):
+        m, info = I.sweep_instance(seed)
+        ny, nx = m.shape
+        assert nx % 32 == 0 and ny % 32 == 0 and 256 <= nx <= 1024 and 256 <= ny <= 512
+        assert 0.38 <= info.porosity <= 0.7
+        assert np.array_equal(m, I.sweep_instance(seed)[0])
+    kinds = []
+    for seed in range(100, 108):
+        m, V = I.serve_instance(seed)
+        assert 0.2 <= V <= 1.2
+        phi = float((m == 0).mean())
+        assert 0.38 <= phi <= 0.6
+        if m.ndim == 2:
+            assert m.shape == (512, 512)
+        else:
+            assert m.shape[0] == m.shape[1] == m.shape[2] and m.shape[0] in (64, 96, 128, 160, 192)
+        kinds.append(m.ndim)
+    assert 2 in kinds and 3 in kinds
