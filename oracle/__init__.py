@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cdi_oracle.c")
+_HDR = os.path.join(_HERE, "cdi_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -48,11 +49,12 @@ def build(force: bool = False) -> str:
     """Compile ``cdi_oracle.c`` into ``_build/liboracle.so`` with gcc."""
     with _lock:
         if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+                and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                       os.path.getmtime(_HDR))):
             return _LIB_PATH
         os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -78,8 +80,24 @@ def _load():
         lib.orc_pnp_run.argtypes = [i, i, i, i, P, i, P, i, P, P, d, d, d, d, d, l, l, d, d,
                                     d, P, P, P, P, P]
         lib.orc_pnp_run.restype = i
+        lib.orc_set_threads.argtypes = [i]
+        lib.orc_set_threads.restype = None
+        lib.orc_threads.argtypes = []
+        lib.orc_threads.restype = i
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's parallel loops (OpenMP).  Results do not
+    depend on the count: parallel loops write disjoint outputs and sums are
+    taken in a fixed order."""
+    _load().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(_load().orc_threads())
 
 
 def _ptr(a: np.ndarray):

@@ -34,6 +34,9 @@
 #include "cdi_oracle.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -101,6 +104,7 @@ static long flow_neighbour(int x, int y, int z, int dx, int dy, int dz,
 /* u = sum_i e_i g_i + F/2 at every pore site; 0 in solid. */
 static void lbm_velocity(const lattice *L, int dim, long N, const uint8_t *solid,
                          const double *g, double fx, double *u) {
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < N; s++) {
     for (int a = 0; a < dim; a++) u[a * N + s] = 0.0;
     if (solid[s]) continue;
@@ -145,7 +149,9 @@ int orc_lbm(int dim, int nx, int ny, int nz, const uint8_t *mask, int mirror,
   double r = NAN;
   int converged = 0;
   while (step < max_steps) {
-    /* one step of Eq. 7: collide (Eq. 8) and push to the neighbours */
+    /* one step of Eq. 7: collide (Eq. 8) and push to the neighbours (every
+     * target slot has exactly one source, so rows may run in any order) */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; z++)
       for (int y = 0; y < ny; y++)
         for (int x = 0; x < NX; x++) {
@@ -248,6 +254,7 @@ static int classify_face(const uint8_t *mask, int nx, int ny, int nz,
 static void psi_apply(int dim, int nx, int ny, int nz, const uint8_t *mask,
                       int walls, double kdx2, const double *v, double *Av) {
   long N = (long)nx * ny * nz;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < nz; z++)
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
@@ -294,6 +301,7 @@ int orc_psi_src(int dim, int nx, int ny, int nz, const uint8_t *mask,
   double *p = (double *)malloc(sizeof(double) * N);
   double *Ap = (double *)malloc(sizeof(double) * N);
   /* right-hand side: the Dirichlet surface potential at solid faces */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < nz; z++)
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
@@ -321,6 +329,7 @@ int orc_psi_src(int dim, int nx, int ny, int nz, const uint8_t *mask,
       double pAp = 0.0;
       for (long P = 0; P < N; P++) pAp += p[P] * Ap[P];
       double alpha = rr / pAp;
+#pragma omp parallel for schedule(static)
       for (long P = 0; P < N; P++) {
         psi[P] += alpha * p[P];
         r[P] -= alpha * Ap[P];
@@ -331,6 +340,7 @@ int orc_psi_src(int dim, int nx, int ny, int nz, const uint8_t *mask,
       rel = sqrt(rr_new / bb);
       if (rel < tol) break;
       double beta = rr_new / rr;
+#pragma omp parallel for schedule(static)
       for (long P = 0; P < N; P++) p[P] = r[P] + beta * p[P];
       rr = rr_new;
     }
@@ -399,6 +409,7 @@ double orc_np_dt(int dim, int nx, int ny, int nz, const uint8_t *mask,
   double *dummyC = (double *)calloc((size_t)N, sizeof(double));
   for (int i = 0; i < ns; i++) {
     double Keff = Ka / (1.0 + Ka * dx / (2.0 * D[i]));
+#pragma omp parallel for collapse(2) schedule(static) reduction(max : maxrate)
     for (int zz = 0; zz < nz; zz++)
       for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
@@ -429,15 +440,21 @@ int orc_np_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
   if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1 || ns < 1) return -1;
   if (dim == 2 && nz != 1) return -1;
   long N = (long)nx * ny * nz;
+  long rows = (long)ny * nz;
   double area = (dim == 2) ? dx : dx * dx; /* face area (per metre in 2D) */
   double *Cn = (double *)malloc(sizeof(double) * N);
+  /* per-row sums of the adsorbed, inflow and outflow fluxes (each row summed
+   * along x, the rows then summed in row order: the same totals whatever
+   * the number of threads) */
+  double *racc = (double *)malloc(sizeof(double) * 3 * rows);
   for (long n = 0; n < n_steps; n++) {
     for (int i = 0; i < ns; i++) {
       double *Ci = C + (long)i * N;
       double Keff = Ka / (1.0 + Ka * dx / (2.0 * D[i]));
-      double gam = 0.0, in = 0.0, out = 0.0;
+#pragma omp parallel for collapse(2) schedule(static)
       for (int zz = 0; zz < nz; zz++)
-        for (int y = 0; y < ny; y++)
+        for (int y = 0; y < ny; y++) {
+          double gam = 0.0, in = 0.0, out = 0.0;
           for (int x = 0; x < nx; x++) {
             long P = ((long)zz * ny + y) * nx + x;
             if (mask[P]) {
@@ -462,13 +479,25 @@ int orc_np_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
             }
             Cn[P] = Ci[P] - dt / dx * sumJ;
           }
+          long row = (long)zz * ny + y;
+          racc[3 * row] = gam;
+          racc[3 * row + 1] = in;
+          racc[3 * row + 2] = out;
+        }
       memcpy(Ci, Cn, sizeof(double) * N);
+      double gam = 0.0, in = 0.0, out = 0.0;
+      for (long row = 0; row < rows; row++) {
+        gam += racc[3 * row];
+        in += racc[3 * row + 1];
+        out += racc[3 * row + 2];
+      }
       Gamma[i] += dt * area * gam;
       In[i] += dt * area * in;
       Out[i] += dt * area * out;
     }
   }
   free(Cn);
+  free(racc);
   return 0;
 }
 
@@ -507,4 +536,21 @@ int orc_pnp_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
   }
   free(src);
   return st < 0 ? st : 0;
+}
+
+/* Number of host threads of the parallel loops (OpenMP; 1 without it). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

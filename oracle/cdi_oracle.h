@@ -77,6 +77,12 @@ int orc_pnp_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
                 double psi_tol, double *C, double *Gamma, double *In, double *Out,
                 double *psi);
 
+/* Host threads used by the loops above (OpenMP).  The loops that run in
+ * parallel write disjoint outputs; sums are formed in a fixed order (per
+ * grid row, then over rows), so results do not depend on the thread count. */
+void orc_set_threads(int n);
+int orc_threads(void);
+
 #ifdef __cplusplus
 }
 #endif
