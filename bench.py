@@ -11,6 +11,12 @@ in MLUPS, with the dominant kernel's bandwidth against the measured HBM peak.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   (the FP64 CPU oracle, as it stands)
+    python bench.py --accuracy [--workload NAME]   (per-field error of the
+        benchmark's storage against FP64 storage at full size and horizon)
+
+The default workload is the 3D 256^3 sphere pack: its working set (2.3 GB of
+populations) is far above the 129 MB L2, so the roofline fraction measures
+HBM bandwidth.  The 2D 1024x512 pack stays reachable with --workload.
 
 Under torchrun each rank runs its own instance (independent problems, no
 data-path collective; weak scaling); rank 0 prints one JSON line.
@@ -192,6 +198,26 @@ def aggregate(elapsed, units):
     return t.item(), u.item()
 
 
+def algorithmic_bytes(prec, dim, n_flow_pore, n_pore, ns=2):
+    """Per-launch algorithmic bytes of the two step kernels, counted from the
+    method alone (populations and fields; SURVEY-style per-site figures):
+    LBM: Q populations read and written per pore site (4 B FP32, 8 B FP64 or
+    an FP32 pair, 2 B BF16); transport: ns concentrations read and written,
+    dim velocity components, the potential (4 B in FP32 storage, 8 B in FP64)
+    and a 1-byte solid mask per pore cell.  Returned beside them, the bytes
+    the compact layout adds per launch: the odd LBM step's neighbour data
+    (averaged over the even/odd pair) and the transport step's potential low
+    words, rank metadata and lateral neighbour ranks."""
+    Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[prec]
+    Tt = 8 if prec == cdi.FP64 else 4
+    Q = 9 if dim == 2 else 19
+    lbm = n_flow_pore * Q * 2 * Tp
+    lbm_layout = n_flow_pore * (Q - 1) * 4 // 2    # odd step: Q-1 neighbour ranks
+    npb = n_pore * (ns * 2 * Tt + dim * Tt + Tt + 1)
+    np_layout = n_pore * ((8 - Tt) + 8 + 2 * (dim - 1) * 4 - 1)
+    return lbm, lbm_layout, npb, np_layout
+
+
 def run_pipeline(dom, w):
     """The hot path on a resident domain; returns the step's counters."""
     steps, res, st = dom.solve_flow(tol=w["flow_tol"], max_steps=w["max_flow"],
@@ -246,29 +272,27 @@ def ours(args, w, mask):
     elapsed = dev_ms / 1e3
     elapsed_all, units_all = aggregate(elapsed, units)
 
-    # dominant kernel and its roofline
-    # algorithmic bytes per launch: every pore site of the flow grid reads and
-    # writes its Q populations (8 B each for FP64 and FP32 pairs, 4 B for
-    # FP32, 2 B for BF16); odd steps also read its Q-1 neighbour ranks (4 B
-    # each), so a launch averages half of that; every pore cell of the
-    # transport grid reads and writes 2 species, reads d velocity components,
-    # the 8-byte potential, its 8-byte rank metadata (flags, x, row) and its
-    # 2 (d - 1) lateral neighbour ranks (4 B each)
-    Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[w["prec"]]
-    Tt = 8 if w["prec"] == cdi.FP64 else 4
-    Q = 9 if dim == 2 else 19
+    # dominant kernel and its roofline: algorithmic bytes per launch (the
+    # method's populations and fields) over the kernel's mean launch time
+    # (CUDA events the library records on the launching stream); the bytes
+    # the compact layout adds are reported beside them, not counted
     n_flow_pore = 2 * n_pore
-    lbm_bytes = n_flow_pore * (Q * 2 * Tp + (Q - 1) * 4 // 2)
-    np_bytes = n_pore * (2 * 2 * Tt + dim * Tt + 8 + 8 + 2 * (dim - 1) * 4)
+    lbm_bytes, lbm_layout, np_bytes, np_layout = algorithmic_bytes(
+        w["prec"], dim, n_flow_pore, n_pore)
     lbm_avg = tim["flow_ms"] / max(tim["flow_launches"], 1) / 1e3
     np_avg = tim["np_ms"] / max(tim["np_launches"], 1) / 1e3
     if tim["flow_ms"] >= tim["np_ms"]:
-        kname, abytes, avg = "k_lbm_step", lbm_bytes, lbm_avg
+        kname, abytes, layout, avg = "k_lbm_step", lbm_bytes, lbm_layout, lbm_avg
     else:
-        kname, abytes, avg = "k_np_step", np_bytes, np_avg
+        kname, abytes, layout, avg = "k_np_step", np_bytes, np_layout, np_avg
     peak, peak_kind = measured_peak_gbs()
     achieved = abytes / avg / 1e9 if avg > 0 else 0.0
     traffic = recorded_traffic(kname, args.workload)
+    # DRAM traffic well below the bytes the kernel touches means the working
+    # set stayed in L2 between launches: then the bound is L2, not HBM
+    bound = "hbm"
+    if traffic is not None and traffic < 0.8 * (abytes + layout):
+        bound = "l2"
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -315,26 +339,79 @@ def ours(args, w, mask):
                    "flow_converged": info["flow_status"] == 0,
                    "np_steps": w["np_steps"], "Gamma_mol_per_m": list(info["Gamma"]),
                    "C_out_molm3": list(info["C_out"]),
-                   "l2": "flushed between steps (256 MB write); working set is L2-resident "
-                         "within a step",
+                   "l2": ("flushed between steps (256 MB write); the populations "
+                          f"({n_flow_pore * (9 if dim == 2 else 19) * {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[w['prec']] / 1e6:.0f} MB) "
+                          + ("exceed the 129 MB L2" if n_flow_pore * (9 if dim == 2 else 19) * 4 > 129e6
+                             else "fit in the 129 MB L2 within a step")),
                    "phase_ms_per_step": {
                        "flow": tim["flow_ms"] / args.steps,
                        "flow_check": tim["flow_check_ms"] / args.steps,
                        "psi": tim["psi_ms"] / args.steps,
                        "np": tim["np_ms"] / args.steps},
                    "wall_s": wall},
-        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+        "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": abytes,
+                     "layout_bytes_per_launch": layout,
                      "avg_launch_us": avg * 1e6,
-                     "other": {"k_lbm_step_GBps": lbm_bytes / lbm_avg / 1e9 if lbm_avg else None,
-                               "k_np_step_GBps": np_bytes / np_avg / 1e9 if np_avg else None}},
+                     "other": {
+                         "k_lbm_step": {"GBps": lbm_bytes / lbm_avg / 1e9 if lbm_avg else None,
+                                        "frac": lbm_bytes / lbm_avg / 1e9 / peak
+                                        if lbm_avg else None,
+                                        "avg_launch_us": lbm_avg * 1e6,
+                                        "algorithmic_bytes_per_launch": lbm_bytes,
+                                        "layout_bytes_per_launch": lbm_layout,
+                                        "block": tim["lbm_block"]},
+                         "k_np_step": {"GBps": np_bytes / np_avg / 1e9 if np_avg else None,
+                                       "frac": np_bytes / np_avg / 1e9 / peak
+                                       if np_avg else None,
+                                       "avg_launch_us": np_avg * 1e6,
+                                       "algorithmic_bytes_per_launch": np_bytes,
+                                       "layout_bytes_per_launch": np_layout,
+                                       "block": tim["np_block"]}}},
         "e2e": e2e,
         "gpu_launches": int(tim["kernel_launches"]),
         "clocks": clk.summary(),
     }
     return line
+
+
+def accuracy(args, w, mask):
+    """Per-field error of the workload's storage precision against FP64
+    storage, both on the GPU, same mask, same parameters, full size and full
+    horizon (flow to its tolerance, all transport steps).  The FP64 path
+    itself matches the FP64 oracle to 1e-11 on the parity cases of the test
+    suite (the oracle cannot run these sizes to convergence)."""
+    import torch
+    torch.cuda.set_device(0)
+
+    def run(prec):
+        with cdi.Domain(mask, precision=prec) as d:
+            t0 = time.perf_counter()
+            info = run_pipeline(d, dict(w, prec=prec))
+            out = dict(info, u=d.u(), C=d.C(), seconds=time.perf_counter() - t0)
+            out["M"], _, out["In"], out["Out"] = d.mass_balance()
+        return out
+
+    ref = run(cdi.FP64)
+    got = run(w["prec"])
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    return {"metric": "per-field relative error vs FP64 storage", "data": "synthetic",
+            "config": {"workload": w["desc"], "name": args.workload},
+            "storage": {cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations",
+                        cdi.BF16_POP: "bf16 populations", cdi.FP64: "fp64"}[w["prec"]],
+            "flow_steps": {"fp64": ref["flow_steps"], "tested": got["flow_steps"]},
+            "flow_residual": {"fp64": ref["flow_residual"], "tested": got["flow_residual"]},
+            "rel_l2_u": rel(got["u"], ref["u"]),
+            "rel_l2_C": [rel(got["C"][k], ref["C"][k]) for k in range(len(ref["C"]))],
+            "rel_Gamma": [float(abs(g - r) / abs(r)) for g, r in zip(got["Gamma"], ref["Gamma"])],
+            "rel_C_out": [float(abs(g - r) / abs(r)) for g, r in zip(got["C_out"], ref["C_out"])],
+            "bars": {"u": 1e-5, "C": 1e-4, "Gamma": 1e-6},
+            "seconds": {"fp64": ref["seconds"], "tested": got["seconds"]}}
 
 
 SWEEP_V = (0.2, 0.6, 1.0, 1.2)
@@ -499,12 +576,14 @@ def serve_bench(args):
     return out
 
 
-def oracle_sample(mask, w, flow_steps, np_steps):
+def oracle_sample(mask, w, flow_steps, np_steps, threads=1):
     """Time the FP64 oracle as it stands on a bounded sample of the workload:
     flow_steps LBM steps on the full flow grid, the potential solve, np_steps
-    transport steps on the full grid.  Returns (MLUPS, seconds, sample text)."""
+    transport steps on the full grid, on `threads` host threads.  Returns
+    (MLUPS, seconds, sample text)."""
     import oracle as O
     O.build()
+    O.set_threads(threads)
     N = mask.size
     t0 = time.perf_counter()
     uf, *_ = O.lbm(mask, tol=0.0, check_every=flow_steps, max_steps=flow_steps)
@@ -515,19 +594,40 @@ def oracle_sample(mask, w, flow_steps, np_steps):
     t = time.perf_counter() - t0
     units = flow_steps * 2 * N + np_steps * N
     return units / t / 1e6, t, (f"{flow_steps} LBM steps on the full {2 * N}-site flow grid + "
-                                f"potential solve + {np_steps} transport steps on {N} cells")
+                                f"potential solve + {np_steps} transport steps on {N} cells, "
+                                f"{threads} host thread{'s' if threads > 1 else ''}")
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baselines(mask, w, flow_steps, np_steps):
+    """The oracle on one host core and on all host cores (OpenMP), each on a
+    bounded sample of the workload (the all-core sample is scaled up by the
+    core count so that both take comparable time)."""
+    cores = host_cores()
+    v1, t1, s1 = oracle_sample(mask, w, flow_steps, np_steps, 1)
+    fs = max(2, (flow_steps * cores) // 2 * 2)
+    v, t, s = oracle_sample(mask, w, fs, max(1, np_steps * cores), cores)
+    return {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": s,
+            "seconds": t,
+            "single_core": {"value": v1, "unit": "MLUPS", "cores": 1, "sample": s1,
+                            "seconds": t1}}
 
 
 def reference(args, w, mask):
     rank, world, local = dist_info()
     if rank != 0:
         return None
-    fs, ns = args.ref_flow_steps, args.ref_np_steps
+    cores = host_cores()
+    fs = max(2, (args.ref_flow_steps * cores) // 2 * 2)
+    ns = max(1, args.ref_np_steps * cores)
     for _ in range(args.warmup):
-        oracle_sample(mask, w, max(2, fs // 10) // 2 * 2, max(1, ns // 10))
+        oracle_sample(mask, w, max(2, fs // 10) // 2 * 2, max(1, ns // 10), cores)
     vals, ts = [], []
     for _ in range(args.steps):
-        v, t, sample = oracle_sample(mask, w, fs, ns)
+        v, t, sample = oracle_sample(mask, w, fs, ns, cores)
         vals.append(v)
         ts.append(t)
     value = float(np.mean(vals))
@@ -537,7 +637,7 @@ def reference(args, w, mask):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": w["desc"], "name": args.workload},
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -549,7 +649,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d-1024x512", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="3d-256", choices=list(WORKLOADS))
+    ap.add_argument("--accuracy", action="store_true",
+                    help="per-field error of the workload's storage against FP64 storage "
+                         "on the GPU, at full size and horizon")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-flow-steps", type=int, default=0,
                     help="oracle sample: LBM steps (0: about 1e8 site updates)")
@@ -591,6 +694,10 @@ def main():
         w["np_steps"] = args.np_steps
         w["desc"] += f" [override: {args.np_steps} transport steps]"
     mask = w["mask"]()
+    if args.accuracy:
+        if rank == 0:
+            print(json.dumps(accuracy(args, w, mask)), flush=True)
+        return
     # bounded oracle sample (10-30 s of single-thread CPU work on any workload)
     if not args.ref_flow_steps:
         args.ref_flow_steps = max(2, int(round(1e8 / (2 * mask.size) / 2)) * 2)
@@ -608,9 +715,7 @@ def main():
     if True:
         line = ours(args, w, mask)
         if line is not None and not args.no_cpu_baseline and world == 1:
-            v, t, sample = oracle_sample(mask, w, args.ref_flow_steps, args.ref_np_steps)
-            line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                                    "sample": sample, "seconds": t}
+            line["cpu_baseline"] = cpu_baselines(mask, w, args.ref_flow_steps, args.ref_np_steps)
         elif line is not None:
             line["cpu_baseline"] = None
     if world > 1:

@@ -323,9 +323,10 @@ cdi_status cdi_query_timing(cdi_domain *dom, cdi_timing *out, int reset);
  * Scratch is a fixed static device array (34,304 bytes per device, held
  * until the process exits); n_species above 4 is rejected with
  * CDI_ERR_INVALID_ARG.  The first call on each device looks up the array's
- * device address, so make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race and must be
- * serialised.  Errors: cdi_last_error(NULL). */
+ * device address, so make that first call before any stream capture; the
+ * address is kept for the process, so calls after a cudaDeviceReset of that
+ * device are not supported.  All calls share the array: calls that overlap
+ * on the GPU race and must be serialised.  Errors: cdi_last_error(NULL). */
 cdi_status cdi_transport_sums_noalloc(const double *C, const double *ux,
                                       const uint8_t *mask, int dim, int nx, int ny,
                                       int nz, int n_species, double dx_m,

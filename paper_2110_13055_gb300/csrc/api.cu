@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "cdi_internal.cuh"
 
@@ -76,6 +78,38 @@ static void free_all(cdi_domain *d) {
   if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
   d->cap_stream = d->stream = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner memory (see cdi_internal.cuh).
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mutex;
+static std::unordered_map<uint64_t, int> g_tune;
+
+uint64_t cdi_tune_key(int kind, int dim, int prec, int ns, long long n, int extra) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    dev = 0;
+  }
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the key fields
+  const long long f[7] = {kind, dim, prec, ns, n, extra, dev};
+  for (long long v : f)
+    for (int b = 0; b < 8; b++) h = (h ^ (uint64_t)((v >> (8 * b)) & 0xff)) * 1099511628211ull;
+  return h;
+}
+
+bool cdi_tune_lookup(uint64_t key, int *variant) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *variant = it->second;
+  return true;
+}
+
+void cdi_tune_store(uint64_t key, int variant) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune[key] = variant;
 }
 
 // ---------------------------------------------------------------------------

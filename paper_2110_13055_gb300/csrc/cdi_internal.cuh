@@ -347,6 +347,14 @@ void cdi_timing_begin(cdi_domain *d, cudaEvent_t *a);
 void cdi_timing_end(cdi_domain *d, cudaEvent_t a, int phase, int64_t launches);
 cudaError_t cdi_timing_resolve(cdi_domain *d);
 
+// Process-wide memory of the autotuners' choices, keyed by the kernel kind,
+// lattice, storage precision, species count, problem size and device: a
+// second domain of the same size runs the kernels the first one picked (so
+// repeated solves time the same code) without re-timing them.
+uint64_t cdi_tune_key(int kind, int dim, int prec, int ns, long long n, int extra);
+bool cdi_tune_lookup(uint64_t key, int *variant);
+void cdi_tune_store(uint64_t key, int variant);
+
 #define CDI_TRY(d, call, what)                           \
   do {                                                   \
     cudaError_t e_ = (call);                             \

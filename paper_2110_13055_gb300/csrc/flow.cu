@@ -564,6 +564,14 @@ cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
   // for more resident warps (FP64 storage skips those: too many spills)
   static const int cand_all[] = {0, 1, 2, 3, 4};
   const int n_cand = M == M_F64 ? 3 : 5;
+  const uint64_t key = cdi_tune_key(1, DIM, M, 0, d->n_flow_pore, tau == 1.0 ? 1 : 0);
+  int known = 0;
+  if (cdi_tune_lookup(key, &known)) {
+    d->lbm_variant = known;
+    d->lbm_block = kLbmVariantBlock[known];
+    d->lbm_tuned = true;
+    return CDI_OK;
+  }
   cudaEvent_t a, b;
   CDI_TRY(d, cudaEventCreate(&a), "tune event");
   cudaError_t e = cudaEventCreate(&b);
@@ -596,6 +604,7 @@ cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
   d->lbm_block = kLbmVariantBlock[best_bs];
   if (e != cudaSuccess) return cdi_cuda_fail(d, e, "tune flow step");
   d->lbm_tuned = true;
+  cdi_tune_store(key, best_bs);
   return CDI_OK;
 }
 

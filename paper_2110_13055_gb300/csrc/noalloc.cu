@@ -39,7 +39,9 @@ double *g_na_ptr[kNaMaxDevices] = {};
 
 // Device address of the scratch on the current device.  The name of the
 // array is only a host-side handle, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  A cudaDeviceReset destroys
+// the context that held the array, and with it the cached address: this
+// entry point is not for use after a reset in the same process.
 cudaError_t na_scratch(double **p) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -69,23 +71,31 @@ __global__ void __launch_bounds__(kRedThreads)
   double v[NV];
 #pragma unroll
   for (int j = 0; j < NV; j++) v[j] = 0.0;
-  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < N;
-       P += (long long)gridDim.x * blockDim.x) {
-    if (mask[P]) continue;
-    const bool outlet = (P % nx) == nx - 1;
-    const double u = ux[P];
-    for (int k = 0; k < ns; k++) {
-      const double ck = C[(size_t)k * N + P];
-      v[k] += ck;
+  // grid-stride loop; the x coordinate advances by the stride modulo nx, so
+  // no division per cell
+  const long long P0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int dxs = (int)(stride % nx);
+  int x = (int)(P0 % nx);
+  for (long long P = P0; P < N; P += stride) {
+    if (!mask[P]) {
+      const bool outlet = x == nx - 1;
+      const double u = outlet ? ux[P] : 0.0;  // the velocity only weights the outlet
+      for (int k = 0; k < ns; k++) {
+        const double ck = C[(size_t)k * N + P];
+        v[k] += ck;
+        if (outlet) {
+          v[kMaxSpecies + k] += u * ck;
+          v[2 * kMaxSpecies + 1 + k] += ck;
+        }
+      }
       if (outlet) {
-        v[kMaxSpecies + k] += u * ck;
-        v[2 * kMaxSpecies + 1 + k] += ck;
+        v[2 * kMaxSpecies] += u;
+        v[NV - 1] += 1.0;
       }
     }
-    if (outlet) {
-      v[2 * kMaxSpecies] += u;
-      v[NV - 1] += 1.0;
-    }
+    x += dxs;
+    if (x >= nx) x -= nx;
   }
   block_reduce<NV>(v, sm, OpSum(), 0.0);
   if (threadIdx.x == 0)

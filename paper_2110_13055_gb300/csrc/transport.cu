@@ -764,6 +764,14 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 constexpr int kNpVariantBlock[5] = {64, 128, 256, 64, 128};
 cdi_status tune_np(cdi_domain *d) {
   static const int cand[] = {0, 1, 2, 3, 4};
+  const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
+  int known = 0;
+  if (cdi_tune_lookup(key, &known)) {
+    d->np_variant = known;
+    d->np_block = kNpVariantBlock[known];
+    d->np_tuned = true;
+    return CDI_OK;
+  }
   cudaEvent_t a, b;
   CDI_TRY(d, cudaEventCreate(&a), "tune event");
   cudaError_t e = cudaEventCreate(&b);
@@ -795,6 +803,7 @@ cdi_status tune_np(cdi_domain *d) {
   d->np_block = kNpVariantBlock[best_bs];
   if (e != cudaSuccess) return cdi_cuda_fail(d, e, "tune transport step");
   d->np_tuned = true;
+  cdi_tune_store(key, best_bs);
   return CDI_OK;
 }
 

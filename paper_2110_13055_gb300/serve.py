@@ -117,6 +117,11 @@ class Server:
     def _run(self, req: Request, need: int):
         req.t_start = time.perf_counter()
         try:
+            # a new host thread starts on device 0: bind it to the server's
+            # device before the request's domain is created there
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.device)
             req.result = self.solver(req)
         except Exception as e:  # a failed request fails alone
             req.error = str(e)

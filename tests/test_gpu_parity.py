@@ -250,6 +250,63 @@ def test_pipeline_3d(prec):
     assert own < (1e-11 if prec == cdi.FP64 else 1e-5)
 
 
+@pytest.fixture(scope="module")
+def spheres48_oracle():
+    """48^3 crop of the 256^3 sphere pack, the benchmark's 3D parameters:
+    flow to the 1e-7 K-lag residual, 1.2 V, c0 = 20 mol/m^3, U = 1e-6 m/s,
+    20,000 transport steps (the benchmark's horizon)."""
+    big, _ = inputs.sphere_pack_256()
+    m = inputs.crop(big, (48, 48, 48))
+    r = O.run_case(m, flow_tol=1e-7, applied_V=1.2, c0=20.0, U_target=1e-6,
+                   n_np_steps=20000)
+    return m, r
+
+
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+def test_pipeline_3d_benchmark_storage_converged(spheres48_oracle, prec):
+    """The 3D benchmark's storage (plain FP32 populations and transport
+    fields) run to convergence and over the full transport horizon on a crop
+    of its own sphere pack: u, C and the adsorbed amount at the stated bars
+    against the oracle; FP64 storage stops at the oracle's check."""
+    m, r = spheres48_oracle
+    g = run_gpu(m, prec, flow_tol=1e-7, max_flow=20000, U=1e-6, V=1.2, c0=20.0, n_np=20000)
+    if prec == cdi.FP64:
+        assert g["flow_steps"] == r["flow_steps"]
+        tolu, tolc, tolg = TOL64, TOL64, 1e-11
+    else:
+        # the FP32 residual is formed in FP64 from FP32 populations; it may
+        # cross the tolerance one check earlier or later
+        assert abs(g["flow_steps"] - r["flow_steps"]) <= 200
+        tolu, tolc, tolg = TOL_U32, TOL_C32, TOL_G32
+    assert rel(g["u"], r["u"]) < tolu
+    assert rel(g["C"], r["C"]) < tolc
+    assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < tolg
+    np.testing.assert_allclose(g["C_out"], r["C_out"], rtol=tolc)
+
+
+@pytest.fixture(scope="module")
+def crop2d_long_oracle():
+    """256x128 crop of the 1024x512 pack with the 2D benchmark's transport
+    parameters (0.8 V, screened potential of the 10 mol/m^3 feed, U = 1e-4
+    m/s) over its full horizon of 50,000 transport steps (fixed 3000-step
+    flow, so the oracle finishes in seconds)."""
+    big, _ = inputs.disc_pack_1024x512()
+    m = inputs.crop(big, (128, 256))
+    r = O.run_case(m, flow_tol=0.0, max_flow_steps=3000, applied_V=0.8, n_np_steps=50000)
+    return m, r
+
+
+def test_pipeline_2d_benchmark_storage_long_horizon(crop2d_long_oracle):
+    """FP32-pair populations and FP32 transport (the 2D benchmark's storage)
+    over the 50,000-step horizon: rounding drift stays inside the bars."""
+    m, r = crop2d_long_oracle
+    g = run_gpu(m, cdi.FP32_SPLIT, flow_tol=0.0, max_flow=3000, V=0.8, n_np=50000)
+    assert rel(g["u"], r["u"]) < TOL_U32
+    assert rel(g["C"], r["C"]) < TOL_C32
+    assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < TOL_G32
+    np.testing.assert_allclose(g["C_out"], r["C_out"], rtol=TOL_C32)
+
+
 # --------------------------------------------------------------------------
 # edge cases and invariants
 # --------------------------------------------------------------------------

@@ -54,9 +54,13 @@ def gpu_coupled(m, h, c, psi0, dt, K, steps, prec):
 @pytest.mark.parametrize("prec,tol", [(cdi.FP64, 1e-9), (cdi.FP32, 1e-4)])
 def test_coupled_half_channel_matches_oracle(prec, tol):
     """Concentrations at the parity bars.  The coupled potential is solved
-    from the charge F (C_Na - C_Cl), a difference of two nearly equal
-    concentrations away from the wall, so in FP32 its relative error is the
-    concentrations' amplified by c / |C_Na - C_Cl|: held to 1e-3 (FP64:
+    (in FP64) from the charge F (C_Na - C_Cl) of Eq. 5, a difference of two
+    nearly equal FP32 concentrations away from the wall: its error is the
+    concentrations' absolute error divided by |C_Na - C_Cl|, i.e. their
+    relative error amplified by c / |C_Na - C_Cl|.  In this channel the
+    charge sits in the resolved double layer, where |C_Na - C_Cl| is of the
+    order of c, so the amplification is of order one: psi is held to twice
+    the spec concentration bar, 2e-4 (measured in FP32: 7.9e-5; FP64:
     1e-9)."""
     m, h, c, psi0, dt, eq10, vt = half_channel(50)
     K, steps = 10, 3001
@@ -64,7 +68,7 @@ def test_coupled_half_channel_matches_oracle(prec, tol):
     Co, _, _, _, pso = O.pnp_run(m, np.zeros((2,) + m.shape), Z, D, c0=c, dt=dt,
                                  n_steps=steps, K=K, psi_s=psi0, dx=h, Ka=0.0)
     assert rel(C, Co) < tol
-    assert rel(ps, pso) < (1e-9 if prec == cdi.FP64 else 1e-3)
+    assert rel(ps, pso) < (1e-9 if prec == cdi.FP64 else 2e-4)
 
 
 def test_coupled_2d_pack_with_flow_matches_oracle():

@@ -21,35 +21,67 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-11  # the FP64 tolerance of the parity tests
 
 
-def test_noalloc_sums_match_domain_queries_on_repeated_calls():
-    import torch
+@pytest.fixture(scope="module", autouse=True)
+def built():
     import __graft_entry__ as g
     g.build()
-    mask = inputs.grain_pack((23, 37), 0.62, 2.0, 4.5, seed=9)[0]
-    with cdi.Domain(mask, precision=cdi.FP64) as d:
-        d.solve_flow(tol=0.0, max_steps=400, U_target=1e-4)
-        d.set_potential(1.0, c_bulk=10.0, lambda_D=1.5e-7, tol=1e-13)
-        d.init_transport(c0=10.0, Ka=1e-6)
-        d.step(300)
-        C = d.C()
-        u = d.u()
-        M_ref, _, _, _ = d.mass_balance()
-        Cout_ref = d.outlet()
+
+
+def _noalloc(C, ux, mask, dx=1e-7):
+    """Two calls in a row of the allocation-free sums on device copies of the
+    host arrays; returns both results."""
+    import torch
     ns = C.shape[0]
-    ny, nx = mask.shape
+    dim = mask.ndim
+    nz = 1 if dim == 2 else mask.shape[0]
+    ny, nx = mask.shape[-2], mask.shape[-1]
     dev = torch.device("cuda", 0)
     Ct = torch.tensor(C, dtype=torch.float64, device=dev).contiguous()
-    ux = torch.tensor(u[0], dtype=torch.float64, device=dev).contiguous()
+    ut = torch.tensor(ux, dtype=torch.float64, device=dev).contiguous()
     mk = torch.tensor(mask, dtype=torch.uint8, device=dev).contiguous()
     out = torch.empty(2 * ns, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    got = []
     for _ in range(2):  # the shared scratch keeps the previous call's contents
         out.fill_(float("nan"))
-        cdi.transport_sums_noalloc(Ct.data_ptr(), ux.data_ptr(), mk.data_ptr(), 2, nx, ny, 1,
-                                   ns, 1e-7, out.data_ptr(), stream.cuda_stream)
+        cdi.transport_sums_noalloc(Ct.data_ptr(), ut.data_ptr(), mk.data_ptr(), dim, nx, ny,
+                                   nz, ns, dx, out.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
-        got = out.cpu().numpy()
+        got.append(out.cpu().numpy())
+    return got
+
+
+def _domain_run(mask, U):
+    with cdi.Domain(mask, precision=cdi.FP64) as d:
+        d.solve_flow(tol=0.0, max_steps=400, U_target=U)
+        d.set_potential(1.0, c_bulk=10.0, lambda_D=1.5e-7, tol=1e-13)
+        d.init_transport(c0=10.0, Ka=1e-6)
+        d.step(300)
+        M_ref, _, _, _ = d.mass_balance()
+        return d.C(), d.u(), M_ref, d.outlet()
+
+
+@pytest.mark.parametrize("shape", [(23, 37), (9, 11, 13)])
+def test_noalloc_sums_match_domain_queries_on_repeated_calls(shape):
+    mask = inputs.grain_pack(shape, 0.62, 2.0, 4.5 if len(shape) == 2 else 3.0, seed=9)[0]
+    C, u, M_ref, Cout_ref = _domain_run(mask, 1e-4)
+    ns = C.shape[0]
+    for got in _noalloc(C, u[0], mask):
         np.testing.assert_allclose(got[:ns], M_ref, rtol=TOL64)
+        np.testing.assert_allclose(got[ns:], Cout_ref, rtol=TOL64)
+
+
+def test_noalloc_plain_outlet_mean_without_flow():
+    """With no flow the outlet concentration falls back to the plain mean
+    over the outlet column's pore cells (checked against numpy)."""
+    mask = inputs.grain_pack((23, 37), 0.62, 2.0, 4.5, seed=9)[0]
+    C, u, M_ref, Cout_ref = _domain_run(mask, 0.0)
+    assert np.all(u == 0.0)
+    ns = C.shape[0]
+    plain = [C[k][:, -1][mask[:, -1] == 0].mean() for k in range(ns)]
+    for got in _noalloc(C, u[0], mask):
+        np.testing.assert_allclose(got[:ns], M_ref, rtol=TOL64)
+        np.testing.assert_allclose(got[ns:], plain, rtol=TOL64)
         np.testing.assert_allclose(got[ns:], Cout_ref, rtol=TOL64)
 
 
