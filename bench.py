@@ -51,13 +51,13 @@ WORKLOADS = {
               "c0=10 mol/m^3, Ka=1e-6 m/s, pore-mean velocity 1e-4 m/s; 50000 explicit "
               "Nernst-Planck steps; FP32 arithmetic: populations stored as FP32 pairs "
               "(plain FP32 stalls at residual 7e-7 with a 4e-5 velocity error here), "
-              "transport fields in FP32"),
+              "transport in FP32 with FP32-pair concentrations"),
         mask=lambda: inputs.disc_pack_1024x512()[0], prec=cdi.FP32_SPLIT, V=0.8, U=1e-4, c0=10.0,
         np_steps=50000, flow_tol=1e-8, max_flow=1_000_000),
     "2d-2048x1024": dict(
         desc=("2D 2048x1024 polydisperse discs r~U[4,16] lu (overlap), porosity 0.5, seed 1; "
               "as 2d-1024x512 but the populations exceed L2; flow to 1e-8; "
-              "50000 Nernst-Planck steps; FP32 pair populations, FP32 transport"),
+              "50000 Nernst-Planck steps; FP32 pair populations and concentrations"),
         mask=lambda: inputs.grain_pack((1024, 2048), 0.5, 4.0, 16.0, seed=1)[0],
         prec=cdi.FP32_SPLIT, V=0.8, U=1e-4, c0=10.0, np_steps=50000, flow_tol=1e-8,
         max_flow=1_000_000),
@@ -66,15 +66,18 @@ WORKLOADS = {
               "tau=1, body force 1e-6 lu, mirror along x; Stokes to K-lag residual 1e-7 (FP64 "
               "residual, K=100; 11200 steps on this pack), capped at 20000; 1.2 V, "
               "c0=20 mol/m^3, pore-mean "
-              "velocity 1e-6 m/s; 20000 Nernst-Planck steps; FP32 storage"),
-        mask=lambda: inputs.sphere_pack_256()[0], prec=cdi.FP32, V=1.2, U=1e-6, c0=20.0,
+              "velocity 1e-6 m/s; 20000 Nernst-Planck steps; FP32 populations, transport "
+              "in FP32 with FP32-pair concentrations (plain FP32 concentrations drift to a "
+              "1e-5 adsorbed-amount error over the 20000 steps)"),
+        mask=lambda: inputs.sphere_pack_256()[0], prec=cdi.FP32_CPAIR, V=1.2, U=1e-6, c0=20.0,
         np_steps=20000, flow_tol=1e-7, max_flow=20000),
     "3d-160": dict(
         desc=("3D 160^3 sphere pack r~U[6,12] lu (overlap), porosity 0.45, seed 2 (a profiling "
               "case of the 256^3 recipe whose populations still exceed L2); D3Q19 tau=1; flow "
               "capped at 20000 steps; 1.2 V, c0=20 mol/m^3; 20000 Nernst-Planck steps; FP32"),
         mask=lambda: inputs.grain_pack((160, 160, 160), 0.45, 6.0, 12.0, seed=2)[0],
-        prec=cdi.FP32, V=1.2, U=1e-6, c0=20.0, np_steps=20000, flow_tol=1e-7, max_flow=20000),
+        prec=cdi.FP32_CPAIR, V=1.2, U=1e-6, c0=20.0, np_steps=20000, flow_tol=1e-7,
+        max_flow=20000),
     "2d-128x64": dict(
         desc=("2D 128x64 non-overlapping discs r=6 lu, porosity 0.6, seed 0; D2Q9 tau=1, "
               "Stokes to residual 1e-8; 1.0 V; Na+/Cl-, c0=10 mol/m^3; 2000 Nernst-Planck "
@@ -208,13 +211,19 @@ def algorithmic_bytes(prec, dim, n_flow_pore, n_pore, ns=2):
     the compact layout adds per launch: the odd LBM step's neighbour data
     (averaged over the even/odd pair) and the transport step's potential low
     words, rank metadata and lateral neighbour ranks."""
-    Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[prec]
+    Tp = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2,
+          cdi.FP32_CPAIR: 4}[prec]
     Tt = 8 if prec == cdi.FP64 else 4
+    Tc = 8 if prec in (cdi.FP64, cdi.FP32_SPLIT, cdi.FP32_CPAIR) else 4  # a pair is 8 B
     Q = 9 if dim == 2 else 19
     lbm = n_flow_pore * Q * 2 * Tp
-    lbm_layout = n_flow_pore * (Q - 1) * 4 // 2    # odd step: Q-1 neighbour ranks
-    npb = n_pore * (ns * 2 * Tt + dim * Tt + Tt + 1)
-    np_layout = n_pore * ((8 - Tt) + 8 + 2 * (dim - 1) * 4 - 1)
+    # odd step: a 4-byte flag word and one 4-byte rank base per lateral row
+    # offset (2 in 2D, 8 in 3D); the even step reads none
+    lbm_layout = n_flow_pore * (4 + 4 * (2 if dim == 2 else 8)) // 2
+    npb = n_pore * (ns * 2 * Tc + dim * Tt + Tt + 1)
+    # potential low words (FP32), 2-byte face flags instead of the mask byte,
+    # 2 (d - 1) lateral neighbour ranks
+    np_layout = n_pore * ((8 - Tt) + 1 + 2 * (dim - 1) * 4)
     return lbm, lbm_layout, npb, np_layout
 
 
@@ -329,8 +338,10 @@ def ours(args, w, mask):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if w["prec"] == cdi.FP64 else "f32",
-        "storage": {cdi.FP64: "fp64", cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations",
+        "dtype": "f64" if w["prec"] == cdi.FP64 else "f32",  # arithmetic type
+        "storage": {cdi.FP64: "fp64", cdi.FP32: "fp32",
+                    cdi.FP32_SPLIT: "fp32-pair populations and concentrations",
+                    cdi.FP32_CPAIR: "fp32 populations, fp32-pair concentrations",
                     cdi.BF16_POP: "bf16 populations, fp32 transport"}[w["prec"]],
         "data": "synthetic",
         "config": {"workload": w["desc"], "name": args.workload,
@@ -340,7 +351,7 @@ def ours(args, w, mask):
                    "np_steps": w["np_steps"], "Gamma_mol_per_m": list(info["Gamma"]),
                    "C_out_molm3": list(info["C_out"]),
                    "l2": ("flushed between steps (256 MB write); the populations "
-                          f"({n_flow_pore * (9 if dim == 2 else 19) * {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[w['prec']] / 1e6:.0f} MB) "
+                          f"({lbm_bytes / 2e6:.0f} MB) "
                           + ("exceed the 129 MB L2" if n_flow_pore * (9 if dim == 2 else 19) * 4 > 129e6
                              else "fit in the 129 MB L2 within a step")),
                    "phase_ms_per_step": {
@@ -402,8 +413,10 @@ def accuracy(args, w, mask):
 
     return {"metric": "per-field relative error vs FP64 storage", "data": "synthetic",
             "config": {"workload": w["desc"], "name": args.workload},
-            "storage": {cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations",
-                        cdi.BF16_POP: "bf16 populations", cdi.FP64: "fp64"}[w["prec"]],
+            "storage": {cdi.FP32: "fp32", cdi.FP32_SPLIT: "fp32-pair populations and "
+                        "concentrations", cdi.FP32_CPAIR: "fp32 populations, fp32-pair "
+                        "concentrations", cdi.BF16_POP: "bf16 populations",
+                        cdi.FP64: "fp64"}[w["prec"]],
             "flow_steps": {"fp64": ref["flow_steps"], "tested": got["flow_steps"]},
             "flow_residual": {"fp64": ref["flow_residual"], "tested": got["flow_residual"]},
             "rel_l2_u": rel(got["u"], ref["u"]),
@@ -533,7 +546,7 @@ def serve_requests(n, seed=100):
             reqs.append(serve.Request(m, V, 1e-4, 2000, precision=cdi.FP32_SPLIT,
                                       flow_tol=1e-8, tag=i))
         else:
-            reqs.append(serve.Request(m, V, 1e-6, 2000, precision=cdi.FP32, flow_tol=1e-7,
+            reqs.append(serve.Request(m, V, 1e-6, 2000, precision=cdi.FP32_CPAIR, flow_tol=1e-7,
                                       max_flow_steps=200_000, c0=20.0, tag=i))
     return reqs
 
@@ -664,7 +677,8 @@ def main():
                          "converging; for short profiling runs")
     ap.add_argument("--np-steps", type=int, default=0,
                     help="override the number of transport steps")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-pair", "bf16"], default=None,
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-pair", "fp32-cpair", "bf16"],
+                    default=None,
                     help="override the workload's storage precision")
     ap.add_argument("--sweep", action="store_true",
                     help="batched parameter sweep against the plain loop (solves/s)")
@@ -685,7 +699,7 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.precision:
         w["prec"] = {"fp64": cdi.FP64, "fp32": cdi.FP32, "fp32-pair": cdi.FP32_SPLIT,
-                     "bf16": cdi.BF16_POP}[args.precision]
+                     "fp32-cpair": cdi.FP32_CPAIR, "bf16": cdi.BF16_POP}[args.precision]
         w["desc"] += f" [override: {args.precision} storage]"
     if args.flow_steps:
         w.update(flow_tol=0.0, max_flow=args.flow_steps)

@@ -65,15 +65,21 @@ typedef enum {
   CDI_FP64 = 0,      /* populations, velocity, potential, concentrations in FP64 */
   CDI_FP32 = 1,      /* the same fields stored and updated in FP32; reductions,
                         the potential solve and all accumulators stay FP64 */
-  CDI_FP32_SPLIT = 2, /* as CDI_FP32, but every population is an unevaluated pair
-                         of FP32 words (hi + lo) updated with error-free FP32
-                         transformations: FP64-class flow accuracy at FP32
-                         arithmetic rates, twice the population memory */
-  CDI_BF16_POP = 3    /* as CDI_FP32, but the populations are stored in BF16
+  CDI_FP32_SPLIT = 2, /* as CDI_FP32, but every population and every
+                         concentration is an unevaluated pair of FP32 words
+                         (hi + lo) updated with error-free FP32
+                         transformations: FP64-class accuracy at FP32
+                         arithmetic rates, twice the memory of those fields */
+  CDI_BF16_POP = 3,   /* as CDI_FP32, but the populations are stored in BF16
                          (shifted, f - w; collision in FP32): half the
                          population bytes of FP32, about 3 significant digits;
                          an option whose flow error is measured and reported,
                          not held to the FP32 bounds */
+  CDI_FP32_CPAIR = 4  /* FP32 populations (as CDI_FP32) and FP32-pair
+                         concentrations (as CDI_FP32_SPLIT): for flows that
+                         converge in plain FP32 while the transport runs many
+                         thousands of steps, over which FP32 rounding of the
+                         concentrations would build up */
 } cdi_precision;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -290,6 +296,34 @@ cdi_status cdi_query_mass_balance(cdi_domain *dom, double *M, double *Gamma,
  * l_c = pi / s, Pe = U l_c / D and Da = Ka l_c / D.  Waits for the stream. */
 cdi_status cdi_query_geometry(cdi_domain *dom, double *porosity,
                               double *specific_surface_per_m);
+
+/* Dimensionless groups and removal figures of Sec. 4 and Sec. 4.1 for the
+ * current transport state (all per species k < n_species, FP64). */
+typedef struct {
+  double porosity;           /* phi = pore cells / cells */
+  double specific_surface;   /* s (1/m), as cdi_query_geometry */
+  double l_c_m;              /* characteristic length l_c = pi / s (Sec. 4) */
+  double U_mps;              /* pore-mean x velocity U = sum(u_x) / (N phi) */
+  double elapsed_s;          /* Delta t: transport steps since cdi_init_transport
+                                times the time step */
+  double Pe[4];              /* Peclet number U l_c / D_k (Sec. 4) */
+  double Da[4];              /* Damkohler number Ka l_c / D_k (Sec. 4) */
+  double removal[4];         /* salt removal P_rm = (C_in - C_out) / C_in with
+                                C_in the feed and C_out the outlet
+                                concentration of cdi_query_outlet (Sec. 4.1) */
+  double amount[4];          /* U A P_rm Delta t / (V_t phi) of Sec. 4.1: A the
+                                inlet cross-section (ny dx per metre of depth
+                                in 2D, ny nz dx^2 in 3D), V_t = nx ny nz dx^d
+                                the electrode volume; dimensionless (times
+                                C_in: mol removed per m^3 of pore space) */
+} cdi_derived;
+
+/* The Pe, Da, l_c, U, P_rm and adsorbed-amount figures the paper reports
+ * (Sec. 4: Pe = U l_c / D, Da = Ka l_c / D, U = sum u / (N phi), l_c =
+ * pi / s; Sec. 4.1: P_rm and U A P_rm Delta t / (V_t phi)), evaluated for the
+ * domain's geometry, velocity field and transport state.  Needs an
+ * initialised transport (CDI_ERR_STATE).  Waits for the stream. */
+cdi_status cdi_query_derived(cdi_domain *dom, cdi_derived *out);
 
 /* Vertically averaged profile (Fig. 6, Fig. 9): the mean of species k over
  * the pore cells of each x column into out[nx] (0 for all-solid columns). */

@@ -344,6 +344,65 @@ def column_means(mask, C):
     return np.array(out)
 
 
+def porosity(mask):
+    """phi = pore cells / cells (Sec. 4)."""
+    m = _mask(mask)
+    return float(np.count_nonzero(m == 0)) / m.size
+
+
+def interface_faces(mask, lateral_walls=False):
+    """Voxel faces between a pore cell and a solid cell of the image (the
+    staircase interface).  Faces across the inlet and outlet planes (x) are
+    not interface; across the lateral image boundary the neighbour wraps
+    periodically, unless the lateral boundary is a wall (then none)."""
+    m = _mask(mask).astype(bool)
+    total = 0
+    for ax in range(m.ndim):
+        x_axis = ax == m.ndim - 1
+        n = m.shape[ax]
+        for lo in range(n):
+            hi = lo + 1
+            if hi == n:
+                if x_axis or lateral_walls:
+                    continue
+                hi = 0
+            a = np.take(m, lo, axis=ax)
+            b = np.take(m, hi, axis=ax)
+            total += int(np.count_nonzero(a != b))
+    return total
+
+
+def specific_surface(mask, dx, lateral_walls=False):
+    """s = pore-solid interface area / image volume (1/m; in 2D interface
+    length / image area), the s of Sec. 4's l_c = pi / s."""
+    m = _mask(mask)
+    return interface_faces(m, lateral_walls) * dx ** (m.ndim - 1) / (m.size * dx ** m.ndim)
+
+
+def derived(mask, u, C_out, *, c0, D, Ka, dx, dt, n_steps, lateral_walls=False):
+    """The figures of Sec. 4 and Sec. 4.1 for a transport state: porosity phi,
+    specific surface s, l_c = pi / s, the pore-mean velocity U = sum u_x /
+    (N phi), elapsed time Delta t = n_steps dt, and per species Pe = U l_c / D,
+    Da = Ka l_c / D, the salt removal P_rm = (C_in - C_out) / C_in (C_in the
+    feed c0) and the adsorbed amount U A P_rm Delta t / (V_t phi) with A the
+    inlet cross-section (ny dx per metre of depth in 2D, ny nz dx^2 in 3D) and
+    V_t the electrode volume N dx^d."""
+    m = _mask(mask)
+    D = np.atleast_1d(np.asarray(D, dtype=np.float64))
+    C_out = np.atleast_1d(np.asarray(C_out, dtype=np.float64))
+    phi = porosity(m)
+    s = specific_surface(m, dx, lateral_walls)
+    l_c = np.pi / s
+    U = float(np.asarray(u)[0][m == 0].sum()) / (m.size * phi)
+    elapsed = n_steps * dt
+    A = m.shape[0] * dx if m.ndim == 2 else m.shape[0] * m.shape[1] * dx * dx
+    Vt = m.size * dx ** m.ndim
+    P_rm = (c0 - C_out) / c0
+    return dict(porosity=phi, specific_surface=s, l_c_m=l_c, U_mps=U, elapsed_s=elapsed,
+                Pe=U * l_c / D, Da=Ka * l_c / D, removal=P_rm,
+                amount=U * A * P_rm * elapsed / (Vt * phi))
+
+
 def run_case(mask, *, mirror=True, lateral_walls=False, tau=1.0, force=1e-6,
              flow_tol=1e-8, check_every=100, max_flow_steps=2_000_000,
              U_target=1e-4, applied_V=1.0, c0=10.0, z=(1, -1),

@@ -21,7 +21,7 @@ c_int, c_double, c_size_t, c_int64, c_void_p = (ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_size_t, ctypes.c_int64,
                                                 ctypes.c_void_p)
 
-FP64, FP32, FP32_SPLIT, BF16_POP = 0, 1, 2, 3
+FP64, FP32, FP32_SPLIT, BF16_POP, FP32_CPAIR = 0, 1, 2, 3, 4
 FIELD_U_LATTICE, FIELD_U, FIELD_PSI, FIELD_C = 0, 1, 2, 3
 STATUS = {0: "CDI_OK", 1: "CDI_ERR_INVALID_ARG", 2: "CDI_ERR_OOM", 3: "CDI_ERR_CUDA",
           4: "CDI_ERR_NOT_CONVERGED", 5: "CDI_ERR_TIMEOUT", 6: "CDI_ERR_STATE"}
@@ -57,6 +57,12 @@ class cdi_species(ctypes.Structure):
 
 class cdi_combo(ctypes.Structure):
     _fields_ = [("U_mps", c_double), ("applied_V", c_double)]
+
+
+class cdi_derived(ctypes.Structure):
+    _fields_ = [("porosity", c_double), ("specific_surface", c_double), ("l_c_m", c_double),
+                ("U_mps", c_double), ("elapsed_s", c_double), ("Pe", c_double * 4),
+                ("Da", c_double * 4), ("removal", c_double * 4), ("amount", c_double * 4)]
 
 
 class cdi_timing(ctypes.Structure):
@@ -100,6 +106,7 @@ SIGNATURES = [
     ("cdi_query_outlet", c_int, [c_void_p, c_void_p]),
     ("cdi_query_mass_balance", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("cdi_query_column_means", c_int, [c_void_p, c_int, c_void_p]),
+    ("cdi_query_derived", c_int, [c_void_p, ctypes.POINTER(cdi_derived)]),
     ("cdi_query_geometry", c_int, [c_void_p, ctypes.POINTER(c_double),
                                    ctypes.POINTER(c_double)]),
     ("cdi_copy_field", c_int, [c_void_p, c_int, c_void_p, c_size_t]),
@@ -284,6 +291,18 @@ def query_geometry(handle):
     return phi.value, s.value
 
 
+def query_derived(handle, ns: int) -> dict:
+    """Pe, Da, l_c, U, salt removal and the adsorbed-amount figure of Sec. 4
+    and 4.1 (per-species entries cut to the domain's species)."""
+    d = cdi_derived()
+    _check(load().cdi_query_derived(handle, ctypes.byref(d)), handle)
+    out = {}
+    for name, _ in cdi_derived._fields_:
+        v = getattr(d, name)
+        out[name] = np.array(v[:ns]) if not isinstance(v, float) else v
+    return out
+
+
 def query_column_means(handle, species: int, nx: int) -> np.ndarray:
     out = np.zeros(nx)
     _check(load().cdi_query_column_means(handle, species, _dptr(out)), handle)
@@ -444,6 +463,10 @@ class Domain:
     def geometry(self):
         """(porosity, specific surface in 1/m)."""
         return query_geometry(self.handle)
+
+    def derived(self):
+        """Pe, Da, l_c, U, salt removal and adsorbed amount (Sec. 4, 4.1)."""
+        return query_derived(self.handle, self.ns)
 
     def u_lattice(self):
         flow_shape = (self.NX,) if self.dim == 2 else (self.NX,)

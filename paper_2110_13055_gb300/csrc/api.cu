@@ -183,7 +183,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   if (!(D.dx_m > 0.0) || !std::isfinite(D.dx_m))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "dx_m must be positive");
   if (D.precision != CDI_FP64 && D.precision != CDI_FP32 && D.precision != CDI_FP32_SPLIT &&
-      D.precision != CDI_BF16_POP)
+      D.precision != CDI_BF16_POP && D.precision != CDI_FP32_CPAIR)
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "unknown precision");
   if (alloc && (!alloc->alloc || !alloc->free))
     return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "allocator needs alloc and free");
@@ -210,6 +210,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->walls = D.lateral_walls ? 1 : 0;
   d->mirror = D.mirror_x ? 1 : 0;
   d->prec = D.precision;
+  d->cpair = D.precision == CDI_FP32_SPLIT || D.precision == CDI_FP32_CPAIR;
   d->dx = D.dx_m;
   d->NX = NX; d->N = N; d->Nf = Nf;
   d->n_pore = n_pore; d->n_pore_inlet = n_inlet;
@@ -242,8 +243,13 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   const int Q = D.dim == 2 ? 9 : 19;
   const size_t fflag = D.dim == 2 ? 2 : 4;
   d->n_flow_pore = n_pore * (D.mirror_x ? 2 : 1);
-  d->np_blocks = (int)((n_pore + cdi::kRowBlock - 1) / cdi::kRowBlock);
-  d->np_accs = (int)((n_pore + 255) / 256) * 8;  // enough warps for any block size <= 256
+  {
+    // FP32 steps run warps of 31 home cells, FP64 steps one thread per cell
+    const long long warps31 = (n_pore + 30) / 31;
+    const long long units = d->prec == CDI_FP64 ? n_pore : warps31 * 32;
+    d->np_blocks = (int)((units + cdi::kRowBlock - 1) / cdi::kRowBlock);
+    d->np_accs = (int)((warps31 + 7) / 8) * 8;  // >= the warps of any launch shape
+  }
   bool ok = true;
   auto A = [&](size_t bytes) {
     void *p = cdi_dev_alloc(d, bytes);
@@ -262,12 +268,16 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   const size_t Tpop = d->prec == CDI_FP64 ? 8 : d->prec == CDI_BF16_POP ? 2 : 4;
   d->d_g = A(nq * Tpop);
   if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A(nq * 4);
-  d->d_nbr = (int *)A((size_t)(Q - 1) * d->n_flow_pore * sizeof(int));
+  d->n_lovf = 2 * D.ny * D.nz;
+  d->d_lf = (unsigned *)A((size_t)d->n_flow_pore * sizeof(unsigned));
+  d->d_lr = (int *)A((size_t)(D.dim == 2 ? 2 : 8) * d->n_flow_pore * sizeof(int));
+  d->d_lovf = (int *)A((size_t)(Q - 1) * d->n_lovf * sizeof(int));
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
   // transport fields by pore rank
   d->W = (D.nx + 31) / 32;
   const size_t n_words = (size_t)D.ny * D.nz * d->W;
   d->d_cmeta = (uint2 *)A((size_t)n_pore * sizeof(uint2));
+  d->d_cfl = (cdi::NFlag *)A((size_t)n_pore * sizeof(cdi::NFlag));
   d->d_words = (uint2 *)A(n_words * sizeof(uint2));
   d->d_latnb = (int *)A((size_t)2 * (D.dim - 1) * n_pore * sizeof(int));
   d->d_u = A((size_t)D.dim * n_pore * T);
@@ -275,6 +285,10 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->d_phi = A((size_t)n_pore * 8);
   d->d_C[0] = A((size_t)cdi::kMaxSpecies * n_pore * T);
   d->d_C[1] = A((size_t)cdi::kMaxSpecies * n_pore * T);
+  if (d->cpair) {
+    d->d_Clo[0] = (float *)A((size_t)cdi::kMaxSpecies * n_pore * 4);
+    d->d_Clo[1] = (float *)A((size_t)cdi::kMaxSpecies * n_pore * 4);
+  }
   d->d_acc = (double *)A((size_t)3 * cdi::kMaxSpecies * d->np_accs * 8);
   d->d_part = (double *)A((size_t)16 * cdi::kRedBlocks * 8);
   d->d_counter = (unsigned int *)A(16 * sizeof(unsigned int));
@@ -308,6 +322,9 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   chk(cudaMemsetAsync(d->d_phi, 0, (size_t)n_pore * 8, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_C[0], 0, (size_t)cdi::kMaxSpecies * n_pore * T, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_C[1], 0, (size_t)cdi::kMaxSpecies * n_pore * T, d->stream), "memset");
+  for (int b = 0; b < 2 && d->cpair; b++)
+    chk(cudaMemsetAsync(d->d_Clo[b], 0, (size_t)cdi::kMaxSpecies * n_pore * 4, d->stream),
+        "memset");
   chk(cudaMemsetAsync(d->d_acc, 0, (size_t)3 * cdi::kMaxSpecies * d->np_accs * 8, d->stream),
       "memset");
   if (s == CDI_OK) s = cdi_flow_build_flags(d);
@@ -644,10 +661,41 @@ cdi_status cdi_query_outlet(cdi_domain *d, double *per_species) {
 cdi_status cdi_query_geometry(cdi_domain *d, double *porosity, double *s_per_m) {
   if (!d || !porosity || !s_per_m) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
   double pores = 0.0, faces = 0.0;
-  cdi_status s = cdi_np_geometry(d, &pores, &faces);
+  cdi_status s = cdi_np_geometry(d, &pores, &faces, nullptr);
   if (s != CDI_OK) return s;
   *porosity = pores / (double)d->N;
   *s_per_m = faces / ((double)d->N * d->dx);
+  return CDI_OK;
+}
+
+cdi_status cdi_query_derived(cdi_domain *d, cdi_derived *out) {
+  if (!d || !out) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (!d->np_ready) return cdi_fail(d, CDI_ERR_STATE, "no transport state");
+  double pores = 0.0, faces = 0.0, sum_ux = 0.0;
+  cdi_status s = cdi_np_geometry(d, &pores, &faces, &sum_ux);
+  if (s != CDI_OK) return s;
+  double cout[cdi::kMaxSpecies] = {0, 0, 0, 0};
+  s = cdi_query_outlet(d, cout);
+  if (s != CDI_OK) return s;
+  std::memset(out, 0, sizeof(*out));
+  const double cells = (double)d->N;
+  out->porosity = pores / cells;
+  out->specific_surface = faces / (cells * d->dx);
+  const double pi = 3.14159265358979323846;
+  out->l_c_m = faces > 0.0 ? pi / out->specific_surface : INFINITY;
+  out->U_mps = pores > 0.0 ? sum_ux / pores : 0.0;  // sum u / (N phi), N phi = pore cells
+  out->elapsed_s = (double)d->np_steps * d->dt;
+  // inlet cross-section (per metre of depth in 2D) and electrode volume
+  const double A = d->dim == 2 ? d->ny * d->dx : (double)d->ny * d->nz * d->dx * d->dx;
+  const double Vt = d->dim == 2 ? cells * d->dx * d->dx : cells * d->dx * d->dx * d->dx;
+  for (int k = 0; k < d->ns; k++) {
+    out->Pe[k] = out->U_mps * out->l_c_m / d->D[k];
+    out->Da[k] = d->Ka * out->l_c_m / d->D[k];
+    out->removal[k] = d->c0 != 0.0 ? (d->c0 - cout[k]) / d->c0 : 0.0;
+    out->amount[k] = out->porosity > 0.0
+                         ? out->U_mps * A * out->removal[k] * out->elapsed_s / (Vt * out->porosity)
+                         : 0.0;
+  }
   return CDI_OK;
 }
 
@@ -667,6 +715,7 @@ cdi_status cdi_copy_field(cdi_domain *d, int field, double *host, size_t count) 
   if (!d || !host) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
   const size_t T = d->prec == CDI_FP64 ? 8 : 4;
   const void *src = nullptr;
+  const float *lo = nullptr;
   int comps = 0;
   double *tmp = d->d_cg;  // 4*N doubles of scratch outside a potential solve
   if (field == CDI_FIELD_U_LATTICE) {
@@ -691,13 +740,14 @@ cdi_status cdi_copy_field(cdi_domain *d, int field, double *host, size_t count) 
     if (!d->np_ready || k >= d->ns) return cdi_fail(d, CDI_ERR_STATE, "no such species state");
     comps = 1;
     src = (const char *)d->d_C[d->cur] + (size_t)k * d->n_pore * T;
+    if (d->cpair) lo = d->d_Clo[d->cur] + (size_t)k * d->n_pore;
   } else {
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "unknown field");
   }
   // rank-ordered transport field -> lattice order (0 in solid cells)
   const size_t n = (size_t)comps * d->N;
   if (count != n) return cdi_fail(d, CDI_ERR_INVALID_ARG, "count mismatch");
-  cdi_status s = cdi_np_scatter(d, src, comps, tmp);
+  cdi_status s = cdi_np_scatter(d, src, lo, comps, tmp);
   if (s != CDI_OK) return s;
   CDI_TRY(d, cudaMemcpyAsync(host, tmp, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy field");
   CDI_TRY(d, cudaStreamSynchronize(d->stream), "copy field");

@@ -243,11 +243,18 @@ struct cdi_domain {
   void *d_fflags = nullptr;     // Nf flow flags
   cdi::NFlag *d_nflags = nullptr;  // N face flags
   int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
-  int *d_nbr = nullptr;         // (Q-1)*n_flow_pore neighbour ranks (-1: solid)
   long long n_flow_pore = 0;
+  // neighbour data of the odd LBM step (see flow.cu): per pore rank a flag
+  // word and the rank bases of the lateral rows; full neighbour ranks of the
+  // x-edge sites in an overflow table of n_lovf = 2 ny nz slots
+  unsigned *d_lf = nullptr;     // n_flow_pore
+  int *d_lr = nullptr;          // (2 in 2D, 8 in 3D) * n_flow_pore
+  int *d_lovf = nullptr;        // (Q-1) * n_lovf
+  int n_lovf = 0;
   int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending:
                                 // entry r is the lattice cell of pore rank r
   uint2 *d_cmeta = nullptr;     // n_pore: {face flags | x << 16, row = z*ny + y}
+  cdi::NFlag *d_cfl = nullptr;  // n_pore: face flags alone (read by the FP32 step)
   uint2 *d_words = nullptr;     // ny*nz*W: per 32 cells of a row {rank of the
                                 // first pore cell at or after it, pore bits}
   int W = 0;                    // words per row, ceil(nx / 32)
@@ -261,6 +268,8 @@ struct cdi_domain {
   double *d_psi = nullptr;      // N potential (V), FP64, lattice order
   void *d_phi = nullptr;        // n_pore psi / V_T, 8 bytes a cell: double
                                 // (FP64) or a float2 (hi, lo) pair (FP32)
+  bool cpair = false;           // concentrations stored as FP32 pairs (hi + lo)
+  float *d_Clo[2] = {nullptr, nullptr};  // their low words (pair storage only)
   void *d_C[2] = {nullptr, nullptr};  // kMaxSpecies*n_pore concentrations,
                                       // ping-pong, T
   double *d_acc = nullptr;      // 3*kMaxSpecies*np_accs per-warp sums (8 B each:
@@ -291,9 +300,11 @@ struct cdi_domain {
   double *d_src = nullptr;      // N charge terms of Eq. 4 (coupled mode only)
   int cur = 0;                  // which of d_C holds the current state
   int64_t np_steps = 0;
-  int np_blocks = 0;            // 128-thread blocks over the pore cells
-  int np_accs = 0;              // account sets, one per warp of 32 pore cells
-                                // (rounded up to a multiple of 8)
+  int np_blocks = 0;            // 128-thread blocks of the fused sweep/batch
+                                // steps (FP64: one thread per pore cell; FP32:
+                                // warps of 31 home cells)
+  int np_accs = 0;              // account sets, one per warp (rounded up to a
+                                // multiple of 8: enough for any launch shape)
   // block sizes of the step kernels, picked by the autotuners
   int lbm_block = 128, np_block = 128;
   int np_variant = 1;           // transport launch shape (see tune_np)
@@ -330,7 +341,7 @@ enum {
   S_OUTP = 36,                              // kMaxSpecies: plain outlet sums
   S_ACC = 40,                               // 3*kMaxSpecies: Gamma/In/Out sums
   S_OUTN = 52,                              // pore cells in the outlet column
-  S_GEOM = 56                               // pore cells, pore-solid faces
+  S_GEOM = 56                               // pore cells, pore-solid faces, sum u_x
 };
 
 // Counter slots in d_counter.
@@ -375,10 +386,11 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double 
 cdi_status cdi_psi_coupled(cdi_domain *d);
 cdi_status cdi_np_build_flags(cdi_domain *d);
 cdi_status cdi_np_build_compact(cdi_domain *d);
-cdi_status cdi_np_scatter(cdi_domain *d, const void *src, int comps, double *dst);
+cdi_status cdi_np_scatter(cdi_domain *d, const void *src, const float *lo, int comps,
+                          double *dst);
 cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used);
 cdi_status cdi_np_dt(cdi_domain *d, double scale, double *dt_out);
-cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces);
+cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces, double *sum_ux);
 cdi_status cdi_np_sweep(cdi_domain *d, int n, const double *scale, const int *group,
                         void *const *phi_groups, const double *dts, int64_t n_steps,
                         double *gamma, double *cout);

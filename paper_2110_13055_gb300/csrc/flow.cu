@@ -142,13 +142,72 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
 }
 
 // Populations are stored compactly by pore rank k (the position of the site
-// in the ascending pore-site list): g[i * n + k].  The neighbour table
-// nbr[(i - 1) * n + k] holds the rank of the site x_k + e_i, or -1 when that
-// site is solid or lies beyond a lateral wall (halfway bounce-back).
+// in the ascending pore-site list): g[i * n + k].
 //
+// Neighbour ranks for the odd step, without a per-direction table.  Per pore
+// rank k (site x_k = (x, row), row = (y, z)):
+//   lf[k]          the site's solid-neighbour bits (bit i: the site x_k + e_i
+//                  is solid or beyond a lateral wall, so the link bounces
+//                  back) and kLinkEdge when x is the first or last column,
+//                  where the periodic x neighbour wraps around;
+//   lr[o * n + k]  for each lateral row offset o = (ey, ez) of the lattice
+//                  (2 for D2Q9, 8 for D3Q19): the rank the site (x, row + o)
+//                  has, or would have if it is solid (the number of pore
+//                  sites before it in lattice order).
+// Pore sites of one row are consecutive ranks, so the neighbour along e_i is
+// k + ex when it stays in the row, and otherwise lr[o] (ex = 0), lr[o] - 1
+// (ex = -1) or lr[o] + [site (x, row + o) is pore] (ex = +1).  At an x-edge
+// site lr[0] instead indexes an overflow table holding all Q - 1 ranks
+// (ovf[(i - 1) * n_ovf + e]; -1 for a bounce-back link).  The odd step reads
+// 4 + 4 * (offsets) bytes per site this way (36 B in 3D) instead of
+// 4 * (Q - 1) (72 B).
+constexpr unsigned kLinkEdge = 1u << 31;
+
+template <int DIM> struct LatOff;
+template <> struct LatOff<2> {
+  static constexpr int NO = 2;
+  __host__ __device__ static constexpr int ey(int o) { return o == 0 ? 1 : -1; }
+  __host__ __device__ static constexpr int ez(int) { return 0; }
+};
+template <> struct LatOff<3> {
+  static constexpr int NO = 8;
+  // (ey, ez): (1,0) (-1,0) (0,1) (0,-1) (1,1) (1,-1) (-1,1) (-1,-1)
+  __host__ __device__ static constexpr int ey(int o) {
+    return o == 0 || o == 4 || o == 5 ? 1 : (o == 1 || o == 6 || o == 7 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int ez(int o) {
+    return o == 2 || o == 4 || o == 6 ? 1 : (o == 3 || o == 5 || o == 7 ? -1 : 0);
+  }
+};
+// Row offset of direction i (-1 when it stays in the row).
+template <int DIM> __host__ __device__ constexpr int off_of(int i) {
+  using L = Lat<DIM>;
+  using O = LatOff<DIM>;
+  if (L::ey(i) == 0 && L::ez(i) == 0) return -1;
+  for (int o = 0; o < O::NO; o++)
+    if (O::ey(o) == L::ey(i) && O::ez(o) == L::ez(i)) return o;
+  return -1;
+}
+// Direction (0, ey, ez) of row offset o.
+template <int DIM> __host__ __device__ constexpr int dir_of_off(int o) {
+  using L = Lat<DIM>;
+  using O = LatOff<DIM>;
+  for (int i = 1; i < L::Q; i++)
+    if (L::ex(i) == 0 && L::ey(i) == O::ey(o) && L::ez(i) == O::ez(o)) return i;
+  return -1;
+}
+
+struct LinkGeo {
+  const unsigned *lf;  // n: solid-neighbour bits | kLinkEdge
+  const int *lr;       // NO * n: rank bases of the lateral rows
+  const int *ovf;      // (Q - 1) * n_ovf: full neighbour ranks of x-edge sites
+  int n_ovf;
+};
+
 // Slot read by direction i at rank k (ODD: the upstream neighbour's opposite
 // slot, or the own slot after a bounce-back), and slot written by the
-// post-collision value of direction i.  nb[j] caches nbr for direction j.
+// post-collision value of direction i.  nb[j] caches the neighbour rank of
+// direction j (-1: bounce-back).
 template <int DIM, bool ODD>
 __device__ __forceinline__ size_t read_slot(const int *nb, int k, int i, long long n) {
   using L = Lat<DIM>;
@@ -168,12 +227,35 @@ __device__ __forceinline__ size_t write_slot(const int *nb, int k, int i, long l
 
 // Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
 template <int DIM, bool ODD>
-__device__ __forceinline__ void load_links(const int *__restrict__ nbr, int k, long long n,
+__device__ __forceinline__ void load_links(const LinkGeo &lg, int k, long long n,
                                            int (&nb)[Lat<DIM>::Q]) {
+  using L = Lat<DIM>;
+  constexpr int NO = LatOff<DIM>::NO;
   nb[0] = k;
-  if (ODD) {
+  if (!ODD) return;
+  const unsigned f = lg.lf[k];
+  int R[NO];
 #pragma unroll
-    for (int i = 1; i < Lat<DIM>::Q; i++) nb[i] = nbr[(size_t)(i - 1) * n + k];
+  for (int o = 0; o < NO; o++) R[o] = lg.lr[(size_t)o * n + k];
+#pragma unroll
+  for (int i = 1; i < L::Q; i++) {
+    const int o = off_of<DIM>(i);
+    int r;
+    if (o < 0) {
+      r = k + L::ex(i);
+    } else if (L::ex(i) == 0) {
+      r = R[o];
+    } else if (L::ex(i) < 0) {
+      r = R[o] - 1;
+    } else {
+      r = R[o] + (int)(((f >> dir_of_off<DIM>(o)) & 1u) ^ 1u);
+    }
+    nb[i] = ((f >> i) & 1u) ? -1 : r;
+  }
+  if (f & kLinkEdge) {  // the x neighbours wrap: all ranks from the overflow table
+    const int e = R[0];
+#pragma unroll
+    for (int i = 1; i < L::Q; i++) nb[i] = lg.ovf[(size_t)(i - 1) * lg.n_ovf + e];
   }
 }
 
@@ -182,19 +264,47 @@ __global__ void k_rank_scatter(const int *__restrict__ list, int n, int *__restr
     rank[list[k]] = k;
 }
 
+// Builds lf, lr and the overflow table (rank[site]: the pore rank, -1 for a
+// solid site).  The overflow slot of an x-edge site is 2 * row + (x != 0).
 template <int DIM>
 __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
                         const int *__restrict__ list, int n, const int *__restrict__ rank,
-                        int *__restrict__ nbr, int NX, int ny, int nz) {
+                        unsigned *__restrict__ lf, int *__restrict__ lr, int *__restrict__ ovf,
+                        int n_ovf, int NX, int ny, int nz, int walls) {
   using L = Lat<DIM>;
+  using O = LatOff<DIM>;
+  using W = WrapBit<DIM>;
+  constexpr unsigned kSolidBits = ((1u << L::Q) - 1u) & ~1u;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int s = list[k];
     const unsigned f = fl[s];
-    const SiteIdx<DIM> ix(s, f, NX, ny, nz);
+    const int x = s % NX, row = s / NX, y = row % ny, z = row / ny;
+    const bool xedge = ((f >> W::XHI) & 1u) || ((f >> W::XLO) & 1u);
+    lf[k] = (f & kSolidBits) | (xedge ? kLinkEdge : 0u);
 #pragma unroll
-    for (int i = 1; i < L::Q; i++)
-      nbr[(size_t)(i - 1) * n + k] =
-          ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
+    for (int o = 0; o < O::NO; o++) {
+      int Y = y + O::ey(o), Z = z + O::ez(o);
+      int R = 0;
+      const bool beyond = Y < 0 || Y >= ny || Z < 0 || Z >= nz;
+      if (!xedge && !(beyond && walls)) {
+        Y = (Y + ny) % ny;
+        Z = (Z + nz) % nz;
+        const int sp = (Z * ny + Y) * NX + x;  // x - 1 and x + 1 stay in the row
+        if (rank[sp] >= 0) R = rank[sp];
+        else if (rank[sp + 1] >= 0) R = rank[sp + 1];
+        else if (rank[sp - 1] >= 0) R = rank[sp - 1] + 1;
+      }
+      lr[(size_t)o * n + k] = R;
+    }
+    if (xedge) {
+      const int e = 2 * row + (x != 0 ? 1 : 0);
+      lr[k] = e;
+      const SiteIdx<DIM> ix(s, f, NX, ny, nz);
+#pragma unroll
+      for (int i = 1; i < L::Q; i++)
+        ovf[(size_t)(i - 1) * n_ovf + e] =
+            ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
+    }
   }
 }
 
@@ -207,7 +317,7 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 // chosen per variant so that nothing spills)
 template <typename S, int DIM, bool ODD, int BS, int MINT>
 __global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128) / BS)
-    k_lbm_step(S *__restrict__ g, const int *__restrict__ nbr, int n,
+    k_lbm_step(S *__restrict__ g, LinkGeo lg, int n,
                typename Arith<S>::type omega, typename Arith<S>::type fx_half,
                typename Arith<S>::type fsrc) {
   using T = typename Arith<S>::type;
@@ -216,7 +326,7 @@ __global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   int nb[Q];
-  load_links<DIM, ODD>(nbr, k0, n, nb);
+  load_links<DIM, ODD>(lg, k0, n, nb);
   T gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) gi[i] = widen(g[read_slot<DIM, ODD>(nb, k0, i, n)]);
@@ -265,7 +375,7 @@ struct SplitConst {
 // collision carried out in pair arithmetic.
 template <int DIM, bool ODD, bool TAU1>
 __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__restrict__ gl,
-                                               const int *__restrict__ nbr, int n,
+                                               const LinkGeo &lg, int n,
                                                const SplitConst &c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
@@ -277,7 +387,7 @@ __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   int nb[Q];
-  load_links<DIM, ODD>(nbr, k0, n, nb);
+  load_links<DIM, ODD>(lg, k0, n, nb);
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -342,17 +452,17 @@ __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__
 // BS threads per block, registers as the compiler sees fit.
 template <int DIM, bool ODD, bool TAU1, int BS>
 __global__ void __launch_bounds__(BS)
-    k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl,
-                     const int *__restrict__ nbr, int n, SplitConst c) {
-  lbm_split_body<DIM, ODD, TAU1>(gh, gl, nbr, n, c);
+    k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl, LinkGeo lg, int n,
+                     SplitConst c) {
+  lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, c);
 }
 
 // The same step with registers capped so that MINT threads share an SM.
 template <int DIM, bool ODD, bool TAU1, int BS, int MINT>
 __global__ void __launch_bounds__(BS, MINT / BS)
-    k_lbm_step_split_occ(float *__restrict__ gh, float *__restrict__ gl,
-                         const int *__restrict__ nbr, int n, SplitConst c) {
-  lbm_split_body<DIM, ODD, TAU1>(gh, gl, nbr, n, c);
+    k_lbm_step_split_occ(float *__restrict__ gh, float *__restrict__ gl, LinkGeo lg, int n,
+                         SplitConst c) {
+  lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, c);
 }
 
 // Velocity u = j = sum e_i g_i + F/2 from the natural layout, written to
@@ -498,7 +608,7 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   // one thread per pore site of the flow grid (pore rank)
   const int n = (int)d->n_flow_pore;
   const int grid = (n + BS - 1) / BS;
-  const int *lk = d->d_nbr;
+  const LinkGeo lk{d->d_lf, d->d_lr, d->d_lovf, d->n_lovf};
   if (M == M_SPLIT) {
     const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
@@ -729,24 +839,27 @@ cdi_status cdi_flow_build_flags(cdi_domain *d) {
   return d->dim == 2 ? build_flags<2>(d) : build_flags<3>(d);
 }
 
-// Neighbour-rank table of the compact population layout (after the pore
-// lists): rank[site] scattered from the list (rank_work: Nf ints, -1 for
-// solid), then nbr[(i-1) n + k] for every pore rank k and direction i.
+// Neighbour data of the compact population layout (after the pore lists):
+// rank[site] scattered from the list (rank_work: Nf ints, -1 for solid), then
+// the flag words, row bases and overflow table of every pore rank.
 cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work) {
   const int n = (int)d->n_flow_pore;
   CDI_TRY(d, cudaMemsetAsync(rank_work, 0xff, (size_t)d->Nf * sizeof(int), d->stream),
           "rank reset");
+  CDI_TRY(d, cudaMemsetAsync(d->d_lovf, 0xff, (size_t)(d->dim == 2 ? 8 : 18) * d->n_lovf * 4,
+                             d->stream),
+          "overflow reset");
   k_rank_scatter<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_flow_list, n, rank_work);
   if (d->dim == 2)
     k_links<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
-        d->ny, d->nz);
+        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_lr,
+        d->d_lovf, d->n_lovf, d->NX, d->ny, d->nz, d->walls);
   else
     k_links<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_nbr, d->NX,
-        d->ny, d->nz);
+        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_lr,
+        d->d_lovf, d->n_lovf, d->NX, d->ny, d->nz, d->walls);
   d->timing.kernel_launches += 2;
-  CDI_TRY(d, cudaGetLastError(), "neighbour table");
+  CDI_TRY(d, cudaGetLastError(), "neighbour data");
   return CDI_OK;
 }
 
@@ -755,6 +868,7 @@ cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
     case CDI_FP64:
       return d->dim == 2 ? flow_run<M_F64, 2>(d, p, steps, res) : flow_run<M_F64, 3>(d, p, steps, res);
     case CDI_FP32:
+    case CDI_FP32_CPAIR:
       return d->dim == 2 ? flow_run<M_F32, 2>(d, p, steps, res) : flow_run<M_F32, 3>(d, p, steps, res);
     case CDI_BF16_POP:
       return d->dim == 2 ? flow_run<M_BF16, 2>(d, p, steps, res)

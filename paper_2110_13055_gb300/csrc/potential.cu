@@ -212,11 +212,13 @@ __global__ void k_cg_dir(long long N, double *__restrict__ p, const double *__re
 // solid cells keep the 0 the caller cleared).
 template <typename T>
 __global__ void k_charge(int n, int ns, const int *__restrict__ cells, const T *__restrict__ C,
-                         int4 z, double coef, double *__restrict__ src) {
+                         const float *__restrict__ Cl, int4 z, double coef,
+                         double *__restrict__ src) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int zz[4] = {z.x, z.y, z.z, z.w};
     double q = 0.0;
-    for (int k = 0; k < ns; k++) q += zz[k] * (double)C[(size_t)k * n + r];
+    for (int k = 0; k < ns; k++)
+      q += zz[k] * ((double)C[(size_t)k * n + r] + (Cl ? (double)Cl[(size_t)k * n + r] : 0.0));
     src[cells[r]] = coef * q;
   }
 }
@@ -300,10 +302,12 @@ cdi_status cdi_psi_coupled(cdi_domain *d) {
   const int4 z = make_int4(d->z[0], d->z[1], d->z[2], d->z[3]);
   if (d->prec == CDI_FP64)
     k_charge<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (int)d->n_pore, d->ns, d->d_cell_list, (const double *)d->d_C[d->cur], z, coef, d->d_src);
+        (int)d->n_pore, d->ns, d->d_cell_list, (const double *)d->d_C[d->cur], nullptr, z, coef,
+        d->d_src);
   else
     k_charge<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (int)d->n_pore, d->ns, d->d_cell_list, (const float *)d->d_C[d->cur], z, coef, d->d_src);
+        (int)d->n_pore, d->ns, d->d_cell_list, (const float *)d->d_C[d->cur], d->d_Clo[d->cur], z,
+        coef, d->d_src);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "charge");
   int it = 0;

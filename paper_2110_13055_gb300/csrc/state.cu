@@ -51,6 +51,7 @@ std::vector<Section> sections(cdi_domain *d, int c_buf) {
   s.push_back({d->d_psi, (size_t)d->N * 8});
   s.push_back({d->d_phi, (size_t)d->n_pore * 8});
   s.push_back({d->d_C[c_buf], (size_t)cdi::kMaxSpecies * d->n_pore * T});
+  if (d->cpair) s.push_back({d->d_Clo[c_buf], (size_t)cdi::kMaxSpecies * d->n_pore * 4});
   s.push_back({d->d_acc, (size_t)3 * cdi::kMaxSpecies * d->np_accs * 8});
   return s;
 }

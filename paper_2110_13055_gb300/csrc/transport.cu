@@ -21,6 +21,7 @@
 // cells map, so the totals are deterministic).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "cdi_internal.cuh"
 
@@ -37,6 +38,7 @@ template <typename T> struct NPConst {
   T zf[kMaxSpecies];    // valence
   T dtdx;               // dt / dx
   T c0;                 // feed concentration
+  T c0lo;               // its low word (c0 - (T)c0) for pair storage
 };
 
 template <int DIM>
@@ -176,12 +178,23 @@ __device__ __forceinline__ float phi_diff(float2 nb, float2 pp) {
 // Geometry of the compact transport layout handed to the step kernels.
 struct NPGeo {
   const uint2 *meta;   // per rank {flags | x << 16, row}
+  const NFlag *fl;     // per rank: its face flags alone (what the step reads)
   const uint2 *words;  // per 32 cells of a row {first rank, pore bits}
   const int *lat;      // per lateral face f (y+, y-, z+, z-) and rank r, at
                        // (f - 2) * n + r: the pore neighbour's rank, or -1
   int n, W, ny, nz, walls;
-  int naccs;           // account sets (warps of 32 ranks), the same for any launch shape
+  int naccs;           // account sets (one per warp), the same for any launch shape
 };
+
+// FP32 storage: warps of 31 home cells.  Warp w holds ranks 31 w - 1 ..
+// 31 w + 30 in lanes 0..31; lane 0 (the last home cell of warp w - 1) is a
+// halo.  Each lane evaluates the flux through the +x face of its cell; when
+// the -x neighbour of a cell is a pore cell it is the rank before it, i.e.
+// the lane before it, so that face's flux is the previous lane's +x flux
+// with its sign flipped (one shuffle).  Every x face is then evaluated once
+// instead of twice, and every lane of the warp takes the same path.
+constexpr int kHome = 31;
+__host__ __device__ constexpr long long np_warps(long long n) { return (n + kHome - 1) / kHome; }
 
 // One explicit step of the pore cell of rank r for NS species: writes the
 // new concentrations and adds the cell's adsorbed (v[k]), inflow (v[NS+k])
@@ -327,45 +340,326 @@ __device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io,
   }
 }
 
-template <typename T, int DIM, int NS>
+template <int NS>
+__device__ __forceinline__ void np_account_f32(float (&v)[3 * NS], bool io, float2 *acc, int wid,
+                                               int nw) {
+  np_account<float, NS>(v, io, acc, wid, nw);
+}
+
+// Two species per packed FP32x2 operation (each component rounded exactly as
+// the scalar operation would be).
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, pneg(b)); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Flux through one face for a pair of species (k0, k1): the same arithmetic,
+// species by species, as face_flux followed by the D/dx factor.  An odd
+// species count pads its last pair with a copy of the last species (k1 = k0).
+// Scalar flux of one species with pair-stored concentrations C + Cl: the
+// difference C_P - C_nb and the two Bernoulli products take the low words
+// along; everything else is face_flux.
+__device__ __forceinline__ float face_flux_lo(float adv, float z, float dd, float2 nb, float2 pp,
+                                              float CP, float Cn, float CPl, float Cnl) {
+  const float p = __fmaf_rn(-z, dd, adv);
+  if (fabsf(p) < 0.5f) {
+    const float p2 = __fmul_rn(p, p);
+    float E = __fmaf_rn(p2, 1.f / 30240.f, -1.f / 720.f);
+    E = __fmaf_rn(E, p2, 1.f / 12.f);
+    E = __fmaf_rn(E, p2, 1.f);
+    const float dC = __fadd_rn(__fsub_rn(CP, Cn), __fsub_rn(CPl, Cnl));
+    return __fmaf_rn(E, dC, __fmul_rn(__fmul_rn(0.5f, p), __fadd_rn(CP, Cn)));
+  }
+  float Bp, Bm;
+  bernoulli_pair_split(adv, z, nb, pp, Bp, Bm);
+  return __fadd_rn(r_fma(Bm, CP, -r_mul(Bp, Cn)), r_fma(Bm, CPl, -r_mul(Bp, Cnl)));
+}
+
+// Flux through one face for a pair of species (k0, k1): the same arithmetic,
+// species by species, as face_flux (face_flux_lo with PAIR) followed by the
+// D/dx factor.  An odd species count pads its last pair with a copy of the
+// last species (k1 = k0).
+template <bool PAIR>
+__device__ __forceinline__ float2 face_flux_pair(float uf, float dd, float2 phn, float2 phP,
+                                                 float2 CP, float2 Cn, float2 CPl, float2 Cnl,
+                                                 const NPConst<float> &c, int k0, int k1) {
+  const float2 adv = pmul(bc(uf), make_float2(c.dxD[k0], c.dxD[k1]));
+  const float2 p = pfma(make_float2(-c.zf[k0], -c.zf[k1]), bc(dd), adv);
+  float2 J;
+  if (fabsf(p.x) < 0.5f && fabsf(p.y) < 0.5f) {
+    const float2 p2 = pmul(p, p);
+    float2 E = pfma(p2, bc(1.f / 30240.f), bc(-1.f / 720.f));
+    E = pfma(E, p2, bc(1.f / 12.f));
+    E = pfma(E, p2, bc(1.f));
+    float2 dC = psub(CP, Cn);
+    if (PAIR) dC = padd(dC, psub(CPl, Cnl));
+    J = pfma(E, dC, pmul(pmul(bc(0.5f), p), padd(CP, Cn)));
+  } else if (PAIR) {
+    J.x = face_flux_lo(adv.x, c.zf[k0], dd, phn, phP, CP.x, Cn.x, CPl.x, Cnl.x);
+    J.y = face_flux_lo(adv.y, c.zf[k1], dd, phn, phP, CP.y, Cn.y, CPl.y, Cnl.y);
+  } else {
+    J.x = face_flux(adv.x, c.zf[k0], dd, phn, phP, CP.x, Cn.x);
+    J.y = face_flux(adv.y, c.zf[k1], dd, phn, phP, CP.y, Cn.y);
+  }
+  return pmul(make_float2(c.Ddx[k0], c.Ddx[k1]), J);
+}
+
+// (s, e) with s + e = a + b exactly (two-sum, component-wise).
+__device__ __forceinline__ void ptwo_sum(float2 a, float2 b, float2 &s, float2 &e) {
+  s = padd(a, b);
+  const float2 bp = psub(s, a);
+  e = padd(psub(a, psub(s, bp)), psub(b, bp));
+}
+
+// One explicit step of the home cells of warp w (FP32, NS species in
+// (NS + 1) / 2 packed pairs), with the per-warp accounts of Gamma, In and
+// Out.  PAIR: every concentration is an unevaluated pair hi + lo (the low
+// words in Cinl/Coutl), updated with the two-sum transformation, so rounding
+// does not build up over long runs; the fluxes take the low words into the
+// concentration differences.  All 32 lanes of the warp must call it.  Per
+// home cell the faces are summed in the order of np_cell (adsorption, +x,
+// -x, +y, -y, +z, -z), so without PAIR a cell whose faces all take the
+// |P| < 1/2 branch gets the bits np_cell gives.
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_warp31(const float *__restrict__ Cin, float *__restrict__ Cout,
+                                          const float *__restrict__ Cinl,
+                                          float *__restrict__ Coutl, const float *__restrict__ u,
+                                          const float2 *__restrict__ phi, const NPGeo &g,
+                                          const NPConst<float> &c, float2 *__restrict__ acc,
+                                          int w) {
+  constexpr int NF = 2 * DIM;
+  constexpr int NP = (NS + 1) / 2;
+  // second species of pair p (a copy of the first when NS is odd)
+  auto K1 = [](int p) { return 2 * p + 1 < NS ? 2 * p + 1 : 2 * p; };
+  const int lane = threadIdx.x & 31;
+  const int r = kHome * w + lane - 1;
+  const bool valid = r >= 0 && r < g.n;
+  const bool home = valid && lane != 0;
+  const size_t n = (size_t)g.n;
+  auto ldC = [&](const float *A, int Q, int p) {
+    return make_float2(A[(size_t)(2 * p) * n + Q], A[(size_t)K1(p) * n + Q]);
+  };
+  const unsigned f = valid ? (unsigned)g.fl[r] : 0u;
+  // lateral neighbour ranks (-1 across a solid face or wall)
+  int q[NF - 2];
+#pragma unroll
+  for (int j = 0; j < NF - 2; j++) q[j] = home ? g.lat[(size_t)j * n + r] : -1;
+  // own values
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 CP[NP], CPl[NP];
+  float uP[DIM];
+  float2 phP = z2;
+#pragma unroll
+  for (int p = 0; p < NP; p++) CP[p] = CPl[p] = z2;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) uP[a] = 0.f;
+  if (valid) {
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      CP[p] = ldC(Cin, r, p);
+      if (PAIR) CPl[p] = ldC(Cinl, r, p);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * n + r];
+    phP = phi[r];
+  }
+  // lateral neighbours' values (a closed face reads the cell's own values,
+  // for which the flux expression is exactly 0)
+  float2 Cl[NF - 2][NP], Cll[NF - 2][NP], phl[NF - 2];
+  float ul[NF - 2];
+#pragma unroll
+  for (int j = 0; j < NF - 2; j++) {
+    const int fc = j + 2;
+    if (q[j] >= 0) {
+      const int Q = q[j];
+      ul[j] = u[(size_t)(fc >> 1) * n + Q];
+      phl[j] = phi[Q];
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        Cl[j][p] = ldC(Cin, Q, p);
+        Cll[j][p] = PAIR ? ldC(Cinl, Q, p) : z2;
+      }
+    } else {
+      ul[j] = uP[fc >> 1];
+      phl[j] = phP;
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        Cl[j][p] = CP[p];
+        Cll[j][p] = CPl[p];
+      }
+    }
+  }
+  // +x face: the neighbour is rank r + 1 (the next lane) when the face is
+  // open and inside the image; the outlet ghost copies the cell
+  const bool xs = (f >> kFaceBit) & 1u, xe = (f >> kEdgeBit) & 1u;
+  const bool xp = valid && !xs && !xe;
+  float2 Cx[NP], Cxl[NP], phx;
+  float ux;
+  ux = __shfl_down_sync(0xffffffffu, uP[0], 1);
+  phx.x = __shfl_down_sync(0xffffffffu, phP.x, 1);
+  phx.y = __shfl_down_sync(0xffffffffu, phP.y, 1);
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    Cx[p].x = __shfl_down_sync(0xffffffffu, CP[p].x, 1);
+    Cx[p].y = __shfl_down_sync(0xffffffffu, CP[p].y, 1);
+    Cxl[p] = z2;
+    if (PAIR) {
+      Cxl[p].x = __shfl_down_sync(0xffffffffu, CPl[p].x, 1);
+      Cxl[p].y = __shfl_down_sync(0xffffffffu, CPl[p].y, 1);
+    }
+  }
+  if (lane == 31 && xp) {  // rank r + 1 is the next warp's first home cell
+    ux = u[r + 1];
+    phx = phi[r + 1];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      Cx[p] = ldC(Cin, r + 1, p);
+      if (PAIR) Cxl[p] = ldC(Cinl, r + 1, p);
+    }
+  }
+  if (!xp) {
+    ux = uP[0];
+    phx = phP;
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      Cx[p] = CP[p];
+      Cxl[p] = CPl[p];
+    }
+  }
+  float2 Jx[NP];
+  {
+    const float uf = (valid && !xs) ? r_mul(0.5f, r_add(uP[0], ux)) : 0.f;
+    const float dd = phi_diff(phx, phP);
+#pragma unroll
+    for (int p = 0; p < NP; p++)
+      Jx[p] = face_flux_pair<PAIR>(uf, dd, phx, phP, CP[p], Cx[p], CPl[p], Cxl[p], c, 2 * p,
+                                   K1(p));
+  }
+  // -x face: the previous lane's +x face (pore neighbour), the feed ghost
+  // (inlet), or closed (solid)
+  const bool ms = (f >> (kFaceBit + 1)) & 1u, me = (f >> (kEdgeBit + 1)) & 1u;
+  float2 Jm[NP];
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    Jm[p].x = -__shfl_up_sync(0xffffffffu, Jx[p].x, 1);
+    Jm[p].y = -__shfl_up_sync(0xffffffffu, Jx[p].y, 1);
+    if (ms) Jm[p] = z2;
+  }
+  if (home && me) {
+    const float uf = r_mul(-0.5f, r_add(uP[0], uP[0]));
+    const float dd = phi_diff(z2, phP);
+#pragma unroll
+    for (int p = 0; p < NP; p++)
+      Jm[p] = face_flux_pair<PAIR>(uf, dd, z2, phP, CP[p], bc(c.c0), CPl[p], bc(c.c0lo), c,
+                                   2 * p, K1(p));
+  }
+  // adsorption on the solid faces (Eq. 6), then the faces in order
+  float v[3 * NS];
+#pragma unroll
+  for (int j = 0; j < 3 * NS; j++) v[j] = 0.f;
+  const float ns_solid = (float)__popc(f & (((1u << NF) - 1u) << kFaceBit));
+  float2 sumJ[NP];
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    const float2 Ja = pmul(pmul(bc(ns_solid), make_float2(c.Keff[2 * p], c.Keff[K1(p)])), CP[p]);
+    sumJ[p] = padd(padd(Ja, Jx[p]), Jm[p]);
+    if (home) {
+      v[2 * p] = r_add(0.f, Ja.x);
+      if (2 * p + 1 < NS) v[2 * p + 1] = r_add(0.f, Ja.y);
+      if (me) {
+        v[NS + 2 * p] = r_sub(0.f, Jm[p].x);
+        if (2 * p + 1 < NS) v[NS + 2 * p + 1] = r_sub(0.f, Jm[p].y);
+      }
+      if (xe) {
+        v[2 * NS + 2 * p] = r_add(0.f, Jx[p].x);
+        if (2 * p + 1 < NS) v[2 * NS + 2 * p + 1] = r_add(0.f, Jx[p].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NF - 2; j++) {
+    const int fc = j + 2;
+    const float half = (fc & 1) ? -0.5f : 0.5f;
+    const float uf = q[j] >= 0 ? r_mul(half, r_add(uP[fc >> 1], ul[j])) : 0.f;
+    const float dd = phi_diff(phl[j], phP);
+#pragma unroll
+    for (int p = 0; p < NP; p++)
+      sumJ[p] = padd(sumJ[p], face_flux_pair<PAIR>(uf, dd, phl[j], phP, CP[p], Cl[j][p], CPl[p],
+                                                   Cll[j][p], c, 2 * p, K1(p)));
+  }
+  if (home) {
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      float2 Cn, Cnl;
+      if (PAIR) {
+        // (hi + lo) - dt/dx sum J by two-sum, renormalised
+        float2 t, e;
+        ptwo_sum(CP[p], pmul(bc(-c.dtdx), sumJ[p]), t, e);
+        const float2 l = padd(CPl[p], e);
+        Cn = padd(t, l);
+        Cnl = psub(l, psub(Cn, t));
+        Coutl[(size_t)(2 * p) * n + r] = Cnl.x;
+        if (2 * p + 1 < NS) Coutl[(size_t)(2 * p + 1) * n + r] = Cnl.y;
+      } else {
+        Cn = pfma(bc(-c.dtdx), sumJ[p], CP[p]);
+      }
+      Cout[(size_t)(2 * p) * n + r] = Cn.x;
+      if (2 * p + 1 < NS) Cout[(size_t)(2 * p + 1) * n + r] = Cn.y;
+    }
+  }
+  np_account_f32<NS>(v, home && (me || xe), acc, w, g.naccs);
+}
+
+template <typename T, int DIM, int NS, bool PAIR>
 __device__ __forceinline__ void np_step_body(const T *__restrict__ Cin, T *__restrict__ Cout,
-                                             const T *__restrict__ u,
+                                             const float *__restrict__ Cinl,
+                                             float *__restrict__ Coutl, const T *__restrict__ u,
                                              const typename PhiStore<T>::type *__restrict__ phi,
                                              const NPGeo &g, const NPConst<T> &c,
                                              typename AccSlot<T>::type *__restrict__ acc) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  T v[3 * NS];
+  if constexpr (std::is_same<T, float>::value) {
+    np_warp31<DIM, NS, PAIR>(Cin, Cout, Cinl, Coutl, u, phi, g, c, acc,
+                             (blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  } else {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    T v[3 * NS];
 #pragma unroll
-  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-  bool io = false;
-  if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
-  np_account<T, NS>(v, io, acc, r >> 5, g.naccs);
+    for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+    bool io = false;
+    if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
+    np_account<T, NS>(v, io, acc, r >> 5, g.naccs);
+  }
 }
 
 // BS threads per block, registers as the compiler sees fit.
-template <typename T, int DIM, int NS, int BS>
+template <typename T, int DIM, int NS, int BS, bool PAIR>
 __global__ void __launch_bounds__(BS)
-    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
+    k_np_step(const T *__restrict__ Cin, T *__restrict__ Cout, const float *__restrict__ Cinl,
+              float *__restrict__ Coutl, const T *__restrict__ u,
               const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
               typename AccSlot<T>::type *__restrict__ acc) {
-  np_step_body<T, DIM, NS>(Cin, Cout, u, phi, g, c, acc);
+  np_step_body<T, DIM, NS, PAIR>(Cin, Cout, Cinl, Coutl, u, phi, g, c, acc);
 }
 
 // The same step with registers capped so that MINT threads share an SM (more
 // resident warps for the gathered loads, at the price of a few spilled
 // values).
-template <typename T, int DIM, int NS, int BS, int MINT>
+template <typename T, int DIM, int NS, int BS, int MINT, bool PAIR>
 __global__ void __launch_bounds__(BS, MINT / BS)
-    k_np_step_occ(const T *__restrict__ Cin, T *__restrict__ Cout, const T *__restrict__ u,
+    k_np_step_occ(const T *__restrict__ Cin, T *__restrict__ Cout, const float *__restrict__ Cinl,
+                  float *__restrict__ Coutl, const T *__restrict__ u,
                   const typename PhiStore<T>::type *__restrict__ phi, NPGeo g, NPConst<T> c,
                   typename AccSlot<T>::type *__restrict__ acc) {
-  np_step_body<T, DIM, NS>(Cin, Cout, u, phi, g, c, acc);
+  np_step_body<T, DIM, NS, PAIR>(Cin, Cout, Cinl, Coutl, u, phi, g, c, acc);
 }
 
 // One member of a fused sweep: its own concentrations, velocity, potential,
 // constants (time step) and accounts.
 template <typename T> struct SweepMember {
   T *C[2];          // concentration buffers (ping-pong)
+  float *Cl[2];     // their low words (FP32 pair storage), else null
   const T *u;
   const typename PhiStore<T>::type *phi;
   typename AccSlot<T>::type *acc;
@@ -376,20 +670,28 @@ template <typename T> struct SweepMember {
 // same cells for every member in turn (the block -> cells map, the arithmetic
 // and the accounts of a member are those of k_np_step, so a member's result
 // equals a single run's bit for bit).
-template <typename T, int DIM, int NS>
+template <typename T, int DIM, int NS, bool PAIR>
 __global__ void __launch_bounds__(kRowBlock)
     k_np_sweep(const SweepMember<T> *__restrict__ members, int n_members, int in, NPGeo g) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint2 meta = r < g.n ? g.meta[r] : make_uint2(1u, 0u);
-  for (int m = 0; m < n_members; m++) {
-    const SweepMember<T> &mb = members[m];
-    T v[3 * NS];
+  if constexpr (std::is_same<T, float>::value) {
+    for (int m = 0; m < n_members; m++) {
+      const SweepMember<T> &mb = members[m];
+      np_warp31<DIM, NS, PAIR>(mb.C[in], mb.C[1 - in], mb.Cl[in], mb.Cl[1 - in], mb.u, mb.phi, g,
+                               mb.c, mb.acc, r >> 5);
+    }
+  } else {
+    const uint2 meta = r < g.n ? g.meta[r] : make_uint2(1u, 0u);
+    for (int m = 0; m < n_members; m++) {
+      const SweepMember<T> &mb = members[m];
+      T v[3 * NS];
 #pragma unroll
-    for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-    bool io = false;
-    if (r < g.n)
-      io = np_cell<T, DIM, NS>(mb.C[in], mb.C[1 - in], mb.u, mb.phi, g, meta, r, mb.c, v);
-    np_account<T, NS>(v, io, mb.acc, r >> 5, g.naccs);
+      for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+      bool io = false;
+      if (r < g.n)
+        io = np_cell<T, DIM, NS>(mb.C[in], mb.C[1 - in], mb.u, mb.phi, g, meta, r, mb.c, v);
+      np_account<T, NS>(v, io, mb.acc, r >> 5, g.naccs);
+    }
   }
 }
 
@@ -407,7 +709,7 @@ template <typename T> struct BatchMember {
 // local block b - block0: the same cells, arithmetic and accounts as block
 // b - block0 of the member's single-run launch, so each member equals its
 // single run bit for bit.
-template <typename T, int DIM, int NS>
+template <typename T, int DIM, int NS, bool PAIR>
 __global__ void __launch_bounds__(kRowBlock)
     k_np_batch(const BatchMember<T> *__restrict__ members, int n_members, int in) {
   int lo = 0, hi = n_members - 1;
@@ -419,14 +721,19 @@ __global__ void __launch_bounds__(kRowBlock)
   const BatchMember<T> &mb = members[lo];
   const int b = (int)blockIdx.x - mb.block0;
   const int r = b * blockDim.x + threadIdx.x;
-  T v[3 * NS];
+  if constexpr (std::is_same<T, float>::value) {
+    np_warp31<DIM, NS, PAIR>(mb.s.C[in], mb.s.C[1 - in], mb.s.Cl[in], mb.s.Cl[1 - in], mb.s.u,
+                             mb.s.phi, mb.g, mb.s.c, mb.s.acc, r >> 5);
+  } else {
+    T v[3 * NS];
 #pragma unroll
-  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-  bool io = false;
-  if (r < mb.g.n)
-    io = np_cell<T, DIM, NS>(mb.s.C[in], mb.s.C[1 - in], mb.s.u, mb.s.phi, mb.g, mb.g.meta[r], r,
-                             mb.s.c, v);
-  np_account<T, NS>(v, io, mb.s.acc, r >> 5, mb.g.naccs);
+    for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+    bool io = false;
+    if (r < mb.g.n)
+      io = np_cell<T, DIM, NS>(mb.s.C[in], mb.s.C[1 - in], mb.s.u, mb.s.phi, mb.g, mb.g.meta[r],
+                               r, mb.s.c, v);
+    np_account<T, NS>(v, io, mb.s.acc, r >> 5, mb.g.naccs);
+  }
 }
 
 // Largest outflow rate over pore cells and species, in FP64 from the FP64
@@ -491,13 +798,19 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 template <typename T>
-__global__ void k_np_init(T *__restrict__ C0, T *__restrict__ C1, int n, int ns, T c0) {
+__global__ void k_np_init(T *__restrict__ C0, T *__restrict__ C1, float *__restrict__ L0,
+                          float *__restrict__ L1, int n, int ns, T c0, float c0lo) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int k = 0; k < kMaxSpecies; k++) {
       const T v = k < ns ? c0 : T(0);
       C0[(size_t)k * n + r] = v;
       C1[(size_t)k * n + r] = v;
+      if (L0) {
+        const float l = k < ns ? c0lo : 0.f;
+        L0[(size_t)k * n + r] = l;
+        L1[(size_t)k * n + r] = l;
+      }
     }
   }
 }
@@ -507,9 +820,9 @@ __global__ void k_np_init(T *__restrict__ C0, T *__restrict__ C1, int n, int ns,
 // sum of C at the outlet, 13 pore cells in the outlet column.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_np_sums(const uint2 *__restrict__ meta, const T *__restrict__ C, const T *__restrict__ u,
-              int n, int ns, double cell_vol, double *__restrict__ part, unsigned int *counter,
-              double *scal) {
+    k_np_sums(const uint2 *__restrict__ meta, const T *__restrict__ C,
+              const float *__restrict__ Cl, const T *__restrict__ u, int n, int ns,
+              double cell_vol, double *__restrict__ part, unsigned int *counter, double *scal) {
   constexpr int NV = 14;
   __shared__ double sm[NV * 32];
   double v[NV];
@@ -521,7 +834,7 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
     for (int k = 0; k < kMaxSpecies; k++) {
       if (k >= ns) break;
-      const double ck = (double)C[(size_t)k * n + r];
+      const double ck = (double)C[(size_t)k * n + r] + (Cl ? (double)Cl[(size_t)k * n + r] : 0.0);
       v[k] += ck;
       if (outlet) {
         v[4 + k] += ux * ck;
@@ -553,27 +866,32 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // Pore cells and pore-solid faces inside the image (the interface the
-// specific surface of Sec. 4 measures), counted over the pore ranks.
+// specific surface of Sec. 4 measures), counted over the pore ranks, and the
+// sum of the x velocity over them (the numerator of Sec. 4's pore mean U).
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_geometry(const uint2 *__restrict__ meta, int n, int faces, double *__restrict__ part,
-               unsigned int *counter, double *scal) {
-  __shared__ double sm[2 * 32];
-  double v[2] = {0.0, 0.0};
+    k_geometry(const uint2 *__restrict__ meta, const T *__restrict__ ux, int n, int faces,
+               double *__restrict__ part, unsigned int *counter, double *scal) {
+  __shared__ double sm[3 * 32];
+  double v[3] = {0.0, 0.0, 0.0};
   const unsigned face_bits = ((1u << faces) - 1u) << kFaceBit;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     v[0] += 1.0;
     v[1] += (double)__popc(meta[r].x & face_bits);
+    v[2] += (double)ux[r];
   }
-  block_reduce<2>(v, sm, OpSum(), 0.0);
+  block_reduce<3>(v, sm, OpSum(), 0.0);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = v[0];
     part[gridDim.x + blockIdx.x] = v[1];
+    part[2 * gridDim.x + blockIdx.x] = v[2];
   }
   if (last_block(counter, gridDim.x)) {
-    combine_partials<2>(part, gridDim.x, v, sm, OpSum(), 0.0);
+    combine_partials<3>(part, gridDim.x, v, sm, OpSum(), 0.0);
     if (threadIdx.x == 0) {
       scal[S_GEOM] = v[0];
       scal[S_GEOM + 1] = v[1];
+      scal[S_GEOM + 2] = v[2];
       *counter = 0;
     }
   }
@@ -609,15 +927,16 @@ void acc_total(const cdi_domain *d, const void *acc, cudaStream_t st, double *sc
 // cells found through the row words).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_colmeans(const uint2 *__restrict__ words, int W, const T *__restrict__ C, int rows,
-               double *__restrict__ out) {
+    k_colmeans(const uint2 *__restrict__ words, int W, const T *__restrict__ C,
+               const float *__restrict__ Cl, int rows, double *__restrict__ out) {
   __shared__ double sm[2 * 32];
   const int x = blockIdx.x;
   double v[2] = {0.0, 0.0};
   for (int row = threadIdx.x; row < rows; row += blockDim.x) {
     const uint2 t = words[(size_t)row * W + (x >> 5)];
     if (!((t.y >> (x & 31)) & 1u)) continue;
-    v[0] += (double)C[t.x + __popc(t.y & ((1u << (x & 31)) - 1u))];
+    const int r = t.x + __popc(t.y & ((1u << (x & 31)) - 1u));
+    v[0] += (double)C[r] + (Cl ? (double)Cl[r] : 0.0);
     v[1] += 1.0;
   }
   block_reduce<2>(v, sm, OpSum(), 0.0);
@@ -646,11 +965,12 @@ __global__ void k_lat_nbr(const uint2 *__restrict__ meta, const uint2 *__restric
 
 // Per pore rank: its face flags, x and row.
 __global__ void k_cmeta(const NFlag *__restrict__ fl, const int *__restrict__ cells, int n,
-                        int nx, uint2 *__restrict__ meta) {
+                        int nx, uint2 *__restrict__ meta, NFlag *__restrict__ cfl) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int P = cells[r];
     const int row = P / nx, x = P - row * nx;
     meta[r] = make_uint2((unsigned)fl[P] | ((unsigned)x << 16), (unsigned)row);
+    cfl[r] = fl[P];
   }
 }
 
@@ -679,11 +999,13 @@ __global__ void k_words(const NFlag *__restrict__ fl, const int *__restrict__ ce
 // Compact (rank-ordered) field -> FP64 lattice field, 0 in solid cells:
 // dst[a * N + cells[r]] = src[a * n + r] for comps components.
 template <typename T>
-__global__ void k_scatter(const T *__restrict__ src, int comps, const int *__restrict__ cells,
-                          int n, long long N, double *__restrict__ dst) {
+__global__ void k_scatter(const T *__restrict__ src, const float *__restrict__ lo, int comps,
+                          const int *__restrict__ cells, int n, long long N,
+                          double *__restrict__ dst) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const long long P = cells[r];
-    for (int a = 0; a < comps; a++) dst[a * N + P] = (double)src[(size_t)a * n + r];
+    for (int a = 0; a < comps; a++)
+      dst[a * N + P] = (double)src[(size_t)a * n + r] + (lo ? (double)lo[(size_t)a * n + r] : 0.0);
   }
 }
 
@@ -697,58 +1019,66 @@ template <typename T> NPConst<T> make_const(const cdi_domain *d) {
   }
   c.dtdx = (T)(d->dt / d->dx);
   c.c0 = (T)d->c0;
+  c.c0lo = (T)(d->c0 - (double)c.c0);
   return c;
 }
 
 NPGeo make_geo(const cdi_domain *d) {
-  return NPGeo{d->d_cmeta, d->d_words, d->d_latnb, (int)d->n_pore, d->W, d->ny, d->nz,
+  return NPGeo{d->d_cmeta, d->d_cfl, d->d_words, d->d_latnb, (int)d->n_pore, d->W, d->ny, d->nz,
                d->walls, d->np_accs};
 }
 
-template <typename T, int DIM, int NS, int BS, int MINT>
+template <typename T, int DIM, int NS, int BS, int MINT, bool PAIR>
 void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
-  // one thread per pore rank, one account set per warp
-  const int grid = (int)((d->n_pore + BS - 1) / BS);
+  // FP64: one thread per pore rank; FP32: warps of 31 home cells (one
+  // account set per warp either way)
+  const long long units = std::is_same<T, float>::value ? np_warps(d->n_pore) * 32 : d->n_pore;
+  const int grid = (int)((units + BS - 1) / BS);
+  const float *Cinl = PAIR ? d->d_Clo[in] : nullptr;
+  float *Coutl = PAIR ? d->d_Clo[1 - in] : nullptr;
   if constexpr (MINT == 0)
-    k_np_step<T, DIM, NS, BS><<<grid, BS, 0, st>>>(
-        (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
+    k_np_step<T, DIM, NS, BS, PAIR><<<grid, BS, 0, st>>>(
+        (const T *)d->d_C[in], (T *)d->d_C[1 - in], Cinl, Coutl, (const T *)d->d_u,
         (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
         (typename AccSlot<T>::type *)d->d_acc);
   else
-    k_np_step_occ<T, DIM, NS, BS, MINT><<<grid, BS, 0, st>>>(
-        (const T *)d->d_C[in], (T *)d->d_C[1 - in], (const T *)d->d_u,
+    k_np_step_occ<T, DIM, NS, BS, MINT, PAIR><<<grid, BS, 0, st>>>(
+        (const T *)d->d_C[in], (T *)d->d_C[1 - in], Cinl, Coutl, (const T *)d->d_u,
         (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
         (typename AccSlot<T>::type *)d->d_acc);
 }
 
-template <typename T, int DIM, int NS>
+template <typename T, int DIM, int NS, bool PAIR>
 void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
   switch (d->np_variant) {
-    case 0: launch_step_bs<T, DIM, NS, 64, 0>(d, st, in); break;
-    case 2: launch_step_bs<T, DIM, NS, 256, 0>(d, st, in); break;
-    case 3: launch_step_bs<T, DIM, NS, 64, 1280>(d, st, in); break;
-    case 4: launch_step_bs<T, DIM, NS, 128, 1280>(d, st, in); break;
-    default: launch_step_bs<T, DIM, NS, 128, 0>(d, st, in); break;
+    case 0: launch_step_bs<T, DIM, NS, 64, 0, PAIR>(d, st, in); break;
+    case 2: launch_step_bs<T, DIM, NS, 256, 0, PAIR>(d, st, in); break;
+    case 3: launch_step_bs<T, DIM, NS, 64, 1280, PAIR>(d, st, in); break;
+    case 4: launch_step_bs<T, DIM, NS, 128, 1280, PAIR>(d, st, in); break;
+    default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool PAIR>
 void launch_step_d(cdi_domain *d, cudaStream_t st, int in) {
   switch (d->ns) {
-    case 1: launch_step_t<T, DIM, 1>(d, st, in); break;
-    case 2: launch_step_t<T, DIM, 2>(d, st, in); break;
-    case 3: launch_step_t<T, DIM, 3>(d, st, in); break;
-    default: launch_step_t<T, DIM, 4>(d, st, in); break;
+    case 1: launch_step_t<T, DIM, 1, PAIR>(d, st, in); break;
+    case 2: launch_step_t<T, DIM, 2, PAIR>(d, st, in); break;
+    case 3: launch_step_t<T, DIM, 3, PAIR>(d, st, in); break;
+    default: launch_step_t<T, DIM, 4, PAIR>(d, st, in); break;
   }
 }
 
 void launch_step(cdi_domain *d, cudaStream_t st, int in) {
   if (d->prec == CDI_FP64) {
-    if (d->dim == 2) launch_step_d<double, 2>(d, st, in);
-    else launch_step_d<double, 3>(d, st, in);
+    if (d->dim == 2) launch_step_d<double, 2, false>(d, st, in);
+    else launch_step_d<double, 3, false>(d, st, in);
+  } else if (d->cpair) {
+    if (d->dim == 2) launch_step_d<float, 2, true>(d, st, in);
+    else launch_step_d<float, 3, true>(d, st, in);
   } else {
-    if (d->dim == 2) launch_step_d<float, 2>(d, st, in);
-    else launch_step_d<float, 3>(d, st, in);
+    if (d->dim == 2) launch_step_d<float, 2, false>(d, st, in);
+    else launch_step_d<float, 3, false>(d, st, in);
   }
 }
 
@@ -838,10 +1168,12 @@ cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
   }
   if (d->prec == CDI_FP64)
     k_np_init<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (double *)d->d_C[0], (double *)d->d_C[1], (int)d->n_pore, d->ns, d->c0);
+        (double *)d->d_C[0], (double *)d->d_C[1], nullptr, nullptr, (int)d->n_pore, d->ns, d->c0,
+        0.f);
   else
     k_np_init<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (float *)d->d_C[0], (float *)d->d_C[1], (int)d->n_pore, d->ns, (float)d->c0);
+        (float *)d->d_C[0], (float *)d->d_C[1], d->d_Clo[0], d->d_Clo[1], (int)d->n_pore, d->ns,
+        (float)d->c0, (float)(d->c0 - (double)(float)d->c0));
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "transport init");
   CDI_TRY(d, cudaMemsetAsync(d->d_acc, 0, (size_t)3 * kMaxSpecies * d->np_accs * 8, d->stream),
@@ -886,25 +1218,28 @@ cdi_status cdi_np_dt(cdi_domain *d, double scale, double *dt_out) {
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool PAIR>
 void launch_sweep_d(cdi_domain *d, cudaStream_t st, const void *members, int n, int in) {
   const SweepMember<T> *m = (const SweepMember<T> *)members;
   const NPGeo g = make_geo(d);
   switch (d->ns) {
-    case 1: k_np_sweep<T, DIM, 1><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
-    case 2: k_np_sweep<T, DIM, 2><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
-    case 3: k_np_sweep<T, DIM, 3><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
-    default: k_np_sweep<T, DIM, 4><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    case 1: k_np_sweep<T, DIM, 1, PAIR><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    case 2: k_np_sweep<T, DIM, 2, PAIR><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    case 3: k_np_sweep<T, DIM, 3, PAIR><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
+    default: k_np_sweep<T, DIM, 4, PAIR><<<d->np_blocks, kRowBlock, 0, st>>>(m, n, in, g); break;
   }
 }
 
 void launch_sweep(cdi_domain *d, cudaStream_t st, const void *members, int n, int in) {
   if (d->prec == CDI_FP64) {
-    if (d->dim == 2) launch_sweep_d<double, 2>(d, st, members, n, in);
-    else launch_sweep_d<double, 3>(d, st, members, n, in);
+    if (d->dim == 2) launch_sweep_d<double, 2, false>(d, st, members, n, in);
+    else launch_sweep_d<double, 3, false>(d, st, members, n, in);
+  } else if (d->cpair) {
+    if (d->dim == 2) launch_sweep_d<float, 2, true>(d, st, members, n, in);
+    else launch_sweep_d<float, 3, true>(d, st, members, n, in);
   } else {
-    if (d->dim == 2) launch_sweep_d<float, 2>(d, st, members, n, in);
-    else launch_sweep_d<float, 3>(d, st, members, n, in);
+    if (d->dim == 2) launch_sweep_d<float, 2, false>(d, st, members, n, in);
+    else launch_sweep_d<float, 3, false>(d, st, members, n, in);
   }
 }
 
@@ -927,11 +1262,15 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
     void *u = take((size_t)d->dim * TN);
     void *c0 = take((size_t)kMaxSpecies * TN), *c1 = take((size_t)kMaxSpecies * TN);
     void *acc = take((size_t)3 * kMaxSpecies * d->np_accs * 8);
-    ok = u && c0 && c1 && acc;
+    void *l0 = d->cpair ? take((size_t)kMaxSpecies * d->n_pore * 4) : nullptr;
+    void *l1 = d->cpair ? take((size_t)kMaxSpecies * d->n_pore * 4) : nullptr;
+    ok = u && c0 && c1 && acc && (!d->cpair || (l0 && l1));
     if (!ok) break;
     d->dt = dts[m];
     hm[m].C[0] = (T *)c0;
     hm[m].C[1] = (T *)c1;
+    hm[m].Cl[0] = (float *)l0;
+    hm[m].Cl[1] = (float *)l1;
     hm[m].u = (const T *)u;
     hm[m].phi = (const typename PhiStore<T>::type *)phi_groups[group[m]];
     hm[m].acc = (typename AccSlot<T>::type *)acc;
@@ -943,8 +1282,9 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
   for (int m = 0; m < n && s == CDI_OK; m++) {
     s = cdi_flow_scale_to(d, scale[m], (void *)hm[m].u);
     if (s != CDI_OK) break;
-    k_np_init<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(hm[m].C[0], hm[m].C[1],
-                                                            (int)d->n_pore, ns, (T)d->c0);
+    k_np_init<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        hm[m].C[0], hm[m].C[1], hm[m].Cl[0], hm[m].Cl[1], (int)d->n_pore, ns, (T)d->c0,
+        (float)(d->c0 - (double)(T)d->c0));
     d->timing.kernel_launches++;
     if (cudaMemsetAsync(hm[m].acc, 0, (size_t)3 * kMaxSpecies * d->np_accs * 8, d->stream) !=
         cudaSuccess)
@@ -990,7 +1330,7 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
   const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
   for (int m = 0; m < n && s == CDI_OK; m++) {
     k_np_sums<T><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_cmeta, hm[m].C[cur], hm[m].u, (int)d->n_pore, ns, vol, d->d_part,
+        d->d_cmeta, hm[m].C[cur], hm[m].Cl[cur], hm[m].u, (int)d->n_pore, ns, vol, d->d_part,
         d->d_counter + C_MASS, d->d_scal);
     acc_total(d, hm[m].acc, d->stream, d->d_scal);
     d->timing.kernel_launches += 2;
@@ -1027,22 +1367,27 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool PAIR>
 void launch_batch_d(cudaStream_t st, int ns, const void *members, int n, int blocks, int in) {
   const BatchMember<T> *m = (const BatchMember<T> *)members;
   switch (ns) {
-    case 1: k_np_batch<T, DIM, 1><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
-    case 2: k_np_batch<T, DIM, 2><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
-    case 3: k_np_batch<T, DIM, 3><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
-    default: k_np_batch<T, DIM, 4><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    case 1: k_np_batch<T, DIM, 1, PAIR><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    case 2: k_np_batch<T, DIM, 2, PAIR><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    case 3: k_np_batch<T, DIM, 3, PAIR><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
+    default: k_np_batch<T, DIM, 4, PAIR><<<blocks, kRowBlock, 0, st>>>(m, n, in); break;
   }
 }
 
 template <typename T>
 void launch_batch(const cdi_domain *lead, cudaStream_t st, const void *members, int n,
                   int blocks, int in) {
-  if (lead->dim == 2) launch_batch_d<T, 2>(st, lead->ns, members, n, blocks, in);
-  else launch_batch_d<T, 3>(st, lead->ns, members, n, blocks, in);
+  if (std::is_same<T, float>::value && lead->cpair) {
+    if (lead->dim == 2) launch_batch_d<T, 2, true>(st, lead->ns, members, n, blocks, in);
+    else launch_batch_d<T, 3, true>(st, lead->ns, members, n, blocks, in);
+  } else {
+    if (lead->dim == 2) launch_batch_d<T, 2, false>(st, lead->ns, members, n, blocks, in);
+    else launch_batch_d<T, 3, false>(st, lead->ns, members, n, blocks, in);
+  }
 }
 
 template <typename T>
@@ -1066,11 +1411,15 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
     void *u = take((size_t)d->dim * TN);
     void *c0 = take((size_t)kMaxSpecies * TN), *c1 = take((size_t)kMaxSpecies * TN);
     void *acc = take((size_t)3 * kMaxSpecies * d->np_accs * 8);
-    ok = u && c0 && c1 && acc;
+    void *l0 = d->cpair ? take((size_t)kMaxSpecies * d->n_pore * 4) : nullptr;
+    void *l1 = d->cpair ? take((size_t)kMaxSpecies * d->n_pore * 4) : nullptr;
+    ok = u && c0 && c1 && acc && (!d->cpair || (l0 && l1));
     if (!ok) break;
     d->dt = dts[m];
     hm[m].s.C[0] = (T *)c0;
     hm[m].s.C[1] = (T *)c1;
+    hm[m].s.Cl[0] = (float *)l0;
+    hm[m].s.Cl[1] = (float *)l1;
     hm[m].s.u = (const T *)u;
     hm[m].s.phi = (const typename PhiStore<T>::type *)phis[group[m]];
     hm[m].s.acc = (typename AccSlot<T>::type *)acc;
@@ -1091,8 +1440,9 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
       s = cdi_fail(L, CDI_ERR_CUDA, "batch: member setup");
   for (int m = 0; m < n && s == CDI_OK; m++) {
     const cdi_domain *d = doms[m / n_combos];
-    k_np_init<T><<<kRedBlocks, kRedThreads, 0, L->stream>>>(hm[m].s.C[0], hm[m].s.C[1],
-                                                            (int)d->n_pore, ns, (T)d->c0);
+    k_np_init<T><<<kRedBlocks, kRedThreads, 0, L->stream>>>(
+        hm[m].s.C[0], hm[m].s.C[1], hm[m].s.Cl[0], hm[m].s.Cl[1], (int)d->n_pore, ns, (T)d->c0,
+        (float)(d->c0 - (double)(T)d->c0));
     L->timing.kernel_launches++;
     if (cudaMemsetAsync(hm[m].s.acc, 0, (size_t)3 * kMaxSpecies * d->np_accs * 8,
                         L->stream) != cudaSuccess)
@@ -1140,8 +1490,8 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
     const double area = d->dim == 2 ? d->dx : d->dx * d->dx;
     const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
     k_np_sums<T><<<kRedBlocks, kRedThreads, 0, L->stream>>>(
-        d->d_cmeta, hm[m].s.C[cur], hm[m].s.u, (int)d->n_pore, ns, vol, L->d_part,
-        L->d_counter + C_MASS, L->d_scal);
+        d->d_cmeta, hm[m].s.C[cur], hm[m].s.Cl[cur], hm[m].s.u, (int)d->n_pore, ns, vol,
+        L->d_part, L->d_counter + C_MASS, L->d_scal);
     acc_total(d, hm[m].s.acc, L->stream, L->d_scal);
     L->timing.kernel_launches += 2;
     cudaError_t e = cudaMemcpyAsync(L->h_scal + S_OUT, L->d_scal + S_OUT,
@@ -1260,12 +1610,12 @@ cdi_status cdi_np_reduce(cdi_domain *d) {
   const double vol = d->dim == 2 ? d->dx * d->dx : d->dx * d->dx * d->dx;
   if (d->prec == CDI_FP64)
     k_np_sums<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_cmeta, (const double *)d->d_C[d->cur], (const double *)d->d_u, (int)d->n_pore,
-        d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
+        d->d_cmeta, (const double *)d->d_C[d->cur], nullptr, (const double *)d->d_u,
+        (int)d->n_pore, d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
   else
     k_np_sums<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        d->d_cmeta, (const float *)d->d_C[d->cur], (const float *)d->d_u, (int)d->n_pore,
-        d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
+        d->d_cmeta, (const float *)d->d_C[d->cur], d->d_Clo[d->cur], (const float *)d->d_u,
+        (int)d->n_pore, d->ns, vol, d->d_part, d->d_counter + C_MASS, d->d_scal);
   acc_total(d, d->d_acc, d->stream, d->d_scal);
   d->timing.kernel_launches += 2;
   CDI_TRY(d, cudaGetLastError(), "transport sums");
@@ -1278,31 +1628,38 @@ cdi_status cdi_np_reduce(cdi_domain *d) {
   return CDI_OK;
 }
 
-cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces) {
-  k_geometry<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_cmeta, (int)d->n_pore, 2 * d->dim,
-                                                         d->d_part, d->d_counter + C_GEOM,
-                                                         d->d_scal);
+cdi_status cdi_np_geometry(cdi_domain *d, double *pores, double *faces, double *sum_ux) {
+  if (d->prec == CDI_FP64)
+    k_geometry<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_cmeta, (const double *)d->d_u, (int)d->n_pore, 2 * d->dim, d->d_part,
+        d->d_counter + C_GEOM, d->d_scal);
+  else
+    k_geometry<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        d->d_cmeta, (const float *)d->d_u, (int)d->n_pore, 2 * d->dim, d->d_part,
+        d->d_counter + C_GEOM, d->d_scal);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "geometry");
-  CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_GEOM, d->d_scal + S_GEOM, 2 * sizeof(double),
+  CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_GEOM, d->d_scal + S_GEOM, 3 * sizeof(double),
                              cudaMemcpyDeviceToHost, d->stream),
           "geometry copy");
   CDI_TRY(d, cudaStreamSynchronize(d->stream), "geometry");
   *pores = d->h_scal[S_GEOM];
   *faces = d->h_scal[S_GEOM + 1];
+  if (sum_ux) *sum_ux = d->h_scal[S_GEOM + 2];
   return CDI_OK;
 }
 
 cdi_status cdi_np_column_means(cdi_domain *d, int k) {
   const size_t T = d->prec == CDI_FP64 ? 8 : 4;
   const void *C = (const char *)d->d_C[d->cur] + (size_t)k * d->n_pore * T;
+  const float *Cl = d->d_Clo[d->cur] ? d->d_Clo[d->cur] + (size_t)k * d->n_pore : nullptr;
   const int rows = d->ny * d->nz;
   if (d->prec == CDI_FP64)
     k_colmeans<double><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_words, d->W, (const double *)C,
-                                                             rows, d->d_colout);
+                                                             nullptr, rows, d->d_colout);
   else
     k_colmeans<float><<<d->nx, kRedThreads, 0, d->stream>>>(d->d_words, d->W, (const float *)C,
-                                                            rows, d->d_colout);
+                                                            Cl, rows, d->d_colout);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "column means");
   return CDI_OK;
@@ -1314,7 +1671,7 @@ cdi_status cdi_np_build_compact(cdi_domain *d) {
   const int n = (int)d->n_pore;
   const long long n_words = (long long)d->ny * d->nz * d->W;
   k_cmeta<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list, n, d->nx,
-                                                     d->d_cmeta);
+                                                     d->d_cmeta, d->d_cfl);
   k_words<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_nflags, d->d_cell_list, n, d->nx, d->W,
                                                      n_words, d->d_words);
   k_lat_nbr<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_cmeta, d->d_words, n, d->W, d->ny,
@@ -1326,14 +1683,15 @@ cdi_status cdi_np_build_compact(cdi_domain *d) {
 
 // comps rank-ordered components of the domain's precision -> FP64 lattice
 // fields (dst: comps * N doubles, 0 in solid cells).
-cdi_status cdi_np_scatter(cdi_domain *d, const void *src, int comps, double *dst) {
+cdi_status cdi_np_scatter(cdi_domain *d, const void *src, const float *lo, int comps,
+                          double *dst) {
   CDI_TRY(d, cudaMemsetAsync(dst, 0, (size_t)comps * d->N * 8, d->stream), "scatter reset");
   if (d->prec == CDI_FP64)
     k_scatter<double><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const double *)src, comps, d->d_cell_list, (int)d->n_pore, d->N, dst);
+        (const double *)src, nullptr, comps, d->d_cell_list, (int)d->n_pore, d->N, dst);
   else
     k_scatter<float><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const float *)src, comps, d->d_cell_list, (int)d->n_pore, d->N, dst);
+        (const float *)src, lo, comps, d->d_cell_list, (int)d->n_pore, d->N, dst);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "scatter");
   return CDI_OK;

@@ -60,11 +60,16 @@ def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> in
     Nf = N * (2 if mirror else 1)
     Q = 9 if dim == 2 else 19
     T = 8 if precision == cdi.FP64 else 4
-    Tpop = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2}[precision]
+    Tpop = {cdi.FP64: 8, cdi.FP32: 4, cdi.FP32_SPLIT: 8, cdi.BF16_POP: 2,
+            cdi.FP32_CPAIR: 4}[precision]
+    Tc = T + (4 if precision in (cdi.FP32_SPLIT, cdi.FP32_CPAIR) else 0)  # + low words
     nx = mask.shape[-1]
     rows = N // nx
-    flow = (Q * Tpop + (Q - 1) * 4 + 4) * n_fp + Nf * (2 if dim == 2 else 4) + dim * Nf * 8
-    transport = n_pore * (4 + 8 + dim * T + 8 + 2 * 4 * T) + rows * ((nx + 31) // 32) * 8
+    n_ovf = 2 * rows                                  # x-edge overflow slots
+    flow = ((Q * Tpop + 4 + 4 * (2 if dim == 2 else 8)) * n_fp + (Q - 1) * 4 * n_ovf
+            + Nf * (2 if dim == 2 else 4) + dim * Nf * 8)
+    transport = (n_pore * (4 + 8 + 2 + 2 * (dim - 1) * 4 + dim * T + 8 + 2 * 4 * Tc)
+                 + rows * ((nx + 31) // 32) * 8)
     lattice = N * (1 + 2 + 8 + 4 * 8)                 # mask, face flags, psi, CG vectors
     work = Nf * 4 + 2 * ((Nf + 2047) // 2048) * 4     # create-time rank and list work
     return flow + transport + lattice + work + (4 << 20)

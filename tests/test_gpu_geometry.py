@@ -65,3 +65,40 @@ def test_fibre_surface_grows_as_diameter_shrinks():
     (p8, s8), (p4, s4) = out
     assert abs(p8 - 0.8) < 0.02 and abs(p4 - 0.8) < 0.02
     assert s4 > 1.5 * s8
+
+
+@pytest.mark.parametrize("case", ["ragged37x23", "spheres19x13x11"])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32_CPAIR])
+def test_derived_figures_match_oracle(case, prec):
+    """cdi_query_derived (Sec. 4: phi, s, l_c = pi / s, U, Pe, Da; Sec. 4.1:
+    P_rm and U A P_rm dt / (V_t phi)) against the oracle's functions on the
+    oracle's own run.  Geometry figures are exact counts; U is a sum of the
+    stored (FP32 or FP64) velocities; the removal figures follow the outlet
+    concentration, so they carry its tolerance."""
+    import oracle as O
+    m = CASES[case]()
+    Z, D, c0, Ka, n = (1, -1), (1.33e-9, 2.03e-9), 10.0, 1e-6, 300
+    r = O.run_case(m, flow_tol=0.0, max_flow_steps=600, U_target=1e-4, applied_V=1.0,
+                   lambda_D=1.5e-7, n_np_steps=n)
+    with cdi.Domain(m, precision=prec) as d:
+        with pytest.raises(cdi.CDIError) as e:
+            d.derived()
+        assert e.value.status == 6
+        d.solve_flow(tol=0.0, max_steps=600, U_target=1e-4)
+        d.set_potential(1.0, c_bulk=c0, lambda_D=1.5e-7, tol=1e-13)
+        d.init_transport(Z, D, c0=c0, Ka=Ka, dt=r["dt"])
+        d.step(n)
+        g = d.derived()
+    o = O.derived(m, r["u"], r["C_out"], c0=c0, D=D, Ka=Ka, dx=1e-7, dt=r["dt"], n_steps=n)
+    for k in ("porosity", "specific_surface", "l_c_m", "elapsed_s"):
+        assert g[k] == pytest.approx(o[k], rel=1e-14), k
+    fp64 = prec == cdi.FP64
+    np.testing.assert_allclose(g["U_mps"], o["U_mps"], rtol=1e-12 if fp64 else 1e-6)
+    np.testing.assert_allclose(g["Pe"], o["Pe"], rtol=1e-12 if fp64 else 1e-6)
+    np.testing.assert_allclose(g["Da"], o["Da"], rtol=1e-14)
+    tol_c = 1e-11 if fp64 else 1e-4
+    atol = tol_c * np.asarray(r["C_out"]) / c0
+    np.testing.assert_allclose(g["removal"], o["removal"], rtol=0, atol=atol)
+    scale = o["amount"] / np.where(o["removal"] != 0, o["removal"], 1.0)
+    np.testing.assert_allclose(g["amount"], o["amount"], rtol=1e-6 if not fp64 else 1e-12,
+                               atol=np.abs(scale) * atol)

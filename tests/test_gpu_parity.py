@@ -203,7 +203,7 @@ def test_pipeline_cfg1_fp32(cfg1_oracle):
     np.testing.assert_allclose(g["C_out"], r["C_out"], rtol=TOL_C32)
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT, cdi.FP32_CPAIR])
 def test_pipeline_crop_of_1024x512(prec):
     """256x128 crop of the 1024x512 polydisperse pack (0.8 V, strong EDL
     override so migration matters), fixed flow horizon, 3000 transport
@@ -228,7 +228,7 @@ def test_pipeline_crop_of_1024x512(prec):
         assert np.max(np.abs(g["Gamma"] - r["Gamma"]) / np.abs(r["Gamma"])) < TOL_G32
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT, cdi.FP32_CPAIR])
 def test_pipeline_3d(prec):
     m, _ = inputs.grain_pack((14, 16, 22), 0.55, 2.0, 3.5, seed=12)
     r = O.run_case(m, flow_tol=0.0, max_flow_steps=1000, applied_V=1.2, c0=20.0,
@@ -262,12 +262,14 @@ def spheres48_oracle():
     return m, r
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32_CPAIR])
 def test_pipeline_3d_benchmark_storage_converged(spheres48_oracle, prec):
-    """The 3D benchmark's storage (plain FP32 populations and transport
-    fields) run to convergence and over the full transport horizon on a crop
-    of its own sphere pack: u, C and the adsorbed amount at the stated bars
-    against the oracle; FP64 storage stops at the oracle's check."""
+    """The 3D benchmark's storage (plain FP32 populations, FP32 transport
+    with FP32-pair concentrations) run to convergence and over the full
+    transport horizon on a crop of its own sphere pack: u, C and the
+    adsorbed amount at the stated bars against the oracle; FP64 storage
+    stops at the oracle's check.  (Plain FP32 concentrations miss the
+    adsorbed-amount bar over this horizon: their rounding builds up.)"""
     m, r = spheres48_oracle
     g = run_gpu(m, prec, flow_tol=1e-7, max_flow=20000, U=1e-6, V=1.2, c0=20.0, n_np=20000)
     if prec == cdi.FP64:
@@ -297,7 +299,7 @@ def crop2d_long_oracle():
 
 
 def test_pipeline_2d_benchmark_storage_long_horizon(crop2d_long_oracle):
-    """FP32-pair populations and FP32 transport (the 2D benchmark's storage)
+    """FP32-pair populations and concentrations (the 2D benchmark's storage)
     over the 50,000-step horizon: rounding drift stays inside the bars."""
     m, r = crop2d_long_oracle
     g = run_gpu(m, cdi.FP32_SPLIT, flow_tol=0.0, max_flow=3000, V=0.8, n_np=50000)
@@ -429,7 +431,7 @@ def test_autotuner_picks_a_block_size():
     assert t["np_block"] in (64, 128, 256)
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT, cdi.FP32_CPAIR])
 def test_save_and_load_state_resume_bitwise(prec):
     """A run stopped after n1 steps, saved, loaded into a fresh domain of the
     same mask and resumed for n2 steps equals the uninterrupted n1 + n2 run."""

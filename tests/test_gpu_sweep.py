@@ -31,7 +31,7 @@ def single_runs(d, combos, lam, c0, Ka, n_steps):
     return np.array(gam), np.array(cout), np.array(dts)
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_CPAIR])
 @pytest.mark.parametrize("shape", [(23, 37), (9, 11, 17)])
 def test_sweep_members_equal_single_runs(prec, shape):
     m, _ = inputs.grain_pack(shape, 0.6, 1.5, 4.0, seed=21)
@@ -76,7 +76,7 @@ def test_sweep_argument_errors():
         assert np.all(g == 0)
 
 
-@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32])
+@pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_CPAIR])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_batch_over_uneven_geometries_equals_single_runs(prec, dim):
     """cdi_sweep_batch: members of several uneven geometries in one launch per
