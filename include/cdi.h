@@ -25,8 +25,10 @@
  *   - The mask is uint8, 1 = solid (carbon), 0 = pore; host memory owned by
  *     the caller and copied by cdi_create_domain.
  *   - All device memory belongs to the domain.  It is obtained from the
- *     caller's allocator when one is given, else from cudaMalloc; everything
- *     is released by cdi_destroy_domain.
+ *     caller's allocator when one is given, else by stream-ordered allocation
+ *     on the domain's stream (cudaMallocAsync/cudaFreeAsync, which do not
+ *     synchronise the device); everything is released by
+ *     cdi_destroy_domain.
  *   - Work runs on the domain's stream: the caller's stream if given, else a
  *     stream the domain creates.  cdi_step_transport returns without waiting;
  *     the queries and cdi_copy_field wait for the stream.
@@ -174,6 +176,27 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
 cdi_status cdi_solve_flow(cdi_domain *dom, const cdi_flow_params *p,
                           int64_t *steps_out, double *residual_out);
 
+/* Stokes flow of several electrode images at once (the geometry studies of
+ * Sec. 4-5 solve Eq. 7-8 on many images): every domain runs the lattice
+ * Boltzmann solve of cdi_solve_flow, but all of them advance together, one
+ * kernel launch per step over the pore sites of every domain still running;
+ * each domain takes its own residual every check_every steps and leaves the
+ * batch at its first check below tol (or at max_steps), so its steps,
+ * residual and field equal, bit for bit, those of cdi_solve_flow with the
+ * same parameters.  Then each velocity is scaled to U_target_mps.
+ *   doms: n_doms >= 1 distinct domains on the current device, all of the
+ *     same dimension and precision; doms[0]'s stream runs the batch and
+ *     doms[0]'s allocator provides a small member table for the call.
+ *   steps_out, residual_out, status_out: host arrays of n_doms (any may be
+ *     NULL); status_out[i] is CDI_OK, CDI_ERR_NOT_CONVERGED (state kept, as
+ *     cdi_solve_flow) or CDI_ERR_CUDA (diverged).
+ * Returns CDI_OK when every domain converged, CDI_ERR_NOT_CONVERGED when
+ * some did not, another error when the batch itself failed (reported on
+ * doms[0]).  Blocks until done. */
+cdi_status cdi_solve_flow_batch(cdi_domain *const *doms, int n_doms,
+                                const cdi_flow_params *p, int64_t *steps_out,
+                                double *residual_out, int *status_out);
+
 /* Rescale the solved Stokes field to another pore-mean velocity U = sum(u) /
  * (N phi) of Sec. 4 (Eq. 2 is linear in the force, so one solve serves every
  * velocity of the Pe sweeps of Sec. 4.1).  Requires a
@@ -214,7 +237,26 @@ cdi_status cdi_init_transport(cdi_domain *dom, const cdi_species *sp,
  * frozen potentials. */
 cdi_status cdi_set_coupling(cdi_domain *dom, int64_t every_steps);
 
-/* Advance n_steps >= 0 explicit steps (Eq. 3 with Eq. 6); asynchronous. */
+/* Implicit finite-volume transport (Sec. 2: the paper integrates Eq. 3 with
+ * an implicit finite-volume scheme).  tol > 0: every later
+ * cdi_step_transport step is a backward Euler step, (I + dt A) C' = C +
+ * dt b per species with the face fluxes of the explicit step (Eq. 3, Eq. 6),
+ * solved by Jacobi-preconditioned BiCGStab in FP64 to a relative residual
+ * below tol within max_iter iterations (else CDI_ERR_NOT_CONVERGED with the
+ * step not taken).  The step is unconditionally stable and keeps C >= 0, so
+ * cdi_init_transport's dt_s may exceed the explicit bound by orders of
+ * magnitude; the adsorbed/inflow/outflow accounts take the fluxes at the new
+ * concentrations (the mass balance closes as in the explicit scheme).
+ * tol <= 0 returns to the explicit scheme.  With cdi_set_coupling the
+ * potential is still re-solved before every block of K steps.  Sweeps and
+ * batches always step explicitly.  cdi_step_transport waits for the stream
+ * at every linear iteration check.  Device memory: (9 or 11 + 7 / species)
+ * FP64 values per pore cell, taken on the first call. */
+cdi_status cdi_set_implicit(cdi_domain *dom, double tol, int max_iter);
+
+/* Advance n_steps >= 0 transport steps (Eq. 3 with Eq. 6): explicit unless
+ * cdi_set_implicit chose the implicit scheme; explicit steps are
+ * asynchronous. */
 cdi_status cdi_step_transport(cdi_domain *dom, int64_t n_steps);
 
 /* One member of a transport sweep. */

@@ -80,6 +80,8 @@ def _load():
         lib.orc_pnp_run.argtypes = [i, i, i, i, P, i, P, i, P, P, d, d, d, d, d, l, l, d, d,
                                     d, P, P, P, P, P]
         lib.orc_pnp_run.restype = i
+        lib.orc_np_operator.argtypes = [i, i, i, i, P, i, P, P, i, d, d, d, d, d, P, P, P, P, P]
+        lib.orc_np_operator.restype = i
         lib.orc_set_threads.argtypes = [i]
         lib.orc_set_threads.restype = None
         lib.orc_threads.argtypes = []
@@ -247,6 +249,71 @@ def np_run(mask, u, psi_field, z, D, *, c0, dt, n_steps, dx=1e-7, Ka=1e-6,
     if st < 0:
         raise ValueError("orc_np_run rejected its arguments")
     return C, G, I, O
+
+
+def np_operator(mask, u, psi_field, zi, Di, *, c0, dx=1e-7, Ka=1e-6, T=T_DEFAULT,
+                lateral_walls=False):
+    """The transport operator of one species (Eq. 3 with Eq. 6, the face rules
+    of np_run): (1/dx) sum_f J_f(C) = A C - b.  Returns (A as a scipy CSR
+    matrix, b)."""
+    import scipy.sparse as sp
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    N = m.size
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    p = np.ascontiguousarray(psi_field, dtype=np.float64)
+    rows = np.zeros(7 * N, dtype=np.int64)
+    cols = np.zeros(7 * N, dtype=np.int64)
+    vals = np.zeros(7 * N)
+    b = np.zeros(N)
+    nnz = ctypes.c_long(0)
+    st = _load().orc_np_operator(dim, nx, ny, nz, _ptr(m), int(lateral_walls), _ptr(u), _ptr(p),
+                                 int(zi), float(Di), float(dx), float(Ka), float(c0),
+                                 thermal_voltage(T), _ptr(rows), _ptr(cols), _ptr(vals),
+                                 ctypes.byref(nnz), _ptr(b))
+    if st < 0:
+        raise ValueError("orc_np_operator rejected its arguments")
+    k = nnz.value
+    A = sp.csr_matrix((vals[:k], (rows[:k], cols[:k])), shape=(N, N))
+    return A, b
+
+
+def np_implicit_run(mask, u, psi_field, z, D, *, c0, dt, n_steps, dx=1e-7, Ka=1e-6,
+                    T=T_DEFAULT, lateral_walls=False, C=None):
+    """The implicit finite-volume transport of Sec. 2: backward Euler steps
+    (I + dt A) C^{n+1} = C^n + dt b per species, solved by a sparse LU
+    factorisation (a library primitive); the adsorbed, inflow and outflow
+    accounts take the face fluxes at C^{n+1}, evaluated by np_run's face
+    rules (one explicit evaluation of the fluxes, whose concentration update
+    is discarded).  Starts from C = c0 in the pore cells unless C is given.
+    Returns (C, Gamma, In, Out) like np_run."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    m = _mask(mask)
+    z, D = _species(z, D)
+    ns = len(z)
+    N = m.size
+    if C is None:
+        C = np.where(m[None] == 0, float(c0), 0.0) * np.ones((ns,) + m.shape)
+    C = np.array(C, dtype=np.float64).reshape(ns, N)
+    solvers, rhs_b = [], []
+    for k in range(ns):
+        A, b = np_operator(m, u, psi_field, z[k], D[k], c0=c0, dx=dx, Ka=Ka, T=T,
+                           lateral_walls=lateral_walls)
+        M = (sp.identity(N, format="csr") + dt * A).tocsc()
+        solvers.append(spla.splu(M))
+        rhs_b.append(b)
+    G, I, O = np.zeros(ns), np.zeros(ns), np.zeros(ns)
+    for _ in range(n_steps):
+        for k in range(ns):
+            C[k] = solvers[k].solve(C[k] + dt * rhs_b[k])
+        # the accounts of this step: the fluxes at C^{n+1}, times dt
+        _, g, i, o = np_run(m, u, psi_field, z, D, c0=c0, dt=dt, n_steps=1, dx=dx, Ka=Ka, T=T,
+                            lateral_walls=lateral_walls, C=C.reshape((ns,) + m.shape))
+        G += g
+        I += i
+        O += o
+    return C.reshape((ns,) + m.shape), G, I, O
 
 
 def charge_coef(dx, eps_r=EPS_R_DEFAULT):

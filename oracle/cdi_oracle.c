@@ -501,6 +501,63 @@ int orc_np_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
   return 0;
 }
 
+/* The transport operator of one species as a sparse matrix: the face fluxes
+ * of orc_np_run are affine in C, (1/dx) sum_f J_f(C)_P = (A C)_P - b_P, with
+ *   pore neighbour: A_PP += (D/dx^2) B(-P_f),  A_P,nb += -(D/dx^2) B(P_f)
+ *   inlet ghost:    A_PP += (D/dx^2) B(-P_f),  b_P += (D/dx^2) B(P_f) c0
+ *   outlet ghost:   A_PP += (D/dx^2) (B(-P_f) - B(P_f))
+ *   solid face:     A_PP += K_eff / dx                          (Eq. 6)
+ * (rows of solid cells are empty).  The triplets (row, col, val) go to
+ * rows/cols/vals (room for 7 per cell; duplicates are to be summed), their
+ * count to *nnz; b (N) is overwritten. */
+int orc_np_operator(int dim, int nx, int ny, int nz, const uint8_t *mask,
+                    int lateral_walls, const double *u, const double *psi, int zi,
+                    double Di, double dx, double Ka, double c0, double VT, long *rows,
+                    long *cols, double *vals, long *nnz, double *b) {
+  if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1) return -1;
+  long N = (long)nx * ny * nz;
+  double Keff = Ka / (1.0 + Ka * dx / (2.0 * Di));
+  double *dummyC = (double *)calloc((size_t)N, sizeof(double));
+  long k = 0;
+  for (int zz = 0; zz < nz; zz++)
+    for (int y = 0; y < ny; y++)
+      for (int x = 0; x < nx; x++) {
+        long P = ((long)zz * ny + y) * nx + x;
+        b[P] = 0.0;
+        if (mask[P]) continue;
+        double diag = 0.0;
+        for (int f = 0; f < 2 * dim; f++) {
+          double Pf = 0.0, Cnb = 0.0;
+          long nb;
+          int kind = np_face(dim, nx, ny, nz, mask, lateral_walls, u, psi, dummyC, c0, zi, Di,
+                             dx, VT, x, y, zz, f, &Pf, &Cnb);
+          if (kind == FACE_WALL) continue;
+          if (kind == FACE_SOLID) {
+            diag += Keff / dx;
+          } else if (kind == FACE_FLUID) {
+            diag += Di / (dx * dx) * bernoulli(-Pf);
+            classify_face(mask, nx, ny, nz, lateral_walls, x, y, zz, f, &nb);
+            rows[k] = P;
+            cols[k] = nb;
+            vals[k] = -Di / (dx * dx) * bernoulli(Pf);
+            k++;
+          } else if (kind == FACE_INLET) {
+            diag += Di / (dx * dx) * bernoulli(-Pf);
+            b[P] += Di / (dx * dx) * bernoulli(Pf) * c0;
+          } else { /* outlet: the ghost copies the cell */
+            diag += Di / (dx * dx) * (bernoulli(-Pf) - bernoulli(Pf));
+          }
+        }
+        rows[k] = P;
+        cols[k] = P;
+        vals[k] = diag;
+        k++;
+      }
+  *nnz = k;
+  free(dummyC);
+  return 0;
+}
+
 /* Coupled Poisson-Nernst-Planck (Eq. 3-5): before every block of K explicit
  * steps, the potential is solved from Eq. 4 with the net charge density of
  * Eq. 5 of the current concentrations (Laplace operator, Dirichlet psi_s at

@@ -77,6 +77,15 @@ int orc_pnp_run(int dim, int nx, int ny, int nz, const uint8_t *mask,
                 double psi_tol, double *C, double *Gamma, double *In, double *Out,
                 double *psi);
 
+/* The transport operator of species (zi, Di): (1/dx) sum_f J_f(C) = A C - b
+ * with the face rules of orc_np_run, as (row, col, val) triplets (room for
+ * 7 per cell; duplicates to be summed) and b (N).  The implicit (backward
+ * Euler) finite-volume step of Sec. 2 solves (I + dt A) C' = C + dt b. */
+int orc_np_operator(int dim, int nx, int ny, int nz, const uint8_t *mask,
+                    int lateral_walls, const double *u, const double *psi, int zi,
+                    double Di, double dx, double Ka, double c0, double VT, long *rows,
+                    long *cols, double *vals, long *nnz, double *b);
+
 /* Host threads used by the loops above (OpenMP).  The loops that run in
  * parallel write disjoint outputs; sums are formed in a fixed order (per
  * grid row, then over rows), so results do not depend on the thread count. */

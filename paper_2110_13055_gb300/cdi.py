@@ -87,6 +87,8 @@ SIGNATURES = [
                                   ctypes.POINTER(c_void_p)]),
     ("cdi_solve_flow", c_int, [c_void_p, ctypes.POINTER(cdi_flow_params),
                                ctypes.POINTER(c_int64), ctypes.POINTER(c_double)]),
+    ("cdi_solve_flow_batch", c_int, [c_void_p, c_int, ctypes.POINTER(cdi_flow_params),
+                                     c_void_p, c_void_p, c_void_p]),
     ("cdi_set_velocity", c_int, [c_void_p, c_double]),
     ("cdi_set_potential", c_int, [c_void_p, c_double, ctypes.POINTER(cdi_elec_params),
                                   ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
@@ -94,6 +96,7 @@ SIGNATURES = [
                                    c_double, c_double, ctypes.POINTER(c_double)]),
     ("cdi_step_transport", c_int, [c_void_p, c_int64]),
     ("cdi_set_coupling", c_int, [c_void_p, c_int64]),
+    ("cdi_set_implicit", c_int, [c_void_p, c_double, c_int]),
     ("cdi_sweep_transport", c_int, [c_void_p, ctypes.POINTER(cdi_combo), c_int,
                                     ctypes.POINTER(cdi_elec_params),
                                     ctypes.POINTER(cdi_species), c_int, c_double, c_double,
@@ -185,6 +188,27 @@ def solve_flow(handle, params: cdi_flow_params, allow_not_converged=False):
     return steps.value, res.value, st
 
 
+def solve_flow_batch(handles, params: cdi_flow_params, allow_not_converged=False):
+    """cdi_solve_flow_batch: returns (steps, residuals, statuses) per domain."""
+    nd = len(handles)
+    hs = (c_void_p * nd)(*[h.value if isinstance(h, c_void_p) else h for h in handles])
+    steps, res = np.zeros(nd, np.int64), np.zeros(nd)
+    st = np.zeros(nd, np.int32)
+    rc = load().cdi_solve_flow_batch(hs, nd, ctypes.byref(params), _dptr(steps), _dptr(res),
+                                     _dptr(st))
+    if not (allow_not_converged and rc == 4):
+        _check(rc, handles[0])
+    return steps, res, st
+
+
+def flow_batch(domains, *, tau=1.0, force=1e-6, tol=1e-8, check_every=100,
+               max_steps=2_000_000, U_target=1e-4, allow_not_converged=False):
+    """cdi_solve_flow_batch over Domain objects."""
+    p = cdi_flow_params(float(tau), float(force), float(tol), int(check_every), int(max_steps),
+                        float(U_target))
+    return solve_flow_batch([d.handle for d in domains], p, allow_not_converged)
+
+
 def set_velocity(handle, U_target: float):
     _check(load().cdi_set_velocity(handle, c_double(U_target)), handle)
 
@@ -247,6 +271,10 @@ def batch(domains, combos, *, z=(1, -1), D=(1.33e-9, 2.03e-9), c0=10.0, Ka=1e-6,
     for d in domains:
         d.ns = 0
     return sweep_batch([d.handle for d in domains], combos, p, z, D, c0, Ka, n_steps)
+
+
+def set_implicit(handle, tol: float, max_iter: int = 1000):
+    _check(load().cdi_set_implicit(handle, c_double(tol), c_int(max_iter)), handle)
 
 
 def set_coupling(handle, every_steps: int):
@@ -487,6 +515,12 @@ class Domain:
 
     def timing(self, reset=False):
         return query_timing(self.handle, reset)
+
+    def set_implicit(self, tol: float = 1e-12, max_iter: int = 1000):
+        """Backward Euler transport steps (Sec. 2's implicit finite volumes),
+        solved to the relative residual tol; tol <= 0 returns to explicit
+        steps."""
+        set_implicit(self.handle, tol, max_iter)
 
     def set_coupling(self, every_steps: int):
         """Re-solve the potential from the net charge every ``every_steps``

@@ -27,13 +27,18 @@ cdi_status cdi_cuda_fail(cdi_domain *d, cudaError_t e, const char *what) {
   return cdi_fail(d, e == cudaErrorMemoryAllocation ? CDI_ERR_OOM : CDI_ERR_CUDA, m);
 }
 
+// Device memory: the caller's allocator when one was given, else
+// stream-ordered allocation on the domain's stream (cudaMallocAsync /
+// cudaFreeAsync from the device's default memory pool), which, unlike
+// cudaMalloc/cudaFree, does not synchronise the device, so domains created
+// and destroyed while others run do not stall them.
 void *cdi_dev_alloc(cdi_domain *d, size_t bytes) {
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~size_t(255);
   void *p = nullptr;
   if (d->has_alloc) {
     p = d->alloc.alloc(bytes, d->alloc.ctx);
-  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  } else if (cudaMallocAsync(&p, bytes, d->stream) != cudaSuccess) {
     (void)cudaGetLastError();
     p = nullptr;
   }
@@ -41,29 +46,52 @@ void *cdi_dev_alloc(cdi_domain *d, size_t bytes) {
   return p;
 }
 
-// Release one block from cdi_dev_alloc (after the stream has finished with it).
+static void dev_free(cdi_domain *d, void *p, size_t bytes) {
+  if (d->has_alloc)
+    d->alloc.free(p, bytes, d->alloc.ctx);
+  else if (cudaFreeAsync(p, d->stream) != cudaSuccess)
+    (void)cudaGetLastError();
+}
+
+// Release one block from cdi_dev_alloc (after the stream has finished with
+// it: stream-ordered frees take effect in stream order).
 void cdi_dev_release(cdi_domain *d, void *p) {
   for (size_t i = 0; i < d->blocks.size(); i++) {
     if (d->blocks[i].p != p) continue;
-    if (d->has_alloc)
-      d->alloc.free(p, d->blocks[i].bytes, d->alloc.ctx);
-    else
-      cudaFree(p);
+    dev_free(d, p, d->blocks[i].bytes);
     d->blocks.erase(d->blocks.begin() + (long)i);
     return;
   }
 }
 
+// Pinned host blocks for the device scalars, recycled across domains
+// (freeing pinned memory would synchronise the device).
+static std::mutex g_pinned_mutex;
+static std::vector<double *> g_pinned_free;
+
+static cudaError_t pinned_take(double **p) {
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mutex);
+    if (!g_pinned_free.empty()) {
+      *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost(reinterpret_cast<void **>(p), S_COUNT * 8);
+}
+
+static void pinned_give(double *p) {
+  std::lock_guard<std::mutex> lock(g_pinned_mutex);
+  g_pinned_free.push_back(p);
+}
+
 static void free_all(cdi_domain *d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
-  for (auto &b : d->blocks) {
-    if (d->has_alloc)
-      d->alloc.free(b.p, b.bytes, d->alloc.ctx);
-    else
-      cudaFree(b.p);
-  }
+  for (auto &b : d->blocks) dev_free(d, b.p, b.bytes);
   d->blocks.clear();
-  if (d->h_scal) cudaFreeHost(d->h_scal);
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  if (d->h_scal) pinned_give(d->h_scal);
   d->h_scal = nullptr;
   if (d->flow_graph) cudaGraphExecDestroy(d->flow_graph);
   if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
@@ -292,7 +320,7 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   d->d_acc = (double *)A((size_t)3 * cdi::kMaxSpecies * d->np_accs * 8);
   d->d_part = (double *)A((size_t)16 * cdi::kRedBlocks * 8);
   d->d_counter = (unsigned int *)A(16 * sizeof(unsigned int));
-  d->d_scal = (double *)A(64 * 8);
+  d->d_scal = (double *)A(S_COUNT * 8);
   d->d_cg = (double *)A((size_t)4 * N * 8);
   d->d_colout = (double *)A((size_t)D.nx * 8);
   if (!ok) {
@@ -300,21 +328,21 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
     delete d;
     return cdi_fail(nullptr, CDI_ERR_OOM, "device allocation failed");
   }
-  e = cudaMallocHost(&d->h_scal, 64 * 8);
+  e = pinned_take(&d->h_scal);
   if (e != cudaSuccess) {
     cdi_cuda_fail(nullptr, e, "pinned scalars");
     free_all(d);
     delete d;
     return CDI_ERR_CUDA;
   }
-  std::memset(d->h_scal, 0, 64 * 8);
+  std::memset(d->h_scal, 0, S_COUNT * 8);
   cdi_status s = CDI_OK;
   auto chk = [&](cudaError_t ee, const char *w) {
     if (s == CDI_OK && ee != cudaSuccess) s = cdi_cuda_fail(d, ee, w);
   };
   chk(cudaMemcpyAsync(d->d_mask, mask, N, cudaMemcpyHostToDevice, d->stream), "upload mask");
   chk(cudaMemsetAsync(d->d_counter, 0, 16 * sizeof(unsigned int), d->stream), "memset");
-  chk(cudaMemsetAsync(d->d_scal, 0, 64 * 8, d->stream), "memset");
+  chk(cudaMemsetAsync(d->d_scal, 0, S_COUNT * 8, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_g, 0, nq * Tpop, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_uflow, 0, (size_t)D.dim * Nf * 8, d->stream), "memset");
   chk(cudaMemsetAsync(d->d_u, 0, (size_t)D.dim * n_pore * T, d->stream), "memset");
@@ -380,6 +408,55 @@ cdi_status cdi_solve_flow(cdi_domain *d, const cdi_flow_params *p, int64_t *step
   return CDI_OK;
 }
 
+cdi_status cdi_solve_flow_batch(cdi_domain *const *doms, int n_doms, const cdi_flow_params *p,
+                                int64_t *steps_out, double *residual_out, int *status_out) {
+  if (!doms || n_doms < 1 || !doms[0])
+    return cdi_fail(nullptr, CDI_ERR_INVALID_ARG, "flow batch: no domains");
+  cdi_domain *L = doms[0];
+  if (!p) return cdi_fail(L, CDI_ERR_INVALID_ARG, "NULL argument");
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+    return cdi_fail(L, CDI_ERR_INVALID_ARG, "tau must be > 1/2");
+  if (p->check_every < 2 || (p->check_every % 2) != 0)
+    return cdi_fail(L, CDI_ERR_INVALID_ARG, "check_every must be even and >= 2");
+  if (p->max_steps < 0 || (p->max_steps % p->check_every) != 0)
+    return cdi_fail(L, CDI_ERR_INVALID_ARG, "max_steps must be a multiple of check_every");
+  if (!std::isfinite(p->force_lu) || !std::isfinite(p->U_target_mps))
+    return cdi_fail(L, CDI_ERR_INVALID_ARG, "non-finite force or velocity");
+  for (int i = 0; i < n_doms; i++) {
+    if (!doms[i]) return cdi_fail(L, CDI_ERR_INVALID_ARG, "flow batch: NULL domain");
+    if (doms[i]->dim != L->dim || doms[i]->prec != L->prec)
+      return cdi_fail(L, CDI_ERR_INVALID_ARG,
+                      "flow batch: domains differ in dimension or precision");
+    for (int j = 0; j < i; j++)
+      if (doms[j] == doms[i]) return cdi_fail(L, CDI_ERR_INVALID_ARG, "flow batch: repeated domain");
+  }
+  std::vector<int64_t> steps(n_doms);
+  std::vector<double> res(n_doms);
+  std::vector<int> st(n_doms);
+  for (int i = 0; i < n_doms; i++) {
+    doms[i]->flow_done = false;
+    doms[i]->np_ready = false;
+  }
+  cdi_status s = cdi_flow_batch(doms, n_doms, p, steps.data(), res.data(), st.data());
+  if (s != CDI_OK) return s;
+  bool all = true;
+  for (int i = 0; i < n_doms; i++) {
+    if (steps_out) steps_out[i] = steps[i];
+    if (residual_out) residual_out[i] = res[i];
+    if (status_out) status_out[i] = st[i];
+    if (st[i] == CDI_ERR_CUDA) {
+      all = false;
+      continue;
+    }
+    cdi_status s2 = cdi_flow_export(doms[i], p->U_target_mps);
+    if (s2 != CDI_OK) return cdi_fail(L, s2, std::string("flow batch: ") + doms[i]->err);
+    doms[i]->flow_done = true;
+    if (st[i] != CDI_OK) all = false;
+  }
+  if (!all) return cdi_fail(L, CDI_ERR_NOT_CONVERGED, "flow batch: some domains did not converge");
+  return CDI_OK;
+}
+
 cdi_status cdi_set_velocity(cdi_domain *d, double U) {
   if (!d) return CDI_ERR_INVALID_ARG;
   if (!d->flow_done) return cdi_fail(d, CDI_ERR_STATE, "no solved flow");
@@ -423,6 +500,21 @@ cdi_status cdi_set_potential(cdi_domain *d, double applied_V, const cdi_elec_par
   if (s == CDI_ERR_NOT_CONVERGED)
     return cdi_fail(d, s, "potential solve did not reach tol within max_iter");
   return s;
+}
+
+cdi_status cdi_set_implicit(cdi_domain *d, double tol, int max_iter) {
+  if (!d) return CDI_ERR_INVALID_ARG;
+  if (!std::isfinite(tol)) return cdi_fail(d, CDI_ERR_INVALID_ARG, "non-finite tolerance");
+  if (tol <= 0.0) {
+    d->imp_tol = 0.0;
+    return CDI_OK;
+  }
+  if (max_iter < 1) return cdi_fail(d, CDI_ERR_INVALID_ARG, "max_iter must be >= 1");
+  cdi_status s = cdi_imp_prepare(d);
+  if (s != CDI_OK) return s;
+  d->imp_tol = tol;
+  d->imp_max_iter = max_iter;
+  return CDI_OK;
 }
 
 cdi_status cdi_set_coupling(cdi_domain *d, int64_t every_steps) {
@@ -531,6 +623,11 @@ cdi_status prepare_sweep(cdi_domain *d, cdi_domain *owner, const cdi_combo *comb
     void *ph = cdi_dev_alloc(owner, (size_t)d->n_pore * 8);
     if (!ph) {
       s = cdi_fail(d, CDI_ERR_OOM, "sweep: potential buffer");
+      break;
+    }
+    // stream-ordered allocation on the owner's stream, used on d's stream
+    if (owner != d && cudaStreamSynchronize(owner->stream) != cudaSuccess) {
+      s = cdi_fail(d, CDI_ERR_CUDA, "sweep: potential buffer");
       break;
     }
     phis.push_back(ph);

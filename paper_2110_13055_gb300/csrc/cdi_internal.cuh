@@ -276,8 +276,8 @@ struct cdi_domain {
                                 // FP64, or an FP32 pair in FP32 modes)
   double *d_part = nullptr;     // reduction partials (8*kRedBlocks)
   unsigned int *d_counter = nullptr;  // last-block counters (8 slots)
-  double *d_scal = nullptr;     // device scalars (64)
-  double *h_scal = nullptr;     // pinned host copy of the scalars (64)
+  double *d_scal = nullptr;     // device scalars (S_COUNT)
+  double *h_scal = nullptr;     // pinned host copy of the scalars (S_COUNT)
   double *d_cg = nullptr;       // 4*N CG work vectors (r, p, q, diag)
   double *d_colout = nullptr;   // nx column means
 
@@ -297,6 +297,15 @@ struct cdi_domain {
   double psi_s = 0.0, eps_r = 78.5, psi_tol = 1e-12;
   int psi_max_iter = 100000;
   int64_t couple_K = 0;
+  // implicit (backward Euler) transport: on when imp_tol > 0
+  double imp_tol = 0.0;
+  int imp_max_iter = 0;
+  bool imp_stale = true;        // the operator must be rebuilt before a step
+  int64_t imp_iters = 0;        // linear iterations so far
+  double imp_last_rel = 0.0;    // last relative residual
+  double *d_icoef = nullptr;    // operator coefficients of every species (FP64)
+  double *d_iwork = nullptr;    // 7 * n_pore FP64 work vectors
+  double *d_iscal = nullptr;    // the solver's device scalars (16)
   double *d_src = nullptr;      // N charge terms of Eq. 4 (coupled mode only)
   int cur = 0;                  // which of d_C holds the current state
   int64_t np_steps = 0;
@@ -341,12 +350,14 @@ enum {
   S_OUTP = 36,                              // kMaxSpecies: plain outlet sums
   S_ACC = 40,                               // 3*kMaxSpecies: Gamma/In/Out sums
   S_OUTN = 52,                              // pore cells in the outlet column
-  S_GEOM = 56                               // pore cells, pore-solid faces, sum u_x
+  S_GEOM = 56,                              // pore cells, pore-solid faces, sum u_x
+  S_IMP = 64,                               // 16: the implicit solver's scalars (host copy)
+  S_COUNT = 80                              // slots in d_scal / h_scal
 };
 
 // Counter slots in d_counter.
 enum { C_RES = 0, C_ULAT = 1, C_CG1 = 2, C_CG2 = 3, C_DT = 4, C_OUT = 5, C_MASS = 6, C_ACC = 7,
-       C_GEOM = 8 };
+       C_GEOM = 8, C_IMP = 9 };
 
 enum { PH_FLOW = 0, PH_CHECK = 1, PH_PSI = 2, PH_NP = 3 };
 
@@ -380,6 +391,8 @@ cdi_status cdi_build_lists(cdi_domain *d, int *work);
 cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
                         double *res);
 cdi_status cdi_flow_export(cdi_domain *d, double U_target);
+cdi_status cdi_flow_batch(cdi_domain *const *doms, int n_doms, const cdi_flow_params *p,
+                          int64_t *steps, double *res, int *status);
 cdi_status cdi_flow_velocity_lattice(cdi_domain *d);
 cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double *src,
                          double tol, int max_iter, int *iters, double *relres);
@@ -402,3 +415,5 @@ void cdi_dev_release(cdi_domain *d, void *p);
 cdi_status cdi_np_steps(cdi_domain *d, int64_t n);
 cdi_status cdi_np_reduce(cdi_domain *d);
 cdi_status cdi_np_column_means(cdi_domain *d, int species);
+cdi_status cdi_imp_prepare(cdi_domain *d);
+cdi_status cdi_imp_steps(cdi_domain *d, int64_t n);

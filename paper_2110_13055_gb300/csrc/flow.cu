@@ -18,6 +18,7 @@
 // (collision in FP32, half the bytes of FP32, low accuracy).
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include <cuda_bf16.h>
 
@@ -315,16 +316,14 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 // (more resident blocks per SM: the step is latency-bound on its scattered
 // loads, so occupancy matters more than a few spare registers; the bound is
 // chosen per variant so that nothing spills)
-template <typename S, int DIM, bool ODD, int BS, int MINT>
-__global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128) / BS)
-    k_lbm_step(S *__restrict__ g, LinkGeo lg, int n,
-               typename Arith<S>::type omega, typename Arith<S>::type fx_half,
-               typename Arith<S>::type fsrc) {
+template <typename S, int DIM, bool ODD>
+__device__ __forceinline__ void lbm_body(S *__restrict__ g, const LinkGeo &lg, int n, int k0,
+                                         typename Arith<S>::type omega,
+                                         typename Arith<S>::type fx_half,
+                                         typename Arith<S>::type fsrc) {
   using T = typename Arith<S>::type;
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n) return;
   int nb[Q];
   load_links<DIM, ODD>(lg, k0, n, nb);
   T gi[Q];
@@ -362,6 +361,16 @@ __global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof
   for (int i = 0; i < Q; i++) g[write_slot<DIM, ODD>(nb, k0, i, n)] = narrow<S>(go[i]);
 }
 
+template <typename S, int DIM, bool ODD, int BS, int MINT>
+__global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128) / BS)
+    k_lbm_step(S *__restrict__ g, LinkGeo lg, int n,
+               typename Arith<S>::type omega, typename Arith<S>::type fx_half,
+               typename Arith<S>::type fsrc) {
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n) return;
+  lbm_body<S, DIM, ODD>(g, lg, n, k0, omega, fx_half, fsrc);
+}
+
 // Constants of the pair collision, each an unevaluated FP32 pair.
 struct SplitConst {
   F2 omega;     // 1 / tau
@@ -375,7 +384,7 @@ struct SplitConst {
 // collision carried out in pair arithmetic.
 template <int DIM, bool ODD, bool TAU1>
 __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__restrict__ gl,
-                                               const LinkGeo &lg, int n,
+                                               const LinkGeo &lg, int n, int k0,
                                                const SplitConst &c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
@@ -384,8 +393,6 @@ __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__
   constexpr F2 kW0 = {(float)w0, (float)(w0 - (double)(float)w0)};
   constexpr F2 kWA = {(float)wa, (float)(wa - (double)(float)wa)};
   constexpr F2 kWD = {(float)wd, (float)(wd - (double)(float)wd)};
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n) return;
   int nb[Q];
   load_links<DIM, ODD>(lg, k0, n, nb);
   F2 gi[Q];
@@ -454,7 +461,9 @@ template <int DIM, bool ODD, bool TAU1, int BS>
 __global__ void __launch_bounds__(BS)
     k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl, LinkGeo lg, int n,
                      SplitConst c) {
-  lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, c);
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n) return;
+  lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, k0, c);
 }
 
 // The same step with registers capped so that MINT threads share an SM.
@@ -462,7 +471,44 @@ template <int DIM, bool ODD, bool TAU1, int BS, int MINT>
 __global__ void __launch_bounds__(BS, MINT / BS)
     k_lbm_step_split_occ(float *__restrict__ gh, float *__restrict__ gl, LinkGeo lg, int n,
                          SplitConst c) {
-  lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, c);
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n) return;
+  lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, k0, c);
+}
+
+// One member of a batched flow solve: a domain's populations, neighbour data
+// and pore-site count; blocks [block0, block0 + ceil(n / kLbmBatchBlock)) of
+// the launch are its own.
+template <typename S> struct LbmMember {
+  S *g;
+  float *glo;  // low words (pair storage) or null
+  LinkGeo lg;
+  int n, block0;
+};
+constexpr int kLbmBatchBlock = 128;
+
+// One LBM step of every member of a batch in one launch: block b belongs to
+// the member whose block range holds it (binary search over the ascending
+// block0) and runs that member's sites with the single-run step's body, so
+// every member's populations equal those of its own solve bit for bit.
+template <typename S, int DIM, bool ODD, int MODE, bool TAU1>
+__global__ void __launch_bounds__(kLbmBatchBlock)
+    k_lbm_batch(const LbmMember<S> *__restrict__ members, int n_members,
+                typename Arith<S>::type omega, typename Arith<S>::type fx_half,
+                typename Arith<S>::type fsrc, SplitConst c) {
+  int lo = 0, hi = n_members - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (members[mid].block0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const LbmMember<S> &m = members[lo];
+  const int k0 = ((int)blockIdx.x - m.block0) * kLbmBatchBlock + threadIdx.x;
+  if (k0 >= m.n) return;
+  if constexpr (MODE == M_SPLIT)
+    lbm_split_body<DIM, ODD, TAU1>((float *)m.g, m.glo, m.lg, m.n, k0, c);
+  else
+    lbm_body<S, DIM, ODD>(m.g, m.lg, m.n, k0, omega, fx_half, fsrc);
 }
 
 // Velocity u = j = sum e_i g_i + F/2 from the natural layout, written to
@@ -719,9 +765,10 @@ cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
 }
 
 template <int M, int DIM>
-cdi_status launch_velocity(cdi_domain *d) {
+cdi_status launch_velocity(cdi_domain *d, cudaStream_t st = nullptr) {
   using T = typename ModeT<M>::T;
-  k_flow_velocity<T, DIM><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+  if (!st) st = d->stream;
+  k_flow_velocity<T, DIM><<<kRedBlocks, kRedThreads, 0, st>>>(
       (const T *)d->d_g, M == M_SPLIT ? d->d_glo : nullptr, d->d_flow_list,
       (int)d->n_flow_pore, d->d_uflow, d->Nf, 0.5 * d->force, d->d_part, d->d_counter + C_RES,
       d->d_scal);
@@ -801,6 +848,157 @@ cdi_status flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps_out,
   return CDI_OK;
 }
 
+// Batched solve: every active member advances in one launch per step (K
+// steps per captured graph on the lead's stream); after each block of K
+// steps each member's residual is taken exactly as in its own solve, and a
+// member that has converged leaves the batch (its populations then stay as
+// its own solve would leave them).
+template <int M, int DIM>
+cdi_status flow_batch(cdi_domain *const *doms, int n_doms, const cdi_flow_params *p,
+                      int64_t *steps_out, double *res_out, int *status_out) {
+  using S = typename ModeT<M>::T;
+  using A = typename Arith<S>::type;
+  cdi_domain *L = doms[0];
+  const int K = p->check_every;
+  const int Q = Lat<DIM>::Q;
+  const double tau = p->tau, force = p->force_lu;
+  const A omega = A(1.0 / tau), fxh = A(0.5 * force), fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
+  const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
+  const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
+                     host_pair(fs * Lat<DIM>::w(1)),
+                     host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
+  LbmMember<S> *dtab = (LbmMember<S> *)cdi_dev_alloc(L, sizeof(LbmMember<S>) * n_doms);
+  if (!dtab) return cdi_fail(L, CDI_ERR_OOM, "flow batch: member table");
+  std::vector<LbmMember<S>> tab;
+  std::vector<int> active(n_doms);
+  cdi_status s = CDI_OK;
+  for (int i = 0; i < n_doms; i++) {
+    cdi_domain *d = doms[i];
+    active[i] = i;
+    steps_out[i] = 0;
+    res_out[i] = NAN;
+    status_out[i] = CDI_ERR_NOT_CONVERGED;
+    d->tau = tau;
+    d->force = force;
+    if (!d->lbm_tuned) {  // the single solve's block size: kept for later solves
+      s = tune_lbm<M, DIM>(d, tau, force);
+      if (s != CDI_OK) break;
+    }
+  }
+  auto chk = [&](cudaError_t e, const char *what) {
+    if (s == CDI_OK && e != cudaSuccess) s = cdi_cuda_fail(L, e, what);
+  };
+  // start from rest on the lead's stream (each domain's memory is ready:
+  // domains synchronise their streams when created)
+  for (int i = 0; i < n_doms && s == CDI_OK; i++) {
+    cdi_domain *d = doms[i];
+    chk(cudaStreamSynchronize(d->stream), "flow batch: member stream");
+    const size_t nq = (size_t)Q * d->n_flow_pore;
+    chk(cudaMemsetAsync(d->d_g, 0, nq * sizeof(S), L->stream), "flow batch: reset");
+    if (M == M_SPLIT) chk(cudaMemsetAsync(d->d_glo, 0, nq * 4, L->stream), "flow batch: reset");
+    if (s == CDI_OK) s = launch_velocity<M, DIM>(d, L->stream);
+  }
+  cudaGraphExec_t exec = nullptr;
+  auto rebuild = [&]() {
+    tab.clear();
+    int blocks = 0;
+    for (int i : active) {
+      cdi_domain *d = doms[i];
+      LbmMember<S> m;
+      m.g = (S *)d->d_g;
+      m.glo = d->d_glo;
+      m.lg = LinkGeo{d->d_lf, d->d_lr, d->d_lovf, d->n_lovf};
+      m.n = (int)d->n_flow_pore;
+      m.block0 = blocks;
+      blocks += (m.n + kLbmBatchBlock - 1) / kLbmBatchBlock;
+      tab.push_back(m);
+    }
+    chk(cudaMemcpyAsync(dtab, tab.data(), sizeof(LbmMember<S>) * tab.size(),
+                        cudaMemcpyHostToDevice, L->stream), "flow batch: member table");
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    if (s != CDI_OK) return;
+    cudaGraph_t graph;
+    chk(cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+    if (s != CDI_OK) return;
+    const int nm = (int)tab.size();
+    for (int k = 0; k < K / 2; k++) {
+      const bool t1 = M == M_SPLIT && tau == 1.0;
+      if (t1) {
+        k_lbm_batch<S, DIM, false, M, true><<<blocks, kLbmBatchBlock, 0, L->cap_stream>>>(
+            dtab, nm, omega, fxh, fsrc, c);
+        k_lbm_batch<S, DIM, true, M, true><<<blocks, kLbmBatchBlock, 0, L->cap_stream>>>(
+            dtab, nm, omega, fxh, fsrc, c);
+      } else {
+        k_lbm_batch<S, DIM, false, M, false><<<blocks, kLbmBatchBlock, 0, L->cap_stream>>>(
+            dtab, nm, omega, fxh, fsrc, c);
+        k_lbm_batch<S, DIM, true, M, false><<<blocks, kLbmBatchBlock, 0, L->cap_stream>>>(
+            dtab, nm, omega, fxh, fsrc, c);
+      }
+    }
+    cudaError_t e = cudaStreamEndCapture(L->cap_stream, &graph);
+    chk(e, "end capture");
+    if (e == cudaSuccess) {
+      chk(cudaGraphInstantiate(&exec, graph, 0), "instantiate flow batch graph");
+      cudaGraphDestroy(graph);
+    }
+  };
+  if (s == CDI_OK && p->max_steps > 0) rebuild();
+  int64_t steps = 0;
+  while (s == CDI_OK && !active.empty() && steps < p->max_steps) {
+    cudaEvent_t a;
+    cdi_timing_begin(L, &a);
+    chk(cudaGraphLaunch(exec, L->stream), "flow batch graph");
+    cdi_timing_end(L, a, PH_FLOW, K);
+    L->timing.kernel_launches += K;
+    steps += K;
+    cdi_timing_begin(L, &a);
+    for (int i : active) {
+      cdi_domain *d = doms[i];
+      if (s == CDI_OK) s = launch_velocity<M, DIM>(d, L->stream);
+      chk(cudaMemcpyAsync(d->h_scal + S_RES_NUM, d->d_scal + S_RES_NUM, 3 * sizeof(double),
+                          cudaMemcpyDeviceToHost, L->stream), "residual copy");
+    }
+    cdi_timing_end(L, a, PH_CHECK, (int64_t)active.size());
+    chk(cudaStreamSynchronize(L->stream), "flow batch chunk");
+    if (s != CDI_OK) break;
+    std::vector<int> still;
+    for (int i : active) {
+      const double r = doms[i]->h_scal[S_RES];
+      steps_out[i] = steps;
+      res_out[i] = r;
+      if (!std::isfinite(r)) {
+        status_out[i] = CDI_ERR_CUDA;   // diverged: leaves the batch
+      } else if (p->tol > 0.0 && r < p->tol) {
+        status_out[i] = CDI_OK;
+      } else {
+        still.push_back(i);
+      }
+    }
+    if (still.size() != active.size()) {
+      active = still;
+      if (!active.empty()) rebuild();
+    }
+  }
+  if (p->tol <= 0.0)
+    for (int i = 0; i < n_doms; i++)
+      if (status_out[i] == CDI_ERR_NOT_CONVERGED) status_out[i] = CDI_OK;
+  if (p->max_steps == 0)
+    for (int i = 0; i < n_doms; i++) res_out[i] = doms[i]->h_scal[S_RES];
+  cudaStreamSynchronize(L->stream);
+  if (exec) cudaGraphExecDestroy(exec);
+  cdi_dev_release(L, dtab);
+  if (s == CDI_OK) {
+    cudaError_t e = cdi_timing_resolve(L);
+    if (e != cudaSuccess) s = cdi_cuda_fail(L, e, "timing");
+  }
+  for (int i = 0; i < n_doms; i++) {
+    doms[i]->flow_steps = steps_out[i];
+    doms[i]->flow_residual = res_out[i];
+  }
+  return s;
+}
+
 template <typename T, int DIM>
 cdi_status flow_export(cdi_domain *d, double U_target) {
   k_flow_mean<<<kRedBlocks, kRedThreads, 0, d->stream>>>(
@@ -876,6 +1074,26 @@ cdi_status cdi_flow_run(cdi_domain *d, const cdi_flow_params *p, int64_t *steps,
     default:
       return d->dim == 2 ? flow_run<M_SPLIT, 2>(d, p, steps, res)
                          : flow_run<M_SPLIT, 3>(d, p, steps, res);
+  }
+}
+
+cdi_status cdi_flow_batch(cdi_domain *const *doms, int n_doms, const cdi_flow_params *p,
+                          int64_t *steps, double *res, int *status) {
+  const cdi_domain *d = doms[0];
+  switch (d->prec) {
+    case CDI_FP64:
+      return d->dim == 2 ? flow_batch<M_F64, 2>(doms, n_doms, p, steps, res, status)
+                         : flow_batch<M_F64, 3>(doms, n_doms, p, steps, res, status);
+    case CDI_FP32:
+    case CDI_FP32_CPAIR:
+      return d->dim == 2 ? flow_batch<M_F32, 2>(doms, n_doms, p, steps, res, status)
+                         : flow_batch<M_F32, 3>(doms, n_doms, p, steps, res, status);
+    case CDI_BF16_POP:
+      return d->dim == 2 ? flow_batch<M_BF16, 2>(doms, n_doms, p, steps, res, status)
+                         : flow_batch<M_BF16, 3>(doms, n_doms, p, steps, res, status);
+    default:
+      return d->dim == 2 ? flow_batch<M_SPLIT, 2>(doms, n_doms, p, steps, res, status)
+                         : flow_batch<M_SPLIT, 3>(doms, n_doms, p, steps, res, status);
   }
 }
 

@@ -142,6 +142,7 @@ cdi_status cdi_load_state(cdi_domain *d, const void *host_buf, size_t bytes) {
   CDI_TRY(d, cudaStreamSynchronize(d->stream), "load_state");
   if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
   d->np_graph = nullptr;
+  d->imp_stale = true;
   d->flow_done = h.flow_done != 0;
   d->psi_done = h.psi_done != 0;
   d->np_ready = h.np_ready != 0;

@@ -1155,6 +1155,7 @@ cdi_status cdi_np_build_flags(cdi_domain *d) {
 cdi_status cdi_np_init(cdi_domain *d, double dt_s, double *dt_used) {
   if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
   d->np_graph = nullptr;
+  d->imp_stale = true;  // the implicit operator follows u, phi and the species
   double dt = dt_s;
   if (dt <= 0.0) {
     cdi_status s = cdi_np_dt(d, d->h_scal[S_SCALE], &dt);
@@ -1432,7 +1433,11 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
   void *dmem = ok ? take(sizeof(BatchMember<T>) * n) : nullptr;
   cdi_status s = CDI_OK;
   if (!ok || !dmem) s = cdi_fail(L, CDI_ERR_OOM, "batch: device allocation failed");
-  // member velocities on their domains' streams, then everything on the lead's
+  // member velocities on their domains' streams (after the lead's stream
+  // has made the members' memory available: stream-ordered allocations),
+  // then everything on the lead's
+  if (s == CDI_OK && cudaStreamSynchronize(L->stream) != cudaSuccess)
+    s = cdi_fail(L, CDI_ERR_CUDA, "batch: member memory");
   for (int m = 0; m < n && s == CDI_OK; m++)
     s = cdi_flow_scale_to(doms[m / n_combos], scale[m], (void *)hm[m].s.u);
   for (int i = 0; i < n_doms && s == CDI_OK; i++)
@@ -1551,6 +1556,13 @@ static cdi_status np_steps_coupled(cdi_domain *d, int64_t n) {
       if (s != CDI_OK) return s;
     }
     const int64_t block = std::min<int64_t>(n, K - d->np_steps % K);
+    if (d->imp_tol > 0.0) {  // implicit steps in the re-solved potential
+      d->imp_stale = true;
+      cdi_status s = cdi_imp_steps(d, block);
+      if (s != CDI_OK) return s;
+      n -= block;
+      continue;
+    }
     cudaEvent_t ev;
     cdi_timing_begin(d, &ev);
     for (int64_t k = 0; k < block; k++) {
@@ -1569,6 +1581,7 @@ static cdi_status np_steps_coupled(cdi_domain *d, int64_t n) {
 cdi_status cdi_np_steps(cdi_domain *d, int64_t n) {
   if (n == 0) return CDI_OK;
   if (d->couple_K > 0) return np_steps_coupled(d, n);
+  if (d->imp_tol > 0.0) return cdi_imp_steps(d, n);
   cudaEvent_t ev;
   cdi_timing_begin(d, &ev);
   int64_t left = n;

@@ -2,9 +2,11 @@
 
 Requests (one electrode image plus potential, velocity and step counts each)
 arrive at any time.  A request is admitted as soon as a slot is free and its
-device footprint fits into the remaining memory budget; admitted requests
-run concurrently, each on its own domain with its own CUDA stream, so their
-kernels overlap on the device while earlier ones are still running.  Fields
+device footprint fits into the remaining memory budget (first fit in arrival
+order, with an ageing bound so that large requests are not passed over for
+ever); admitted requests run concurrently, each on its own domain with its
+own CUDA stream, so their kernels overlap on the device while earlier ones
+are still running.  Fields
 stay resident in device memory for the whole solve; the domain (and its
 memory) is released when the request completes, which admits the next.
 
@@ -17,7 +19,6 @@ library's kernels.
 """
 from __future__ import annotations
 
-import queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -76,15 +77,24 @@ def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> in
 
 
 class Server:
-    """Admits requests while slots and memory allow; runs them concurrently."""
+    """Admits requests while slots and memory allow; runs them concurrently.
+
+    Admission is first-fit in arrival order: the oldest waiting request that
+    fits the free slots and memory is started, so small requests need not
+    queue behind a large one that does not fit yet.  To keep a large request
+    from waiting for ever, a waiting request that has been passed over
+    ``max_bypass`` times is served next: nothing younger is admitted until it
+    fits."""
 
     def __init__(self, slots: int = 4, memory_budget: int = 16 << 30, device: int = 0,
-                 solver=None):
+                 solver=None, max_bypass: int | None = None):
         self.solver = solver or solve
         self.slots = slots
         self.budget = memory_budget
         self.device = device
-        self.pending: queue.Queue = queue.Queue()
+        self.max_bypass = 2 * slots if max_bypass is None else max_bypass
+        self._waiting: list = []
+        self._closing = False
         self.done: list = []
         self._lock = threading.Condition()
         self._in_use = 0
@@ -96,23 +106,42 @@ class Server:
 
     def submit(self, req: Request) -> None:
         req.t_arrival = time.perf_counter()
-        self.pending.put(req)
+        need = footprint_bytes(req.mask, req.precision)
+        with self._lock:
+            self._waiting.append((req, need, [0]))
+            self._lock.notify_all()
+
+    def _pick(self):
+        """Index of the request to start now, or None (lock held)."""
+        if self._running >= self.slots:
+            return None
+        for i, (req, need, passed) in enumerate(self._waiting):
+            if self._in_use + need <= self.budget:
+                return i
+            if passed[0] >= self.max_bypass:
+                return None        # this one is due: hold the others back
+        return None
 
     def _admit_loop(self):
         while True:
-            req = self.pending.get()
-            if req is None:
-                return
-            need = footprint_bytes(req.mask, req.precision)
             with self._lock:
-                if need > self.budget:
+                # requests larger than the whole budget fail at once
+                for item in [w for w in self._waiting if w[1] > self.budget]:
+                    req, need, _ = item
                     req.error = f"request needs {need} bytes, budget {self.budget}"
                     req.t_done = time.perf_counter()
                     self.done.append(req)
+                    self._waiting.remove(item)
                     self._lock.notify_all()
+                i = self._pick()
+                if i is None:
+                    if self._closing and not self._waiting:
+                        return
+                    self._lock.wait(timeout=0.5)
                     continue
-                while self._running >= self.slots or self._in_use + need > self.budget:
-                    self._lock.wait()
+                req, need, _ = self._waiting.pop(i)
+                for _, _, passed in self._waiting[:i]:
+                    passed[0] += 1
                 self._running += 1
                 self._in_use += need
                 self.max_running = max(self.max_running, self._running)
@@ -149,7 +178,9 @@ class Server:
             return list(self.done)
 
     def close(self):
-        self.pending.put(None)
+        with self._lock:
+            self._closing = True
+            self._lock.notify_all()
         self._admitter.join(timeout=10)
 
 

@@ -115,3 +115,56 @@ def test_batch_argument_errors():
         with pytest.raises(cdi.CDIError) as e:       # the same domain twice
             cdi.batch([a, a], COMBOS[:1], n_steps=1)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec,dim", [(cdi.FP64, 2), (cdi.FP32_SPLIT, 2), (cdi.FP32, 3),
+                                      (cdi.FP32_CPAIR, 3)])
+def test_flow_batch_members_equal_single_solves(prec, dim):
+    """cdi_solve_flow_batch: uneven geometries advance in one launch per
+    step and leave the batch at their own first converged check; each
+    member's step count, residual and velocity field equal its own
+    cdi_solve_flow bit for bit."""
+    shapes = [(23, 37), (31, 45), (17, 70)] if dim == 2 else [(9, 11, 17), (7, 13, 21)]
+    masks = [inputs.grain_pack(s, 0.6, 1.5, 4.0, seed=50 + i)[0] for i, s in enumerate(shapes)]
+    tol = 1e-7
+    single = []
+    for m in masks:
+        with cdi.Domain(m, precision=prec) as d:
+            st, r, _ = d.solve_flow(tol=tol, max_steps=200_000, U_target=1e-4)
+            single.append((st, r, d.u_lattice(), d.u()))
+    doms = [cdi.Domain(m, precision=prec) for m in masks]
+    try:
+        steps, res, status = cdi.flow_batch(doms, tol=tol, max_steps=200_000, U_target=1e-4)
+        assert list(status) == [0] * len(doms)
+        assert len(set(steps)) > 1          # the members stop at different checks
+        for i, d in enumerate(doms):
+            assert steps[i] == single[i][0]
+            assert res[i] == single[i][1]
+            assert np.array_equal(d.u_lattice(), single[i][2])
+            assert np.array_equal(d.u(), single[i][3])
+        # the transport that follows runs on the batched flows
+        g_b, c_b, _ = cdi.batch(doms, COMBOS[:2], n_steps=40)
+        assert np.all(np.isfinite(g_b)) and np.all(g_b > 0)
+    finally:
+        for d in doms:
+            d.close()
+
+
+def test_flow_batch_limits_and_errors():
+    m, _ = inputs.grain_pack((23, 37), 0.6, 1.5, 4.0, seed=21)
+    m3, _ = inputs.grain_pack((9, 11, 17), 0.6, 1.5, 4.0, seed=21)
+    with cdi.Domain(m) as a, cdi.Domain(m) as b, cdi.Domain(m3) as c:
+        with pytest.raises(cdi.CDIError) as e:       # mixed dimensions
+            cdi.flow_batch([a, c], max_steps=100)
+        assert e.value.status == 1
+        with pytest.raises(cdi.CDIError) as e:       # the same domain twice
+            cdi.flow_batch([a, a], max_steps=100)
+        assert e.value.status == 1
+        steps, res, st = cdi.flow_batch([a, b], tol=1e-30, max_steps=300,
+                                        allow_not_converged=True)
+        assert list(steps) == [300, 300] and list(st) == [4, 4]
+        steps, res, st = cdi.flow_batch([a, b], tol=0.0, max_steps=200)
+        assert list(steps) == [200, 200] and list(st) == [0, 0]
+        a.set_potential(1.0)
+        a.init_transport()
+        a.step(5)

@@ -86,9 +86,70 @@ def test_results_same_alone_and_in_the_mix():
 
     alone = [serve.solve(r) for r in make()]
     reqs = make()
+    # a bad request in the mix (no pore cell in the inlet column) fails alone
+    bad = masks[0].copy()
+    bad[:, 0] = 1
+    reqs.insert(2, serve.Request(bad, 1.0, 1e-4, 300, tag="bad"))
     done = serve.run_served(reqs, [0.0] * len(reqs), slots=4, memory_budget=8 << 30)
-    assert all(not r.error for r in done)
+    by = {r.tag: r for r in done}
+    assert "inlet" in by["bad"].error
+    assert all(not r.error for r in done if r.tag != "bad")
     for r in done:
+        if r.tag == "bad":
+            continue
         a = alone[r.tag]
         assert np.array_equal(r.result["Gamma"], a["Gamma"])
         assert np.array_equal(r.result["C_out"], a["C_out"])
+
+
+@pytest.mark.gpu
+def test_served_result_matches_the_oracle():
+    """One request served in a mix, in FP64 storage, against the oracle's
+    run of the same request (flow, potential, transport, outputs)."""
+    import __graft_entry__ as g
+    import oracle as O
+    g.build()
+    m = inputs.grain_pack((24, 40), 0.6, 2.0, 4.0, seed=35)[0]
+    other = inputs.grain_pack((10, 12, 16), 0.55, 1.5, 3.0, seed=36)[0]
+    reqs = [serve.Request(m, 0.8, 1e-4, 400, precision=cdi.FP64, flow_tol=1e-8, tag=0),
+            serve.Request(other, 1.2, 1e-6, 400, flow_tol=1e-7, max_flow_steps=20000, tag=1)]
+    done = serve.run_served(reqs, [0.0, 0.0], slots=2, memory_budget=8 << 30)
+    r = {q.tag: q for q in done}[0]
+    assert not r.error
+    o = O.run_case(m, flow_tol=1e-8, U_target=1e-4, applied_V=0.8, c0=10.0, psi_tol=1e-12,
+                   n_np_steps=400)
+    assert r.result["flow_steps"] == o["flow_steps"]
+    np.testing.assert_allclose(r.result["Gamma"], o["Gamma"], rtol=1e-10)
+    np.testing.assert_allclose(r.result["C_out"], o["C_out"], rtol=1e-10)
+
+
+def test_first_fit_admission_and_ageing():
+    """A small request that arrives behind a large one that does not fit yet
+    starts first; a large request passed over max_bypass times is served
+    next, before any younger small one."""
+    log, lock = [], threading.Lock()
+    small = np.zeros((64, 64), np.uint8)
+    big = np.zeros((512, 512), np.uint8)
+    ns, nb = serve.footprint_bytes(small, cdi.FP32), serve.footprint_bytes(big, cdi.FP32)
+    assert nb > 2 * ns
+
+    def solver(req):
+        time.sleep(0.15 if req.tag == "big" else 0.05)
+        with lock:
+            log.append(req.tag)
+        return {}
+
+    srv = serve.Server(slots=2, memory_budget=nb, solver=solver, max_bypass=2)
+    reqs = [serve.Request(small, 1.0, 1e-4, 1, tag="s0"),
+            serve.Request(big, 1.0, 1e-4, 1, tag="big")]
+    reqs += [serve.Request(small, 1.0, 1e-4, 1, tag=f"s{i}") for i in range(1, 6)]
+    for r in reqs:
+        srv.submit(r)
+    done = srv.drain(len(reqs), timeout=60)
+    srv.close()
+    t = {r.tag: r.t_start for r in done}
+    assert not any(r.error for r in done)
+    assert t["s1"] < t["big"]                    # first fit: s1 did not wait for big
+    passed = [k for k in ("s1", "s2", "s3", "s4", "s5") if t[k] < t["big"]]
+    assert len(passed) <= 3                      # ageing: big is not passed over for ever
+    assert max(t.values()) > t["big"]
