@@ -205,25 +205,62 @@ struct LinkGeo {
   int n_ovf;
 };
 
+// Where direction i of pore rank k lives: plane i of the population array
+// (plane i = direction i of every pore rank).  Planes<S, Q> passes the Q
+// plane base pointers by value, so a kernel reads them from its parameter
+// space and an address is one 32-bit-index multiply-add; Strided forms them
+// from the array base and the plane length (used where one launch serves
+// several domains).
+template <typename S, int Q> struct Planes {
+  S *p[Q];
+  __device__ __forceinline__ S *plane(int i) const { return p[i]; }
+};
+template <typename S> struct Strided {
+  S *g;
+  long long n;
+  __device__ __forceinline__ S *plane(int i) const { return g + (size_t)i * n; }
+};
+template <typename S, int Q> Planes<S, Q> make_planes(S *g, long long n) {
+  Planes<S, Q> pl;
+  for (int i = 0; i < Q; i++) pl.p[i] = g + (size_t)i * n;
+  return pl;
+}
+
 // Slot read by direction i at rank k (ODD: the upstream neighbour's opposite
 // slot, or the own slot after a bounce-back), and slot written by the
 // post-collision value of direction i.  nb[j] caches the neighbour rank of
-// direction j (-1: bounce-back).
+// direction j (-1: bounce-back).  Returned as (plane, index in the plane).
 template <int DIM, bool ODD>
-__device__ __forceinline__ size_t read_slot(const int *nb, int k, int i, long long n) {
+__device__ __forceinline__ int read_slot(const int *nb, int k, int i, int &idx) {
   using L = Lat<DIM>;
-  if (!ODD || i == 0) return (size_t)i * n + k;
+  idx = k;
+  if (!ODD || i == 0) return i;
   const int src = nb[L::opp(i)];  // the site x - e_i
-  if (src < 0) return (size_t)i * n + k;  // upstream solid: the bounced value
-  return (size_t)L::opp(i) * n + src;
+  if (src < 0) return i;          // upstream solid: the bounced value
+  idx = src;
+  return L::opp(i);
 }
 template <int DIM, bool ODD>
-__device__ __forceinline__ size_t write_slot(const int *nb, int k, int i, long long n) {
+__device__ __forceinline__ int write_slot(const int *nb, int k, int i, int &idx) {
   using L = Lat<DIM>;
-  if (!ODD || i == 0) return (size_t)L::opp(i) * n + k;
-  const int dst = nb[i];  // the site x + e_i
-  if (dst < 0) return (size_t)L::opp(i) * n + k;  // bounce back from a solid
-  return (size_t)i * n + dst;
+  idx = k;
+  if (!ODD || i == 0) return L::opp(i);
+  const int dst = nb[i];          // the site x + e_i
+  if (dst < 0) return L::opp(i);  // bounce back from a solid
+  idx = dst;
+  return i;
+}
+// The address of a slot: the two candidate planes are compile-time indices,
+// so only the base pointer and the index are selected at run time.
+template <int DIM, bool ODD, bool READ, typename PL>
+__device__ __forceinline__ auto slot_ptr(const PL &pl, const int *nb, int k, int i) {
+  using L = Lat<DIM>;
+  if (!ODD || i == 0) return pl.plane(READ ? i : L::opp(i)) + k;
+  const int q = READ ? nb[L::opp(i)] : nb[i];
+  const bool bounce = q < 0;
+  auto *own = pl.plane(READ ? i : L::opp(i));
+  auto *other = pl.plane(READ ? L::opp(i) : i);
+  return (bounce ? own : other) + (bounce ? k : q);
 }
 
 // Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
@@ -316,8 +353,8 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 // (more resident blocks per SM: the step is latency-bound on its scattered
 // loads, so occupancy matters more than a few spare registers; the bound is
 // chosen per variant so that nothing spills)
-template <typename S, int DIM, bool ODD>
-__device__ __forceinline__ void lbm_body(S *__restrict__ g, const LinkGeo &lg, int n, int k0,
+template <typename S, int DIM, bool ODD, typename PL>
+__device__ __forceinline__ void lbm_body(const PL &g, const LinkGeo &lg, int n, int k0,
                                          typename Arith<S>::type omega,
                                          typename Arith<S>::type fx_half,
                                          typename Arith<S>::type fsrc) {
@@ -328,7 +365,7 @@ __device__ __forceinline__ void lbm_body(S *__restrict__ g, const LinkGeo &lg, i
   load_links<DIM, ODD>(lg, k0, n, nb);
   T gi[Q];
 #pragma unroll
-  for (int i = 0; i < Q; i++) gi[i] = widen(g[read_slot<DIM, ODD>(nb, k0, i, n)]);
+  for (int i = 0; i < Q; i++) gi[i] = widen(*slot_ptr<DIM, ODD, true>(g, nb, k0, i));
   T drho = T(0), jx = fx_half, jy = T(0), jz = T(0);
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -358,12 +395,12 @@ __device__ __forceinline__ void lbm_body(S *__restrict__ g, const LinkGeo &lg, i
     go[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
   }
 #pragma unroll
-  for (int i = 0; i < Q; i++) g[write_slot<DIM, ODD>(nb, k0, i, n)] = narrow<S>(go[i]);
+  for (int i = 0; i < Q; i++) *slot_ptr<DIM, ODD, false>(g, nb, k0, i) = narrow<S>(go[i]);
 }
 
 template <typename S, int DIM, bool ODD, int BS, int MINT>
 __global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128) / BS)
-    k_lbm_step(S *__restrict__ g, LinkGeo lg, int n,
+    k_lbm_step(Planes<S, Lat<DIM>::Q> g, LinkGeo lg, int n,
                typename Arith<S>::type omega, typename Arith<S>::type fx_half,
                typename Arith<S>::type fsrc) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,10 +419,9 @@ struct SplitConst {
 
 // The same step with every population stored as an FP32 pair gh + gl and the
 // collision carried out in pair arithmetic.
-template <int DIM, bool ODD, bool TAU1>
-__device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__restrict__ gl,
-                                               const LinkGeo &lg, int n, int k0,
-                                               const SplitConst &c) {
+template <int DIM, bool ODD, bool TAU1, typename PL>
+__device__ __forceinline__ void lbm_split_body(const PL &gh, const PL &gl, const LinkGeo &lg,
+                                               int n, int k0, const SplitConst &c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   // lattice weights as FP32 pairs: rest, axis, diagonal
@@ -398,8 +434,9 @@ __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    const size_t a = read_slot<DIM, ODD>(nb, k0, i, n);
-    gi[i] = {gh[a], gl[a]};
+    int idx;
+    const int pl = read_slot<DIM, ODD>(nb, k0, i, idx);
+    gi[i] = {gh.plane(pl)[idx], gl.plane(pl)[idx]};
   }
   // moments as pairs: exact sums of the high parts plus the low parts
   float rs = 0.f, rc = 0.f, xs = 0.f, xc = 0.f, ys = 0.f, yc = 0.f, zs = 0.f, zc = 0.f;
@@ -450,17 +487,18 @@ __device__ __forceinline__ void lbm_split_body(float *__restrict__ gh, float *__
       const F2 sv = axis ? c.src_axis : c.src_diag;
       go = f2_add(go, L::ex(i) > 0 ? sv : f2_neg(sv));
     }
-    const size_t a = write_slot<DIM, ODD>(nb, k0, i, n);
-    gh[a] = go.h;
-    gl[a] = go.l;
+    int idx;
+    const int pl = write_slot<DIM, ODD>(nb, k0, i, idx);
+    gh.plane(pl)[idx] = go.h;
+    gl.plane(pl)[idx] = go.l;
   }
 }
 
 // BS threads per block, registers as the compiler sees fit.
 template <int DIM, bool ODD, bool TAU1, int BS>
 __global__ void __launch_bounds__(BS)
-    k_lbm_step_split(float *__restrict__ gh, float *__restrict__ gl, LinkGeo lg, int n,
-                     SplitConst c) {
+    k_lbm_step_split(Planes<float, Lat<DIM>::Q> gh, Planes<float, Lat<DIM>::Q> gl, LinkGeo lg,
+                     int n, SplitConst c) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, k0, c);
@@ -469,8 +507,8 @@ __global__ void __launch_bounds__(BS)
 // The same step with registers capped so that MINT threads share an SM.
 template <int DIM, bool ODD, bool TAU1, int BS, int MINT>
 __global__ void __launch_bounds__(BS, MINT / BS)
-    k_lbm_step_split_occ(float *__restrict__ gh, float *__restrict__ gl, LinkGeo lg, int n,
-                         SplitConst c) {
+    k_lbm_step_split_occ(Planes<float, Lat<DIM>::Q> gh, Planes<float, Lat<DIM>::Q> gl,
+                         LinkGeo lg, int n, SplitConst c) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n) return;
   lbm_split_body<DIM, ODD, TAU1>(gh, gl, lg, n, k0, c);
@@ -506,9 +544,10 @@ __global__ void __launch_bounds__(kLbmBatchBlock)
   const int k0 = ((int)blockIdx.x - m.block0) * kLbmBatchBlock + threadIdx.x;
   if (k0 >= m.n) return;
   if constexpr (MODE == M_SPLIT)
-    lbm_split_body<DIM, ODD, TAU1>((float *)m.g, m.glo, m.lg, m.n, k0, c);
+    lbm_split_body<DIM, ODD, TAU1>(Strided<float>{(float *)m.g, m.n},
+                                   Strided<float>{m.glo, m.n}, m.lg, m.n, k0, c);
   else
-    lbm_body<S, DIM, ODD>(m.g, m.lg, m.n, k0, omega, fx_half, fsrc);
+    lbm_body<S, DIM, ODD>(Strided<S>{m.g, m.n}, m.lg, m.n, k0, omega, fx_half, fsrc);
 }
 
 // Velocity u = j = sum e_i g_i + F/2 from the natural layout, written to
@@ -660,36 +699,33 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
                        host_pair(fs * Lat<DIM>::w(1)),
                        host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
-    float *gh = (float *)d->d_g;
+    constexpr int Q = Lat<DIM>::Q;
+    const Planes<float, Q> gh = make_planes<float, Q>((float *)d->d_g, n);
+    const Planes<float, Q> gl = make_planes<float, Q>(d->d_glo, n);
     if constexpr (MINT == 0) {
       if (tau == 1.0) {
-        k_lbm_step_split<DIM, false, true, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
-        k_lbm_step_split<DIM, true, true, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
+        k_lbm_step_split<DIM, false, true, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+        k_lbm_step_split<DIM, true, true, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       } else {
-        k_lbm_step_split<DIM, false, false, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
-        k_lbm_step_split<DIM, true, false, BS><<<grid, BS, 0, st>>>(gh, d->d_glo, lk, n, c);
+        k_lbm_step_split<DIM, false, false, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+        k_lbm_step_split<DIM, true, false, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       }
     } else {
       if (tau == 1.0) {
-        k_lbm_step_split_occ<DIM, false, true, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
-                                                                              n, c);
-        k_lbm_step_split_occ<DIM, true, true, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
-                                                                             n, c);
+        k_lbm_step_split_occ<DIM, false, true, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+        k_lbm_step_split_occ<DIM, true, true, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       } else {
-        k_lbm_step_split_occ<DIM, false, false, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
-                                                                               n, c);
-        k_lbm_step_split_occ<DIM, true, false, BS, MINT><<<grid, BS, 0, st>>>(gh, d->d_glo, lk,
-                                                                              n, c);
+        k_lbm_step_split_occ<DIM, false, false, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+        k_lbm_step_split_occ<DIM, true, false, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       }
     }
   } else {
     using A = typename Arith<T>::type;
     const A omega = A(1.0 / tau), fxh = A(0.5 * force);
     const A fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
-    k_lbm_step<T, DIM, false, BS, MINT><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh,
-                                                              fsrc);
-    k_lbm_step<T, DIM, true, BS, MINT><<<grid, BS, 0, st>>>((T *)d->d_g, lk, n, omega, fxh,
-                                                             fsrc);
+    const Planes<T, Lat<DIM>::Q> g = make_planes<T, Lat<DIM>::Q>((T *)d->d_g, n);
+    k_lbm_step<T, DIM, false, BS, MINT><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
+    k_lbm_step<T, DIM, true, BS, MINT><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
   }
 }
 

@@ -194,6 +194,22 @@ struct NPGeo {
 // with its sign flipped (one shuffle).  Every x face is then evaluated once
 // instead of twice, and every lane of the warp takes the same path.
 constexpr int kHome = 31;
+
+// The fields of one FP32 transport state as per-species / per-component
+// plane pointers: by value as kernel parameters (one launch, one state) or
+// in a member table (fused sweeps and batches), so that every access is a
+// base pointer plus a 32-bit rank.
+struct NPFields {
+  const float *C[kMaxSpecies];   // concentrations read (hi words)
+  const float *Cl[kMaxSpecies];  // their low words (pair storage), else null
+  float *Co[kMaxSpecies];        // concentrations written
+  float *Col[kMaxSpecies];       // their low words
+  const float *u[3];             // velocity components
+  const int *lat[4];             // lateral neighbour ranks (y+, y-, z+, z-)
+  const float2 *phi;             // psi / V_T as (hi, lo)
+  const NFlag *fl;               // face flags
+  float2 *acc;                   // per-warp accounts
+};
 __host__ __device__ constexpr long long np_warps(long long n) { return (n + kHome - 1) / kHome; }
 
 // One explicit step of the pore cell of rank r for NS species: writes the
@@ -423,29 +439,24 @@ __device__ __forceinline__ void ptwo_sum(float2 a, float2 b, float2 &s, float2 &
 // -x, +y, -y, +z, -z), so without PAIR a cell whose faces all take the
 // |P| < 1/2 branch gets the bits np_cell gives.
 template <int DIM, int NS, bool PAIR>
-__device__ __forceinline__ void np_warp31(const float *__restrict__ Cin, float *__restrict__ Cout,
-                                          const float *__restrict__ Cinl,
-                                          float *__restrict__ Coutl, const float *__restrict__ u,
-                                          const float2 *__restrict__ phi, const NPGeo &g,
-                                          const NPConst<float> &c, float2 *__restrict__ acc,
-                                          int w) {
+__device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int naccs,
+                                          const NPConst<float> &c, int w) {
   constexpr int NF = 2 * DIM;
   constexpr int NP = (NS + 1) / 2;
   // second species of pair p (a copy of the first when NS is odd)
   auto K1 = [](int p) { return 2 * p + 1 < NS ? 2 * p + 1 : 2 * p; };
   const int lane = threadIdx.x & 31;
   const int r = kHome * w + lane - 1;
-  const bool valid = r >= 0 && r < g.n;
+  const bool valid = r >= 0 && r < n_cells;
   const bool home = valid && lane != 0;
-  const size_t n = (size_t)g.n;
-  auto ldC = [&](const float *A, int Q, int p) {
-    return make_float2(A[(size_t)(2 * p) * n + Q], A[(size_t)K1(p) * n + Q]);
+  auto ldC = [&](const float *const *A, int Q, int p) {
+    return make_float2(A[2 * p][Q], A[K1(p)][Q]);
   };
-  const unsigned f = valid ? (unsigned)g.fl[r] : 0u;
+  const unsigned f = valid ? (unsigned)F.fl[r] : 0u;
   // lateral neighbour ranks (-1 across a solid face or wall)
   int q[NF - 2];
 #pragma unroll
-  for (int j = 0; j < NF - 2; j++) q[j] = home ? g.lat[(size_t)j * n + r] : -1;
+  for (int j = 0; j < NF - 2; j++) q[j] = home ? F.lat[j][r] : -1;
   // own values
   const float2 z2 = make_float2(0.f, 0.f);
   float2 CP[NP], CPl[NP];
@@ -458,12 +469,12 @@ __device__ __forceinline__ void np_warp31(const float *__restrict__ Cin, float *
   if (valid) {
 #pragma unroll
     for (int p = 0; p < NP; p++) {
-      CP[p] = ldC(Cin, r, p);
-      if (PAIR) CPl[p] = ldC(Cinl, r, p);
+      CP[p] = ldC(F.C, r, p);
+      if (PAIR) CPl[p] = ldC(F.Cl, r, p);
     }
 #pragma unroll
-    for (int a = 0; a < DIM; a++) uP[a] = u[(size_t)a * n + r];
-    phP = phi[r];
+    for (int a = 0; a < DIM; a++) uP[a] = F.u[a][r];
+    phP = F.phi[r];
   }
   // lateral neighbours' values (a closed face reads the cell's own values,
   // for which the flux expression is exactly 0)
@@ -474,12 +485,12 @@ __device__ __forceinline__ void np_warp31(const float *__restrict__ Cin, float *
     const int fc = j + 2;
     if (q[j] >= 0) {
       const int Q = q[j];
-      ul[j] = u[(size_t)(fc >> 1) * n + Q];
-      phl[j] = phi[Q];
+      ul[j] = F.u[fc >> 1][Q];
+      phl[j] = F.phi[Q];
 #pragma unroll
       for (int p = 0; p < NP; p++) {
-        Cl[j][p] = ldC(Cin, Q, p);
-        Cll[j][p] = PAIR ? ldC(Cinl, Q, p) : z2;
+        Cl[j][p] = ldC(F.C, Q, p);
+        Cll[j][p] = PAIR ? ldC(F.Cl, Q, p) : z2;
       }
     } else {
       ul[j] = uP[fc >> 1];
@@ -511,12 +522,12 @@ __device__ __forceinline__ void np_warp31(const float *__restrict__ Cin, float *
     }
   }
   if (lane == 31 && xp) {  // rank r + 1 is the next warp's first home cell
-    ux = u[r + 1];
-    phx = phi[r + 1];
+    ux = F.u[0][r + 1];
+    phx = F.phi[r + 1];
 #pragma unroll
     for (int p = 0; p < NP; p++) {
-      Cx[p] = ldC(Cin, r + 1, p);
-      if (PAIR) Cxl[p] = ldC(Cinl, r + 1, p);
+      Cx[p] = ldC(F.C, r + 1, p);
+      if (PAIR) Cxl[p] = ldC(F.Cl, r + 1, p);
     }
   }
   if (!xp) {
@@ -600,16 +611,16 @@ __device__ __forceinline__ void np_warp31(const float *__restrict__ Cin, float *
         const float2 l = padd(CPl[p], e);
         Cn = padd(t, l);
         Cnl = psub(l, psub(Cn, t));
-        Coutl[(size_t)(2 * p) * n + r] = Cnl.x;
-        if (2 * p + 1 < NS) Coutl[(size_t)(2 * p + 1) * n + r] = Cnl.y;
+        F.Col[2 * p][r] = Cnl.x;
+        if (2 * p + 1 < NS) F.Col[2 * p + 1][r] = Cnl.y;
       } else {
         Cn = pfma(bc(-c.dtdx), sumJ[p], CP[p]);
       }
-      Cout[(size_t)(2 * p) * n + r] = Cn.x;
-      if (2 * p + 1 < NS) Cout[(size_t)(2 * p + 1) * n + r] = Cn.y;
+      F.Co[2 * p][r] = Cn.x;
+      if (2 * p + 1 < NS) F.Co[2 * p + 1][r] = Cn.y;
     }
   }
-  np_account_f32<NS>(v, home && (me || xe), acc, w, g.naccs);
+  np_account_f32<NS>(v, home && (me || xe), F.acc, w, naccs);
 }
 
 template <typename T, int DIM, int NS, bool PAIR>
@@ -619,18 +630,26 @@ __device__ __forceinline__ void np_step_body(const T *__restrict__ Cin, T *__res
                                              const typename PhiStore<T>::type *__restrict__ phi,
                                              const NPGeo &g, const NPConst<T> &c,
                                              typename AccSlot<T>::type *__restrict__ acc) {
-  if constexpr (std::is_same<T, float>::value) {
-    np_warp31<DIM, NS, PAIR>(Cin, Cout, Cinl, Coutl, u, phi, g, c, acc,
-                             (blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  } else {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    T v[3 * NS];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  T v[3 * NS];
 #pragma unroll
-    for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
-    bool io = false;
-    if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
-    np_account<T, NS>(v, io, acc, r >> 5, g.naccs);
-  }
+  for (int j = 0; j < 3 * NS; j++) v[j] = T(0);
+  bool io = false;
+  if (r < g.n) io = np_cell<T, DIM, NS>(Cin, Cout, u, phi, g, g.meta[r], r, c, v);
+  np_account<T, NS>(v, io, acc, r >> 5, g.naccs);
+}
+
+// FP32 storage: warps of 31 home cells (np_warp31), fields by plane pointer.
+template <int DIM, int NS, int BS, bool PAIR>
+__global__ void __launch_bounds__(BS)
+    k_np_step32(NPFields F, int n, int naccs, NPConst<float> c) {
+  np_warp31<DIM, NS, PAIR>(F, n, naccs, c, (blockIdx.x * BS + threadIdx.x) >> 5);
+}
+
+template <int DIM, int NS, int BS, int MINT, bool PAIR>
+__global__ void __launch_bounds__(BS, MINT / BS)
+    k_np_step32_occ(NPFields F, int n, int naccs, NPConst<float> c) {
+  np_warp31<DIM, NS, PAIR>(F, n, naccs, c, (blockIdx.x * BS + threadIdx.x) >> 5);
 }
 
 // BS threads per block, registers as the compiler sees fit.
@@ -660,6 +679,7 @@ __global__ void __launch_bounds__(BS, MINT / BS)
 template <typename T> struct SweepMember {
   T *C[2];          // concentration buffers (ping-pong)
   float *Cl[2];     // their low words (FP32 pair storage), else null
+  NPFields f[2];    // FP32: the fields as plane pointers, stepping from buffer 0 / 1
   const T *u;
   const typename PhiStore<T>::type *phi;
   typename AccSlot<T>::type *acc;
@@ -677,8 +697,7 @@ __global__ void __launch_bounds__(kRowBlock)
   if constexpr (std::is_same<T, float>::value) {
     for (int m = 0; m < n_members; m++) {
       const SweepMember<T> &mb = members[m];
-      np_warp31<DIM, NS, PAIR>(mb.C[in], mb.C[1 - in], mb.Cl[in], mb.Cl[1 - in], mb.u, mb.phi, g,
-                               mb.c, mb.acc, r >> 5);
+      np_warp31<DIM, NS, PAIR>(mb.f[in], g.n, g.naccs, mb.c, r >> 5);
     }
   } else {
     const uint2 meta = r < g.n ? g.meta[r] : make_uint2(1u, 0u);
@@ -722,8 +741,7 @@ __global__ void __launch_bounds__(kRowBlock)
   const int b = (int)blockIdx.x - mb.block0;
   const int r = b * blockDim.x + threadIdx.x;
   if constexpr (std::is_same<T, float>::value) {
-    np_warp31<DIM, NS, PAIR>(mb.s.C[in], mb.s.C[1 - in], mb.s.Cl[in], mb.s.Cl[1 - in], mb.s.u,
-                             mb.s.phi, mb.g, mb.s.c, mb.s.acc, r >> 5);
+    np_warp31<DIM, NS, PAIR>(mb.s.f[in], mb.g.n, mb.g.naccs, mb.s.c, r >> 5);
   } else {
     T v[3 * NS];
 #pragma unroll
@@ -1023,6 +1041,26 @@ template <typename T> NPConst<T> make_const(const cdi_domain *d) {
   return c;
 }
 
+// The FP32 fields of a transport state as plane pointers (stepping from
+// Cin/Cinl into Cout/Coutl).
+NPFields fields32(const cdi_domain *d, const void *Cin, const float *Cinl, void *Cout,
+                  float *Coutl, const void *u, const void *phi, void *acc) {
+  NPFields F{};
+  const size_t n = (size_t)d->n_pore;
+  for (int k = 0; k < kMaxSpecies; k++) {
+    F.C[k] = (const float *)Cin + (size_t)k * n;
+    F.Cl[k] = Cinl ? Cinl + (size_t)k * n : nullptr;
+    F.Co[k] = (float *)Cout + (size_t)k * n;
+    F.Col[k] = Coutl ? Coutl + (size_t)k * n : nullptr;
+  }
+  for (int a = 0; a < d->dim; a++) F.u[a] = (const float *)u + (size_t)a * n;
+  for (int j = 0; j < 2 * (d->dim - 1); j++) F.lat[j] = d->d_latnb + (size_t)j * n;
+  F.phi = (const float2 *)phi;
+  F.fl = d->d_cfl;
+  F.acc = (float2 *)acc;
+  return F;
+}
+
 NPGeo make_geo(const cdi_domain *d) {
   return NPGeo{d->d_cmeta, d->d_cfl, d->d_words, d->d_latnb, (int)d->n_pore, d->W, d->ny, d->nz,
                d->walls, d->np_accs};
@@ -1036,16 +1074,26 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   const int grid = (int)((units + BS - 1) / BS);
   const float *Cinl = PAIR ? d->d_Clo[in] : nullptr;
   float *Coutl = PAIR ? d->d_Clo[1 - in] : nullptr;
-  if constexpr (MINT == 0)
+  if constexpr (std::is_same<T, float>::value) {
+    const NPFields F = fields32(d, d->d_C[in], Cinl, d->d_C[1 - in], Coutl, d->d_u, d->d_phi,
+                                d->d_acc);
+    if constexpr (MINT == 0)
+      k_np_step32<DIM, NS, BS, PAIR><<<grid, BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
+                                                          make_const<float>(d));
+    else
+      k_np_step32_occ<DIM, NS, BS, MINT, PAIR><<<grid, BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
+                                                                    make_const<float>(d));
+  } else if constexpr (MINT == 0) {
     k_np_step<T, DIM, NS, BS, PAIR><<<grid, BS, 0, st>>>(
         (const T *)d->d_C[in], (T *)d->d_C[1 - in], Cinl, Coutl, (const T *)d->d_u,
         (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
         (typename AccSlot<T>::type *)d->d_acc);
-  else
+  } else {
     k_np_step_occ<T, DIM, NS, BS, MINT, PAIR><<<grid, BS, 0, st>>>(
         (const T *)d->d_C[in], (T *)d->d_C[1 - in], Cinl, Coutl, (const T *)d->d_u,
         (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
         (typename AccSlot<T>::type *)d->d_acc);
+  }
 }
 
 template <typename T, int DIM, int NS, bool PAIR>
@@ -1055,6 +1103,8 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 2: launch_step_bs<T, DIM, NS, 256, 0, PAIR>(d, st, in); break;
     case 3: launch_step_bs<T, DIM, NS, 64, 1280, PAIR>(d, st, in); break;
     case 4: launch_step_bs<T, DIM, NS, 128, 1280, PAIR>(d, st, in); break;
+    case 5: launch_step_bs<T, DIM, NS, 128, 1024, PAIR>(d, st, in); break;
+    case 6: launch_step_bs<T, DIM, NS, 256, 1024, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1086,14 +1136,14 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 
 // Autotuner: times a few transport steps with each candidate launch shape
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
-// for 1280 resident threads per SM) on the domain's stream and keeps the
-// fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// for 1280 resident threads per SM, for 128 and 256 one for 1024) on the
+// domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[5] = {64, 128, 256, 64, 128};
+constexpr int kNpVariantBlock[7] = {64, 128, 256, 64, 128, 128, 256};
 cdi_status tune_np(cdi_domain *d) {
-  static const int cand[] = {0, 1, 2, 3, 4};
+  static const int cand[] = {0, 1, 2, 3, 4, 5, 6};
   const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
@@ -1272,6 +1322,9 @@ cdi_status sweep_run(cdi_domain *d, int n, const double *scale, const int *group
     hm[m].C[1] = (T *)c1;
     hm[m].Cl[0] = (float *)l0;
     hm[m].Cl[1] = (float *)l1;
+    for (int in = 0; in < 2; in++)
+      hm[m].f[in] = fields32(d, in ? c1 : c0, in ? (float *)l1 : (float *)l0, in ? c0 : c1,
+                             in ? (float *)l0 : (float *)l1, u, phi_groups[group[m]], acc);
     hm[m].u = (const T *)u;
     hm[m].phi = (const typename PhiStore<T>::type *)phi_groups[group[m]];
     hm[m].acc = (typename AccSlot<T>::type *)acc;
@@ -1421,6 +1474,9 @@ cdi_status batch_run(cdi_domain *const *doms, int n_doms, int n_combos, const do
     hm[m].s.C[1] = (T *)c1;
     hm[m].s.Cl[0] = (float *)l0;
     hm[m].s.Cl[1] = (float *)l1;
+    for (int in = 0; in < 2; in++)
+      hm[m].s.f[in] = fields32(d, in ? c1 : c0, in ? (float *)l1 : (float *)l0, in ? c0 : c1,
+                               in ? (float *)l0 : (float *)l1, u, phis[group[m]], acc);
     hm[m].s.u = (const T *)u;
     hm[m].s.phi = (const typename PhiStore<T>::type *)phis[group[m]];
     hm[m].s.acc = (typename AccSlot<T>::type *)acc;
