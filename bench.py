@@ -593,10 +593,19 @@ def serve_requests(n, seed=100):
 def serve_bench(args):
     """Poisson arrivals at rates around the sequential capacity, the
     continuous-batching server against the plain sequential loop."""
-    import torch
     from paper_2110_13055_gb300 import serve
-    torch.cuda.set_device(0)
     n = args.serve_requests
+    # the request geometries, built on all host cores before the first GPU
+    # call (a spawned pool: no CUDA state is forked)
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    seeds = [7] + [100 + i for i in range(n)]
+    with ProcessPoolExecutor(max_workers=os.cpu_count(),
+                             mp_context=mp.get_context("spawn")) as ex:
+        for sd, mv in zip(seeds, ex.map(inputs.serve_instance, seeds, chunksize=4)):
+            _SERVE_MASKS[sd] = mv
+    import torch
+    torch.cuda.set_device(0)
     serve.solve(serve_requests(1, seed=7)[0])           # warm-up
     # capacity of the plain loop (back-to-back, no waiting)
     probe = serve_requests(n, seed=100)
@@ -724,11 +733,11 @@ def main():
     ap.add_argument("--sweep-geometries", type=int, default=64)
     ap.add_argument("--sweep-plain", action="store_true",
                     help="also run the plain loop that re-solves the flow for every solve")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 1.5, 2.0],
                     help="offered load as fractions of the sequential capacity")
     ap.add_argument("--serve", action="store_true",
                     help="continuous-batching server against the sequential loop")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--serve-slots", type=int, default=6)
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     args = ap.parse_args()

@@ -16,6 +16,7 @@
 // updated with error-free FP32 transformations: FP64-class accuracy at FP32
 // arithmetic rates, which matters on a part whose FP64 rate is low); and BF16
 // (collision in FP32, half the bytes of FP32, low accuracy).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -263,18 +264,28 @@ __device__ __forceinline__ auto slot_ptr(const PL &pl, const int *nb, int k, int
   return (bounce ? own : other) + (bounce ? k : q);
 }
 
-// Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
-template <int DIM, bool ODD>
-__device__ __forceinline__ void load_links(const LinkGeo &lg, int k, long long n,
-                                           int (&nb)[Lat<DIM>::Q]) {
-  using L = Lat<DIM>;
-  constexpr int NO = LatOff<DIM>::NO;
-  nb[0] = k;
-  if (!ODD) return;
-  const unsigned f = lg.lf[k];
-  int R[NO];
+// The link data of pore rank k: its flag word and row bases.
+template <int DIM> struct LinkData {
+  unsigned f;
+  int R[LatOff<DIM>::NO];
+};
+template <int DIM>
+__device__ __forceinline__ LinkData<DIM> load_link_data(const LinkGeo &lg, int k, long long n) {
+  LinkData<DIM> ld;
+  ld.f = lg.lf[k];
 #pragma unroll
-  for (int o = 0; o < NO; o++) R[o] = lg.lr[(size_t)o * n + k];
+  for (int o = 0; o < LatOff<DIM>::NO; o++) ld.R[o] = lg.lr[(size_t)o * n + k];
+  return ld;
+}
+
+// Neighbour ranks of pore rank k (all Q-1 directions) from its link data.
+template <int DIM>
+__device__ __forceinline__ void decode_links(const LinkGeo &lg, const LinkData<DIM> &ld, int k,
+                                             int (&nb)[Lat<DIM>::Q]) {
+  using L = Lat<DIM>;
+  const unsigned f = ld.f;
+  const int *R = ld.R;
+  nb[0] = k;
 #pragma unroll
   for (int i = 1; i < L::Q; i++) {
     const int o = off_of<DIM>(i);
@@ -295,6 +306,15 @@ __device__ __forceinline__ void load_links(const LinkGeo &lg, int k, long long n
 #pragma unroll
     for (int i = 1; i < L::Q; i++) nb[i] = lg.ovf[(size_t)(i - 1) * lg.n_ovf + e];
   }
+}
+
+// Neighbour ranks of pore rank k for the odd step (all Q-1 directions).
+template <int DIM, bool ODD>
+__device__ __forceinline__ void load_links(const LinkGeo &lg, int k, long long n,
+                                           int (&nb)[Lat<DIM>::Q]) {
+  nb[0] = k;
+  if (!ODD) return;
+  decode_links<DIM>(lg, load_link_data<DIM>(lg, k, n), k, nb);
 }
 
 __global__ void k_rank_scatter(const int *__restrict__ list, int n, int *__restrict__ rank) {
@@ -354,15 +374,13 @@ __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
 // loads, so occupancy matters more than a few spare registers; the bound is
 // chosen per variant so that nothing spills)
 template <typename S, int DIM, bool ODD, typename PL>
-__device__ __forceinline__ void lbm_body(const PL &g, const LinkGeo &lg, int n, int k0,
-                                         typename Arith<S>::type omega,
-                                         typename Arith<S>::type fx_half,
-                                         typename Arith<S>::type fsrc) {
+__device__ __forceinline__ void lbm_body_nb(const PL &g, const int (&nb)[Lat<DIM>::Q], int k0,
+                                            typename Arith<S>::type omega,
+                                            typename Arith<S>::type fx_half,
+                                            typename Arith<S>::type fsrc) {
   using T = typename Arith<S>::type;
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
-  int nb[Q];
-  load_links<DIM, ODD>(lg, k0, n, nb);
   T gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) gi[i] = widen(*slot_ptr<DIM, ODD, true>(g, nb, k0, i));
@@ -398,6 +416,42 @@ __device__ __forceinline__ void lbm_body(const PL &g, const LinkGeo &lg, int n, 
   for (int i = 0; i < Q; i++) *slot_ptr<DIM, ODD, false>(g, nb, k0, i) = narrow<S>(go[i]);
 }
 
+template <typename S, int DIM, bool ODD, typename PL>
+__device__ __forceinline__ void lbm_body(const PL &g, const LinkGeo &lg, int n, int k0,
+                                         typename Arith<S>::type omega,
+                                         typename Arith<S>::type fx_half,
+                                         typename Arith<S>::type fsrc) {
+  int nb[Lat<DIM>::Q];
+  load_links<DIM, ODD>(lg, k0, n, nb);
+  lbm_body_nb<S, DIM, ODD>(g, nb, k0, omega, fx_half, fsrc);
+}
+
+// The odd step as a grid-stride loop: while a site gathers, collides and
+// scatters, the link data of the thread's next site is already on its way
+// (sites may run in any order: in the AA pattern every slot is read and
+// written by one site only), so the link load no longer adds a memory round
+// trip ahead of the gathers.  Same arithmetic per site as k_lbm_step.
+template <typename S, int DIM, int BS>
+__global__ void __launch_bounds__(BS, sizeof(S) == 8 ? 1 : (DIM == 2 ? 8 : 6) * 128 / BS)
+    k_lbm_odd_pf(Planes<S, Lat<DIM>::Q> g, LinkGeo lg, int n, typename Arith<S>::type omega,
+                 typename Arith<S>::type fx_half, typename Arith<S>::type fsrc) {
+  const int stride = gridDim.x * BS;
+  int k = blockIdx.x * BS + threadIdx.x;
+  if (k >= n) return;
+  LinkData<DIM> cur = load_link_data<DIM>(lg, k, n);
+  while (true) {
+    const int kn = k + stride;
+    LinkData<DIM> nxt;
+    if (kn < n) nxt = load_link_data<DIM>(lg, kn, n);
+    int nb[Lat<DIM>::Q];
+    decode_links<DIM>(lg, cur, k, nb);
+    lbm_body_nb<S, DIM, true>(g, nb, k, omega, fx_half, fsrc);
+    if (kn >= n) break;
+    k = kn;
+    cur = nxt;
+  }
+}
+
 template <typename S, int DIM, bool ODD, int BS, int MINT>
 __global__ void __launch_bounds__(BS, (MINT > 0 ? MINT : (DIM == 2 ? 8 : (sizeof(S) == 8 ? 4 : 7)) * 128) / BS)
     k_lbm_step(Planes<S, Lat<DIM>::Q> g, LinkGeo lg, int n,
@@ -420,8 +474,9 @@ struct SplitConst {
 // The same step with every population stored as an FP32 pair gh + gl and the
 // collision carried out in pair arithmetic.
 template <int DIM, bool ODD, bool TAU1, typename PL>
-__device__ __forceinline__ void lbm_split_body(const PL &gh, const PL &gl, const LinkGeo &lg,
-                                               int n, int k0, const SplitConst &c) {
+__device__ __forceinline__ void lbm_split_body_nb(const PL &gh, const PL &gl,
+                                                  const int (&nb)[Lat<DIM>::Q], int k0,
+                                                  const SplitConst &c) {
   using L = Lat<DIM>;
   constexpr int Q = L::Q;
   // lattice weights as FP32 pairs: rest, axis, diagonal
@@ -429,8 +484,6 @@ __device__ __forceinline__ void lbm_split_body(const PL &gh, const PL &gl, const
   constexpr F2 kW0 = {(float)w0, (float)(w0 - (double)(float)w0)};
   constexpr F2 kWA = {(float)wa, (float)(wa - (double)(float)wa)};
   constexpr F2 kWD = {(float)wd, (float)(wd - (double)(float)wd)};
-  int nb[Q];
-  load_links<DIM, ODD>(lg, k0, n, nb);
   F2 gi[Q];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -492,6 +545,52 @@ __device__ __forceinline__ void lbm_split_body(const PL &gh, const PL &gl, const
     gh.plane(pl)[idx] = go.h;
     gl.plane(pl)[idx] = go.l;
   }
+}
+
+template <int DIM, bool ODD, bool TAU1, typename PL>
+__device__ __forceinline__ void lbm_split_body(const PL &gh, const PL &gl, const LinkGeo &lg,
+                                               int n, int k0, const SplitConst &c) {
+  int nb[Lat<DIM>::Q];
+  load_links<DIM, ODD>(lg, k0, n, nb);
+  lbm_split_body_nb<DIM, ODD, TAU1>(gh, gl, nb, k0, c);
+}
+
+// The pair-storage odd step as a prefetching grid-stride loop (as
+// k_lbm_odd_pf).
+template <int DIM, bool TAU1, int BS>
+__global__ void __launch_bounds__(BS)
+    k_lbm_split_odd_pf(Planes<float, Lat<DIM>::Q> gh, Planes<float, Lat<DIM>::Q> gl,
+                       LinkGeo lg, int n, SplitConst c) {
+  const int stride = gridDim.x * BS;
+  int k = blockIdx.x * BS + threadIdx.x;
+  if (k >= n) return;
+  LinkData<DIM> cur = load_link_data<DIM>(lg, k, n);
+  while (true) {
+    const int kn = k + stride;
+    LinkData<DIM> nxt;
+    if (kn < n) nxt = load_link_data<DIM>(lg, kn, n);
+    int nb[Lat<DIM>::Q];
+    decode_links<DIM>(lg, cur, k, nb);
+    lbm_split_body_nb<DIM, true, TAU1>(gh, gl, nb, k, c);
+    if (kn >= n) break;
+    k = kn;
+    cur = nxt;
+  }
+}
+
+// Blocks that fill every SM with the kernel at block size bs (once per
+// kernel; at most one block per bs sites).
+template <typename K> int resident_grid(K kernel, int bs, int n) {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, bs, 0);
+    (void)cudaGetLastError();
+    blocks = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+  }
+  return std::max(1, std::min(blocks, (n + bs - 1) / bs));
 }
 
 // BS threads per block, registers as the compiler sees fit.
@@ -687,9 +786,14 @@ template <int M> struct ModeT { using T = float; };
 template <> struct ModeT<M_F64> { using T = double; };
 template <> struct ModeT<M_BF16> { using T = __nv_bfloat16; };
 
+// One even + one odd step.  MINT: 0 registers as the compiler sees fit; > 0
+// capped so that MINT threads share an SM; -1 the odd step as the
+// prefetching grid-stride kernel.
 template <int M, int DIM, int BS, int MINT>
 void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   using T = typename ModeT<M>::T;
+  constexpr int Q = Lat<DIM>::Q;
+  constexpr int MI = MINT < 0 ? 0 : MINT;
   // one thread per pore site of the flow grid (pore rank)
   const int n = (int)d->n_flow_pore;
   const int grid = (n + BS - 1) / BS;
@@ -699,33 +803,37 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
                        host_pair(fs * Lat<DIM>::w(1)),
                        host_pair(fs * (DIM == 2 ? Lat<2>::w(3) : Lat<3>::w(4)))};
-    constexpr int Q = Lat<DIM>::Q;
     const Planes<float, Q> gh = make_planes<float, Q>((float *)d->d_g, n);
     const Planes<float, Q> gl = make_planes<float, Q>(d->d_glo, n);
-    if constexpr (MINT == 0) {
-      if (tau == 1.0) {
-        k_lbm_step_split<DIM, false, true, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-        k_lbm_step_split<DIM, true, true, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+    auto pair = [&](auto tau1) {
+      constexpr bool T1 = decltype(tau1)::value;
+      if constexpr (MI == 0)
+        k_lbm_step_split<DIM, false, T1, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+      else
+        k_lbm_step_split_occ<DIM, false, T1, BS, MI><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+      if constexpr (MINT < 0) {
+        auto *kern = k_lbm_split_odd_pf<DIM, T1, BS>;
+        kern<<<resident_grid(kern, BS, n), BS, 0, st>>>(gh, gl, lk, n, c);
+      } else if constexpr (MI == 0) {
+        k_lbm_step_split<DIM, true, T1, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       } else {
-        k_lbm_step_split<DIM, false, false, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-        k_lbm_step_split<DIM, true, false, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
+        k_lbm_step_split_occ<DIM, true, T1, BS, MI><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       }
-    } else {
-      if (tau == 1.0) {
-        k_lbm_step_split_occ<DIM, false, true, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-        k_lbm_step_split_occ<DIM, true, true, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-      } else {
-        k_lbm_step_split_occ<DIM, false, false, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-        k_lbm_step_split_occ<DIM, true, false, BS, MINT><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-      }
-    }
+    };
+    if (tau == 1.0) pair(std::true_type());
+    else pair(std::false_type());
   } else {
     using A = typename Arith<T>::type;
     const A omega = A(1.0 / tau), fxh = A(0.5 * force);
     const A fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
-    const Planes<T, Lat<DIM>::Q> g = make_planes<T, Lat<DIM>::Q>((T *)d->d_g, n);
-    k_lbm_step<T, DIM, false, BS, MINT><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
-    k_lbm_step<T, DIM, true, BS, MINT><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
+    const Planes<T, Q> g = make_planes<T, Q>((T *)d->d_g, n);
+    k_lbm_step<T, DIM, false, BS, MI><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
+    if constexpr (MINT < 0) {
+      auto *kern = k_lbm_odd_pf<T, DIM, BS>;
+      kern<<<resident_grid(kern, BS, n), BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
+    } else {
+      k_lbm_step<T, DIM, true, BS, MI><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
+    }
   }
 }
 
@@ -740,6 +848,7 @@ void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) 
     case 2: step_pair_bs<M, DIM, 256, 0>(d, st, tau, force); break;
     case 3: step_pair_bs<M, DIM, 64, OCC>(d, st, tau, force); break;
     case 4: step_pair_bs<M, DIM, 128, OCC>(d, st, tau, force); break;
+    case 5: step_pair_bs<M, DIM, 128, -1>(d, st, tau, force); break;
     default: step_pair_bs<M, DIM, 128, 0>(d, st, tau, force); break;
   }
 }
@@ -749,13 +858,14 @@ void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) 
 // bits (one thread per site, no cross-thread arithmetic), so the choice only
 // changes speed.  Runs once per domain, before its first solve resets the
 // populations.
-constexpr int kLbmVariantBlock[5] = {64, 128, 256, 64, 128};
+constexpr int kLbmVariantBlock[6] = {64, 128, 256, 64, 128, 128};
 template <int M, int DIM>
 cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
-  // 64, 128 or 256 threads per block, and 64 or 128 with registers capped
-  // for more resident warps (FP64 storage skips those: too many spills)
-  static const int cand_all[] = {0, 1, 2, 3, 4};
-  const int n_cand = M == M_F64 ? 3 : 5;
+  // 64, 128 or 256 threads per block, 64 or 128 with registers capped for
+  // more resident warps (FP64 storage skips those: too many spills), and 128
+  // with the prefetching odd step
+  static const int cand_all[] = {0, 1, 2, 5, 3, 4};
+  const int n_cand = M == M_F64 ? 4 : 6;
   const uint64_t key = cdi_tune_key(1, DIM, M, 0, d->n_flow_pore, tau == 1.0 ? 1 : 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {

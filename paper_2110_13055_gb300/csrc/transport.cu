@@ -438,9 +438,36 @@ __device__ __forceinline__ void ptwo_sum(float2 a, float2 b, float2 &s, float2 &
 // home cell the faces are summed in the order of np_cell (adsorption, +x,
 // -x, +y, -y, +z, -z), so without PAIR a cell whose faces all take the
 // |P| < 1/2 branch gets the bits np_cell gives.
+// The per-lane link data of warp w's tile: the lane's face flags and its
+// lateral neighbour ranks (-1 across a solid face or wall, or for the halo
+// lane).
+template <int DIM> struct NPLinks {
+  unsigned f;
+  int q[2 * DIM - 2];
+};
+template <int DIM>
+__device__ __forceinline__ NPLinks<DIM> np_links(const NPFields &F, int n_cells, int w) {
+  const int lane = threadIdx.x & 31;
+  const int r = kHome * w + lane - 1;
+  const bool valid = r >= 0 && r < n_cells;
+  const bool home = valid && lane != 0;
+  NPLinks<DIM> L;
+  L.f = valid ? (unsigned)F.fl[r] : 0u;
+#pragma unroll
+  for (int j = 0; j < 2 * DIM - 2; j++) L.q[j] = home ? F.lat[j][r] : -1;
+  return L;
+}
+
 template <int DIM, int NS, bool PAIR>
 __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int naccs,
                                           const NPConst<float> &c, int w) {
+  np_warp31<DIM, NS, PAIR>(F, n_cells, naccs, c, w, np_links<DIM>(F, n_cells, w));
+}
+
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int naccs,
+                                          const NPConst<float> &c, int w,
+                                          const NPLinks<DIM> &lk) {
   constexpr int NF = 2 * DIM;
   constexpr int NP = (NS + 1) / 2;
   // second species of pair p (a copy of the first when NS is odd)
@@ -452,11 +479,9 @@ __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int na
   auto ldC = [&](const float *const *A, int Q, int p) {
     return make_float2(A[2 * p][Q], A[K1(p)][Q]);
   };
-  const unsigned f = valid ? (unsigned)F.fl[r] : 0u;
+  const unsigned f = lk.f;
   // lateral neighbour ranks (-1 across a solid face or wall)
-  int q[NF - 2];
-#pragma unroll
-  for (int j = 0; j < NF - 2; j++) q[j] = home ? F.lat[j][r] : -1;
+  const int *q = lk.q;
   // own values
   const float2 z2 = make_float2(0.f, 0.f);
   float2 CP[NP], CPl[NP];
@@ -650,6 +675,45 @@ template <int DIM, int NS, int BS, int MINT, bool PAIR>
 __global__ void __launch_bounds__(BS, MINT / BS)
     k_np_step32_occ(NPFields F, int n, int naccs, NPConst<float> c) {
   np_warp31<DIM, NS, PAIR>(F, n, naccs, c, (blockIdx.x * BS + threadIdx.x) >> 5);
+}
+
+// The same step with a resident grid: each warp walks tiles w, w + W, ...
+// (W the warps of the launch) and loads the next tile's link data while it
+// computes the current tile, so that load no longer adds a memory round trip
+// ahead of the neighbour loads.  Tiles and accounts are those of the other
+// launch shapes.
+template <int DIM, int NS, int BS, bool PAIR>
+__global__ void __launch_bounds__(BS)
+    k_np_step32_pf(NPFields F, int n, int naccs, NPConst<float> c) {
+  const int nw = (int)np_warps(n);
+  const int W = gridDim.x * (BS / 32);
+  int w = (blockIdx.x * BS + threadIdx.x) >> 5;
+  if (w >= nw) return;  // whole warps leave together
+  NPLinks<DIM> cur = np_links<DIM>(F, n, w);
+  while (true) {
+    const int wn = w + W;
+    NPLinks<DIM> nxt;
+    if (wn < nw) nxt = np_links<DIM>(F, n, wn);
+    np_warp31<DIM, NS, PAIR>(F, n, naccs, c, w, cur);
+    if (wn >= nw) break;
+    w = wn;
+    cur = nxt;
+  }
+}
+
+// Blocks that fill every SM with the kernel at block size bs (once per
+// kernel; at most the blocks the work needs).
+template <typename K> int resident_grid(K kernel, int bs, long long units) {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, bs, 0);
+    (void)cudaGetLastError();
+    blocks = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+  }
+  return (int)std::max<long long>(1, std::min<long long>(blocks, (units + bs - 1) / bs));
 }
 
 // BS threads per block, registers as the compiler sees fit.
@@ -1077,13 +1141,17 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   if constexpr (std::is_same<T, float>::value) {
     const NPFields F = fields32(d, d->d_C[in], Cinl, d->d_C[1 - in], Coutl, d->d_u, d->d_phi,
                                 d->d_acc);
-    if constexpr (MINT == 0)
+    if constexpr (MINT < 0) {
+      auto *kern = k_np_step32_pf<DIM, NS, BS, PAIR>;
+      kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
+                                                          make_const<float>(d));
+    } else if constexpr (MINT == 0)
       k_np_step32<DIM, NS, BS, PAIR><<<grid, BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
                                                           make_const<float>(d));
     else
       k_np_step32_occ<DIM, NS, BS, MINT, PAIR><<<grid, BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
                                                                     make_const<float>(d));
-  } else if constexpr (MINT == 0) {
+  } else if constexpr (MINT <= 0) {
     k_np_step<T, DIM, NS, BS, PAIR><<<grid, BS, 0, st>>>(
         (const T *)d->d_C[in], (T *)d->d_C[1 - in], Cinl, Coutl, (const T *)d->d_u,
         (const typename PhiStore<T>::type *)d->d_phi, make_geo(d), make_const<T>(d),
@@ -1105,6 +1173,7 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 4: launch_step_bs<T, DIM, NS, 128, 1280, PAIR>(d, st, in); break;
     case 5: launch_step_bs<T, DIM, NS, 128, 1024, PAIR>(d, st, in); break;
     case 6: launch_step_bs<T, DIM, NS, 256, 1024, PAIR>(d, st, in); break;
+    case 7: launch_step_bs<T, DIM, NS, 128, -1, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1136,14 +1205,17 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 
 // Autotuner: times a few transport steps with each candidate launch shape
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
-// for 1280 resident threads per SM, for 128 and 256 one for 1024) on the
-// domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// for 1280 resident threads per SM, for 128 and 256 one for 1024, and an
+// FP32 resident grid that prefetches each warp's next tile) on the domain's
+// stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[7] = {64, 128, 256, 64, 128, 128, 256};
+constexpr int kNpVariantBlock[8] = {64, 128, 256, 64, 128, 128, 256, 128};
 cdi_status tune_np(cdi_domain *d) {
-  static const int cand[] = {0, 1, 2, 3, 4, 5, 6};
+  // variant 7 (resident grid with prefetch) is an FP32 launch shape; for
+  // FP64 it is the plain 128-thread launch again
+  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7};
   const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
