@@ -392,28 +392,34 @@ __device__ __forceinline__ void lbm_body_nb(const PL &g, const int (&nb)[Lat<DIM
     if (L::ey(i)) jy += T(L::ey(i)) * gi[i];
     if (DIM == 3 && L::ez(i)) jz += T(L::ez(i)) * gi[i];
   }
-  T go[Q];
-#pragma unroll
-  for (int i = 0; i < Q; i++) {
-    const T eu = T(L::ex(i)) * jx + T(L::ey(i)) * jy + T(L::ez(i)) * jz;
-    const T geq = T(L::w(i)) * (drho + T(3) * eu);
-    go[i] = gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
-  }
-  if (std::is_same<S, float>::value) {
-    // FP32 storage: the collision conserves mass exactly, but rounding the
-    // stored values does not, and the leak is biased; it feeds the slowest
-    // (pressure-diffusion) modes of the porous flow.  The rest population
-    // closes the balance: g*_0 = sum_i g_i - sum_{i>0} g*_i, both sums carried
-    // exactly as (sum, error) pairs.
-    float ms = 0.f, mc = 0.f, ss = 0.f, sc = 0.f;
+  // Post-collision values, each stored as soon as it is formed (fewer live
+  // registers, so more resident warps for the gathered loads); the rest
+  // population last.
+  //
+  // FP32 storage: the collision conserves mass exactly, but rounding the
+  // stored values does not, and the leak is biased; it feeds the slowest
+  // (pressure-diffusion) modes of the porous flow.  The rest population
+  // closes the balance: g*_0 = sum_i g_i - sum_{i>0} g*_i, both sums carried
+  // exactly as (sum, error) pairs.
+  constexpr bool kClose = std::is_same<S, float>::value;
+  float ms = 0.f, mc = 0.f, ss = 0.f, sc = 0.f;
+  if (kClose) {
 #pragma unroll
     for (int i = 0; i < Q; i++) two_sum_acc((float)gi[i], ms, mc);
-#pragma unroll
-    for (int i = 1; i < Q; i++) two_sum_acc((float)go[i], ss, sc);
-    go[0] = (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc));
   }
+  auto post = [&](int i) {
+    const T eu = T(L::ex(i)) * jx + T(L::ey(i)) * jy + T(L::ez(i)) * jz;
+    const T geq = T(L::w(i)) * (drho + T(3) * eu);
+    return gi[i] - omega * (gi[i] - geq) + T(L::w(i) * L::ex(i)) * fsrc;
+  };
 #pragma unroll
-  for (int i = 0; i < Q; i++) *slot_ptr<DIM, ODD, false>(g, nb, k0, i) = narrow<S>(go[i]);
+  for (int i = 1; i < Q; i++) {
+    const T go = post(i);
+    if (kClose) two_sum_acc((float)go, ss, sc);
+    *slot_ptr<DIM, ODD, false>(g, nb, k0, i) = narrow<S>(go);
+  }
+  const T go0 = kClose ? (T)__fadd_rn(__fsub_rn(ms, ss), __fsub_rn(mc, sc)) : post(0);
+  *slot_ptr<DIM, ODD, false>(g, nb, k0, 0) = narrow<S>(go0);
 }
 
 template <typename S, int DIM, bool ODD, typename PL>
