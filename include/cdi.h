@@ -254,6 +254,20 @@ cdi_status cdi_set_coupling(cdi_domain *dom, int64_t every_steps);
  * FP64 values per pore cell, taken on the first call. */
 cdi_status cdi_set_implicit(cdi_domain *dom, double tol, int max_iter);
 
+/* Launch shapes of the two step kernels (the paper has no counterpart: it
+ * states the method, not its launch configuration).  By default (-1) an autotuner
+ * times every candidate shape of the LBM step (0-5) and of the transport
+ * step (0-11) on the domain's first flow solve and first transport
+ * initialisation and keeps the fastest; every shape computes the same bits
+ * (the arithmetic of a lattice site or pore cell, and the per-warp account
+ * slots, do not depend on the shape), so the choice changes speed only.
+ * lbm_shape / np_shape in range fix the shape from the next step on; -1
+ * returns the kernel to the autotuner (its cached choice, if any).  Shapes
+ * are those of the FP32 kernels; FP64 maps the resident-grid shapes to plain
+ * launches.  Out-of-range values fail with CDI_ERR_INVALID_ARG and change
+ * nothing. */
+cdi_status cdi_set_launch_shapes(cdi_domain *dom, int32_t lbm_shape, int32_t np_shape);
+
 /* Advance n_steps >= 0 transport steps (Eq. 3 with Eq. 6): explicit unless
  * cdi_set_implicit chose the implicit scheme; explicit steps are
  * asynchronous. */

@@ -97,6 +97,7 @@ SIGNATURES = [
     ("cdi_step_transport", c_int, [c_void_p, c_int64]),
     ("cdi_set_coupling", c_int, [c_void_p, c_int64]),
     ("cdi_set_implicit", c_int, [c_void_p, c_double, c_int]),
+    ("cdi_set_launch_shapes", c_int, [c_void_p, c_int, c_int]),
     ("cdi_sweep_transport", c_int, [c_void_p, ctypes.POINTER(cdi_combo), c_int,
                                     ctypes.POINTER(cdi_elec_params),
                                     ctypes.POINTER(cdi_species), c_int, c_double, c_double,
@@ -275,6 +276,10 @@ def batch(domains, combos, *, z=(1, -1), D=(1.33e-9, 2.03e-9), c0=10.0, Ka=1e-6,
 
 def set_implicit(handle, tol: float, max_iter: int = 1000):
     _check(load().cdi_set_implicit(handle, c_double(tol), c_int(max_iter)), handle)
+
+
+def set_launch_shapes(handle, lbm_shape: int = -1, np_shape: int = -1):
+    _check(load().cdi_set_launch_shapes(handle, c_int(lbm_shape), c_int(np_shape)), handle)
 
 
 def set_coupling(handle, every_steps: int):
@@ -521,6 +526,12 @@ class Domain:
         solved to the relative residual tol; tol <= 0 returns to explicit
         steps."""
         set_implicit(self.handle, tol, max_iter)
+
+    def set_launch_shapes(self, lbm_shape: int = -1, np_shape: int = -1):
+        """Fix the launch shape of the LBM step (0-5) and of the transport
+        step (0-11); -1 leaves it to the autotuner.  Every shape computes the
+        same bits."""
+        set_launch_shapes(self.handle, lbm_shape, np_shape)
 
     def set_coupling(self, every_steps: int):
         """Re-solve the potential from the net charge every ``every_steps``

@@ -517,6 +517,25 @@ cdi_status cdi_set_implicit(cdi_domain *d, double tol, int max_iter) {
   return CDI_OK;
 }
 
+cdi_status cdi_set_launch_shapes(cdi_domain *d, int32_t lbm_shape, int32_t np_shape) {
+  if (!d) return CDI_ERR_INVALID_ARG;
+  if (lbm_shape < -1 || (lbm_shape >= 0 && cdi_lbm_shape_block(lbm_shape) == 0))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "no such LBM launch shape");
+  if (np_shape < -1 || (np_shape >= 0 && cdi_np_shape_block(np_shape) == 0))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "no such transport launch shape");
+  if (lbm_shape >= 0) {
+    d->lbm_variant = lbm_shape;
+    d->lbm_block = cdi_lbm_shape_block(lbm_shape);
+  }
+  d->lbm_tuned = lbm_shape >= 0;
+  if (np_shape >= 0) {
+    d->np_variant = np_shape;
+    d->np_block = cdi_np_shape_block(np_shape);
+  }
+  d->np_tuned = np_shape >= 0;
+  return CDI_OK;
+}
+
 cdi_status cdi_set_coupling(cdi_domain *d, int64_t every_steps) {
   if (!d) return CDI_ERR_INVALID_ARG;
   if (every_steps < 0) return cdi_fail(d, CDI_ERR_INVALID_ARG, "every_steps < 0");

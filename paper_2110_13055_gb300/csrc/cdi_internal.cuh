@@ -416,4 +416,7 @@ cdi_status cdi_np_steps(cdi_domain *d, int64_t n);
 cdi_status cdi_np_reduce(cdi_domain *d);
 cdi_status cdi_np_column_means(cdi_domain *d, int species);
 cdi_status cdi_imp_prepare(cdi_domain *d);
+// Threads per block of LBM / transport launch shape v (0 if v is no shape).
+int cdi_lbm_shape_block(int v);
+int cdi_np_shape_block(int v);
 cdi_status cdi_imp_steps(cdi_domain *d, int64_t n);

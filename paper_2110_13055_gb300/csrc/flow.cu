@@ -1185,6 +1185,8 @@ cdi_status build_flags(cdi_domain *d) {
 
 }  // namespace
 
+int cdi_lbm_shape_block(int v) { return v >= 0 && v < 6 ? kLbmVariantBlock[v] : 0; }
+
 cdi_status cdi_flow_build_flags(cdi_domain *d) {
   return d->dim == 2 ? build_flags<2>(d) : build_flags<3>(d);
 }

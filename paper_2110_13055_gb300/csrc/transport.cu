@@ -464,114 +464,146 @@ __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int na
   np_warp31<DIM, NS, PAIR>(F, n_cells, naccs, c, w, np_links<DIM>(F, n_cells, w));
 }
 
+// The values one lane of a warp tile works from: its cell's own fields, its
+// lateral neighbours' (the cell's own values across a closed face) and its +x
+// neighbour's (replaced by the cell's own unless that face is open and inside
+// the image).
+template <int DIM, int NS> struct NPLane {
+  static constexpr int NP = (NS + 1) / 2, NL = 2 * DIM - 2;
+  float2 CP[NP], CPl[NP], phP;
+  float uP[DIM];
+  float2 Cl[NL][NP], Cll[NL][NP], phl[NL];
+  float ul[NL];
+  float2 Cx[NP], Cxl[NP], phx;
+  float ux;
+};
+
+// Second species of pair p (a copy of the first when NS is odd).
+template <int NS> __device__ __forceinline__ constexpr int np_k1(int p) {
+  return 2 * p + 1 < NS ? 2 * p + 1 : 2 * p;
+}
+
+// Lateral neighbours' values, read from the field arrays (own values are
+// already in V).
 template <int DIM, int NS, bool PAIR>
-__device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int naccs,
-                                          const NPConst<float> &c, int w,
-                                          const NPLinks<DIM> &lk) {
+__device__ __forceinline__ void np_load_lateral(const NPFields &F, const int *q,
+                                                NPLane<DIM, NS> &V) {
+  constexpr int NP = (NS + 1) / 2;
+#pragma unroll
+  for (int j = 0; j < 2 * DIM - 2; j++) {
+    const int fc = j + 2;
+    if (q[j] >= 0) {
+      const int Q = q[j];
+      V.ul[j] = F.u[fc >> 1][Q];
+      V.phl[j] = F.phi[Q];
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        V.Cl[j][p] = make_float2(F.C[2 * p][Q], F.C[np_k1<NS>(p)][Q]);
+        V.Cll[j][p] = PAIR ? make_float2(F.Cl[2 * p][Q], F.Cl[np_k1<NS>(p)][Q])
+                           : make_float2(0.f, 0.f);
+      }
+    } else {
+      V.ul[j] = V.uP[fc >> 1];
+      V.phl[j] = V.phP;
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        V.Cl[j][p] = V.CP[p];
+        V.Cll[j][p] = V.CPl[p];
+      }
+    }
+  }
+}
+
+// Own, lateral and +x values of warp w's tile, read from the field arrays:
+// the +x neighbour is the next lane's cell, or for lane 31 the next tile's
+// first home cell.
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_load_global(const NPFields &F, int n_cells, int w,
+                                               unsigned f, const int *q, NPLane<DIM, NS> &V) {
+  constexpr int NP = (NS + 1) / 2;
+  const int lane = threadIdx.x & 31;
+  const int r = kHome * w + lane - 1;
+  const bool valid = r >= 0 && r < n_cells;
+  auto ldC = [&](const float *const *A, int Q, int p) {
+    return make_float2(A[2 * p][Q], A[np_k1<NS>(p)][Q]);
+  };
+  const float2 z2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int p = 0; p < NP; p++) V.CP[p] = V.CPl[p] = z2;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) V.uP[a] = 0.f;
+  V.phP = z2;
+  if (valid) {
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      V.CP[p] = ldC(F.C, r, p);
+      if (PAIR) V.CPl[p] = ldC(F.Cl, r, p);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; a++) V.uP[a] = F.u[a][r];
+    V.phP = F.phi[r];
+  }
+  np_load_lateral<DIM, NS, PAIR>(F, q, V);
+  V.ux = __shfl_down_sync(0xffffffffu, V.uP[0], 1);
+  V.phx.x = __shfl_down_sync(0xffffffffu, V.phP.x, 1);
+  V.phx.y = __shfl_down_sync(0xffffffffu, V.phP.y, 1);
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    V.Cx[p].x = __shfl_down_sync(0xffffffffu, V.CP[p].x, 1);
+    V.Cx[p].y = __shfl_down_sync(0xffffffffu, V.CP[p].y, 1);
+    V.Cxl[p] = z2;
+    if (PAIR) {
+      V.Cxl[p].x = __shfl_down_sync(0xffffffffu, V.CPl[p].x, 1);
+      V.Cxl[p].y = __shfl_down_sync(0xffffffffu, V.CPl[p].y, 1);
+    }
+  }
+  const bool xp = valid && !((f >> kFaceBit) & 1u) && !((f >> kEdgeBit) & 1u);
+  if (lane == 31 && xp) {  // rank r + 1 is the next warp's first home cell
+    V.ux = F.u[0][r + 1];
+    V.phx = F.phi[r + 1];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      V.Cx[p] = ldC(F.C, r + 1, p);
+      if (PAIR) V.Cxl[p] = ldC(F.Cl, r + 1, p);
+    }
+  }
+}
+
+// The update of warp w's tile from the values in V: the +x face flux is
+// evaluated once per face and handed to the next lane as its -x flux; then
+// adsorption, the x faces and the lateral faces are summed in that order and
+// the new concentrations and the warp's accounts written.
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_tile_update(const NPFields &F, int n_cells, int naccs,
+                                               const NPConst<float> &c, int w, unsigned f,
+                                               const int *q, NPLane<DIM, NS> &V) {
   constexpr int NF = 2 * DIM;
   constexpr int NP = (NS + 1) / 2;
-  // second species of pair p (a copy of the first when NS is odd)
-  auto K1 = [](int p) { return 2 * p + 1 < NS ? 2 * p + 1 : 2 * p; };
   const int lane = threadIdx.x & 31;
   const int r = kHome * w + lane - 1;
   const bool valid = r >= 0 && r < n_cells;
   const bool home = valid && lane != 0;
-  auto ldC = [&](const float *const *A, int Q, int p) {
-    return make_float2(A[2 * p][Q], A[K1(p)][Q]);
-  };
-  const unsigned f = lk.f;
-  // lateral neighbour ranks (-1 across a solid face or wall)
-  const int *q = lk.q;
-  // own values
   const float2 z2 = make_float2(0.f, 0.f);
-  float2 CP[NP], CPl[NP];
-  float uP[DIM];
-  float2 phP = z2;
-#pragma unroll
-  for (int p = 0; p < NP; p++) CP[p] = CPl[p] = z2;
-#pragma unroll
-  for (int a = 0; a < DIM; a++) uP[a] = 0.f;
-  if (valid) {
-#pragma unroll
-    for (int p = 0; p < NP; p++) {
-      CP[p] = ldC(F.C, r, p);
-      if (PAIR) CPl[p] = ldC(F.Cl, r, p);
-    }
-#pragma unroll
-    for (int a = 0; a < DIM; a++) uP[a] = F.u[a][r];
-    phP = F.phi[r];
-  }
-  // lateral neighbours' values (a closed face reads the cell's own values,
-  // for which the flux expression is exactly 0)
-  float2 Cl[NF - 2][NP], Cll[NF - 2][NP], phl[NF - 2];
-  float ul[NF - 2];
-#pragma unroll
-  for (int j = 0; j < NF - 2; j++) {
-    const int fc = j + 2;
-    if (q[j] >= 0) {
-      const int Q = q[j];
-      ul[j] = F.u[fc >> 1][Q];
-      phl[j] = F.phi[Q];
-#pragma unroll
-      for (int p = 0; p < NP; p++) {
-        Cl[j][p] = ldC(F.C, Q, p);
-        Cll[j][p] = PAIR ? ldC(F.Cl, Q, p) : z2;
-      }
-    } else {
-      ul[j] = uP[fc >> 1];
-      phl[j] = phP;
-#pragma unroll
-      for (int p = 0; p < NP; p++) {
-        Cl[j][p] = CP[p];
-        Cll[j][p] = CPl[p];
-      }
-    }
-  }
-  // +x face: the neighbour is rank r + 1 (the next lane) when the face is
-  // open and inside the image; the outlet ghost copies the cell
+  // +x face: open and inside the image, else the outlet ghost copies the cell
   const bool xs = (f >> kFaceBit) & 1u, xe = (f >> kEdgeBit) & 1u;
   const bool xp = valid && !xs && !xe;
-  float2 Cx[NP], Cxl[NP], phx;
-  float ux;
-  ux = __shfl_down_sync(0xffffffffu, uP[0], 1);
-  phx.x = __shfl_down_sync(0xffffffffu, phP.x, 1);
-  phx.y = __shfl_down_sync(0xffffffffu, phP.y, 1);
-#pragma unroll
-  for (int p = 0; p < NP; p++) {
-    Cx[p].x = __shfl_down_sync(0xffffffffu, CP[p].x, 1);
-    Cx[p].y = __shfl_down_sync(0xffffffffu, CP[p].y, 1);
-    Cxl[p] = z2;
-    if (PAIR) {
-      Cxl[p].x = __shfl_down_sync(0xffffffffu, CPl[p].x, 1);
-      Cxl[p].y = __shfl_down_sync(0xffffffffu, CPl[p].y, 1);
-    }
-  }
-  if (lane == 31 && xp) {  // rank r + 1 is the next warp's first home cell
-    ux = F.u[0][r + 1];
-    phx = F.phi[r + 1];
-#pragma unroll
-    for (int p = 0; p < NP; p++) {
-      Cx[p] = ldC(F.C, r + 1, p);
-      if (PAIR) Cxl[p] = ldC(F.Cl, r + 1, p);
-    }
-  }
   if (!xp) {
-    ux = uP[0];
-    phx = phP;
+    V.ux = V.uP[0];
+    V.phx = V.phP;
 #pragma unroll
     for (int p = 0; p < NP; p++) {
-      Cx[p] = CP[p];
-      Cxl[p] = CPl[p];
+      V.Cx[p] = V.CP[p];
+      V.Cxl[p] = V.CPl[p];
     }
   }
   float2 Jx[NP];
   {
-    const float uf = (valid && !xs) ? r_mul(0.5f, r_add(uP[0], ux)) : 0.f;
-    const float dd = phi_diff(phx, phP);
+    const float uf = (valid && !xs) ? r_mul(0.5f, r_add(V.uP[0], V.ux)) : 0.f;
+    const float dd = phi_diff(V.phx, V.phP);
 #pragma unroll
     for (int p = 0; p < NP; p++)
-      Jx[p] = face_flux_pair<PAIR>(uf, dd, phx, phP, CP[p], Cx[p], CPl[p], Cxl[p], c, 2 * p,
-                                   K1(p));
+      Jx[p] = face_flux_pair<PAIR>(uf, dd, V.phx, V.phP, V.CP[p], V.Cx[p], V.CPl[p], V.Cxl[p], c,
+                                   2 * p, np_k1<NS>(p));
   }
   // -x face: the previous lane's +x face (pore neighbour), the feed ghost
   // (inlet), or closed (solid)
@@ -584,12 +616,12 @@ __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int na
     if (ms) Jm[p] = z2;
   }
   if (home && me) {
-    const float uf = r_mul(-0.5f, r_add(uP[0], uP[0]));
-    const float dd = phi_diff(z2, phP);
+    const float uf = r_mul(-0.5f, r_add(V.uP[0], V.uP[0]));
+    const float dd = phi_diff(z2, V.phP);
 #pragma unroll
     for (int p = 0; p < NP; p++)
-      Jm[p] = face_flux_pair<PAIR>(uf, dd, z2, phP, CP[p], bc(c.c0), CPl[p], bc(c.c0lo), c,
-                                   2 * p, K1(p));
+      Jm[p] = face_flux_pair<PAIR>(uf, dd, z2, V.phP, V.CP[p], bc(c.c0), V.CPl[p], bc(c.c0lo), c,
+                                   2 * p, np_k1<NS>(p));
   }
   // adsorption on the solid faces (Eq. 6), then the faces in order
   float v[3 * NS];
@@ -599,7 +631,8 @@ __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int na
   float2 sumJ[NP];
 #pragma unroll
   for (int p = 0; p < NP; p++) {
-    const float2 Ja = pmul(pmul(bc(ns_solid), make_float2(c.Keff[2 * p], c.Keff[K1(p)])), CP[p]);
+    const float2 Ja =
+        pmul(pmul(bc(ns_solid), make_float2(c.Keff[2 * p], c.Keff[np_k1<NS>(p)])), V.CP[p]);
     sumJ[p] = padd(padd(Ja, Jx[p]), Jm[p]);
     if (home) {
       v[2 * p] = r_add(0.f, Ja.x);
@@ -618,12 +651,13 @@ __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int na
   for (int j = 0; j < NF - 2; j++) {
     const int fc = j + 2;
     const float half = (fc & 1) ? -0.5f : 0.5f;
-    const float uf = q[j] >= 0 ? r_mul(half, r_add(uP[fc >> 1], ul[j])) : 0.f;
-    const float dd = phi_diff(phl[j], phP);
+    const float uf = q[j] >= 0 ? r_mul(half, r_add(V.uP[fc >> 1], V.ul[j])) : 0.f;
+    const float dd = phi_diff(V.phl[j], V.phP);
 #pragma unroll
     for (int p = 0; p < NP; p++)
-      sumJ[p] = padd(sumJ[p], face_flux_pair<PAIR>(uf, dd, phl[j], phP, CP[p], Cl[j][p], CPl[p],
-                                                   Cll[j][p], c, 2 * p, K1(p)));
+      sumJ[p] = padd(sumJ[p], face_flux_pair<PAIR>(uf, dd, V.phl[j], V.phP, V.CP[p], V.Cl[j][p],
+                                                   V.CPl[p], V.Cll[j][p], c, 2 * p,
+                                                   np_k1<NS>(p)));
   }
   if (home) {
 #pragma unroll
@@ -632,20 +666,29 @@ __device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int na
       if (PAIR) {
         // (hi + lo) - dt/dx sum J by two-sum, renormalised
         float2 t, e;
-        ptwo_sum(CP[p], pmul(bc(-c.dtdx), sumJ[p]), t, e);
-        const float2 l = padd(CPl[p], e);
+        ptwo_sum(V.CP[p], pmul(bc(-c.dtdx), sumJ[p]), t, e);
+        const float2 l = padd(V.CPl[p], e);
         Cn = padd(t, l);
         Cnl = psub(l, psub(Cn, t));
         F.Col[2 * p][r] = Cnl.x;
         if (2 * p + 1 < NS) F.Col[2 * p + 1][r] = Cnl.y;
       } else {
-        Cn = pfma(bc(-c.dtdx), sumJ[p], CP[p]);
+        Cn = pfma(bc(-c.dtdx), sumJ[p], V.CP[p]);
       }
       F.Co[2 * p][r] = Cn.x;
       if (2 * p + 1 < NS) F.Co[2 * p + 1][r] = Cn.y;
     }
   }
   np_account_f32<NS>(v, home && (me || xe), F.acc, w, naccs);
+}
+
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_warp31(const NPFields &F, int n_cells, int naccs,
+                                          const NPConst<float> &c, int w,
+                                          const NPLinks<DIM> &lk) {
+  NPLane<DIM, NS> V;
+  np_load_global<DIM, NS, PAIR>(F, n_cells, w, lk.f, lk.q, V);
+  np_tile_update<DIM, NS, PAIR>(F, n_cells, naccs, c, w, lk.f, lk.q, V);
 }
 
 template <typename T, int DIM, int NS, bool PAIR>
@@ -695,6 +738,129 @@ __global__ void __launch_bounds__(BS)
     NPLinks<DIM> nxt;
     if (wn < nw) nxt = np_links<DIM>(F, n, wn);
     np_warp31<DIM, NS, PAIR>(F, n, naccs, c, w, cur);
+    if (wn >= nw) break;
+    w = wn;
+    cur = nxt;
+  }
+}
+
+// Asynchronous global-to-shared copies of 4 or 8 bytes (cp.async): the copy
+// lands in shared memory while the warp computes; cp.async.wait_group makes
+// it visible to the issuing thread.
+__device__ __forceinline__ void cp_async4(void *smem, const void *g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *g) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One warp tile's own fields in shared memory: entry e holds rank 31 w - 1 + e
+// (e = 0 the halo cell, e = 32 the next tile's first home cell); entries past
+// the last rank hold zeros.
+template <int DIM, int NS, bool PAIR> struct NPStage {
+  float2 phi[33];
+  float C[NS][33];
+  float Cl[PAIR ? NS : 1][33];
+  float u[DIM][33];
+};
+
+// Issues the copies of warp w's tile into S (lane l fills entry l, lane 31
+// also entry 32).
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_stage_fill(const NPFields &F, int n_cells, int w,
+                                              NPStage<DIM, NS, PAIR> &S) {
+  const int lane = threadIdx.x & 31;
+  auto put = [&](int e, int r) {
+    if (r >= 0 && r < n_cells) {
+      cp_async8(&S.phi[e], F.phi + r);
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        cp_async4(&S.C[s][e], F.C[s] + r);
+        if (PAIR) cp_async4(&S.Cl[s][e], F.Cl[s] + r);
+      }
+#pragma unroll
+      for (int a = 0; a < DIM; a++) cp_async4(&S.u[a][e], F.u[a] + r);
+    } else {
+      S.phi[e] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        S.C[s][e] = 0.f;
+        if (PAIR) S.Cl[s][e] = 0.f;
+      }
+#pragma unroll
+      for (int a = 0; a < DIM; a++) S.u[a][e] = 0.f;
+    }
+  };
+  const int r = kHome * w + lane - 1;
+  put(lane, r);
+  if (lane == 31) put(32, r + 1);
+}
+
+// Own and +x values of the tile from its stage (the same values
+// np_load_global reads: zeros past the last rank, entry l + 1 for the +x
+// neighbour), then the lateral neighbours from the field arrays.
+template <int DIM, int NS, bool PAIR>
+__device__ __forceinline__ void np_load_stage(const NPFields &F, const NPStage<DIM, NS, PAIR> &S,
+                                              const int *q, NPLane<DIM, NS> &V) {
+  constexpr int NP = (NS + 1) / 2;
+  const int e = threadIdx.x & 31;
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    V.CP[p] = make_float2(S.C[2 * p][e], S.C[np_k1<NS>(p)][e]);
+    V.CPl[p] = PAIR ? make_float2(S.Cl[2 * p][e], S.Cl[np_k1<NS>(p)][e]) : make_float2(0.f, 0.f);
+    V.Cx[p] = make_float2(S.C[2 * p][e + 1], S.C[np_k1<NS>(p)][e + 1]);
+    V.Cxl[p] =
+        PAIR ? make_float2(S.Cl[2 * p][e + 1], S.Cl[np_k1<NS>(p)][e + 1]) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; a++) V.uP[a] = S.u[a][e];
+  V.phP = S.phi[e];
+  V.ux = S.u[0][e + 1];
+  V.phx = S.phi[e + 1];
+  np_load_lateral<DIM, NS, PAIR>(F, q, V);
+}
+
+// The step with a resident grid whose warps stage their tiles in shared
+// memory one tile ahead: while a warp computes tile w it has the copies of
+// tile w + W's own fields (cp.async) and the loads of that tile's link data in
+// flight, so the only memory round trip left in front of its arithmetic is
+// the lateral neighbours'.  Tiles, values and accounts are those of the
+// other launch shapes, so it computes the same bits.
+// MINB > 0 caps the registers for MINB resident blocks per SM.
+template <int DIM, int NS, int BS, int MINB, bool PAIR>
+__global__ void __launch_bounds__(BS, MINB)
+    k_np_step32_cp(NPFields F, int n, int naccs, NPConst<float> c) {
+  __shared__ NPStage<DIM, NS, PAIR> stage[BS / 32][2];
+  const int nw = (int)np_warps(n);
+  const int W = gridDim.x * (BS / 32);
+  const int wi = threadIdx.x >> 5;
+  int w = (blockIdx.x * BS + threadIdx.x) >> 5;
+  if (w >= nw) return;  // whole warps leave together
+  np_stage_fill<DIM, NS, PAIR>(F, n, w, stage[wi][0]);
+  cp_async_commit();
+  NPLinks<DIM> cur = np_links<DIM>(F, n, w);
+  for (int t = 0;; t++) {
+    const int wn = w + W;
+    NPLinks<DIM> nxt;
+    if (wn < nw) {
+      np_stage_fill<DIM, NS, PAIR>(F, n, wn, stage[wi][(t + 1) & 1]);
+      nxt = np_links<DIM>(F, n, wn);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // this tile's copies have landed
+    __syncwarp();
+    NPLane<DIM, NS> V;
+    np_load_stage<DIM, NS, PAIR>(F, stage[wi][t & 1], cur.q, V);
+    np_tile_update<DIM, NS, PAIR>(F, n, naccs, c, w, cur.f, cur.q, V);
+    __syncwarp();  // every lane has read the stage before it is refilled
     if (wn >= nw) break;
     w = wn;
     cur = nxt;
@@ -1141,7 +1307,12 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   if constexpr (std::is_same<T, float>::value) {
     const NPFields F = fields32(d, d->d_C[in], Cinl, d->d_C[1 - in], Coutl, d->d_u, d->d_phi,
                                 d->d_acc);
-    if constexpr (MINT < 0) {
+    if constexpr (MINT == -2 || MINT == -3) {
+      // -3: registers capped for 1024 resident threads per SM
+      auto *kern = k_np_step32_cp<DIM, NS, BS, MINT == -3 ? 1024 / BS : 0, PAIR>;
+      kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
+                                                          make_const<float>(d));
+    } else if constexpr (MINT < 0) {
       auto *kern = k_np_step32_pf<DIM, NS, BS, PAIR>;
       kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
                                                           make_const<float>(d));
@@ -1174,6 +1345,10 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 5: launch_step_bs<T, DIM, NS, 128, 1024, PAIR>(d, st, in); break;
     case 6: launch_step_bs<T, DIM, NS, 256, 1024, PAIR>(d, st, in); break;
     case 7: launch_step_bs<T, DIM, NS, 128, -1, PAIR>(d, st, in); break;
+    case 8: launch_step_bs<T, DIM, NS, 128, -2, PAIR>(d, st, in); break;
+    case 9: launch_step_bs<T, DIM, NS, 256, -2, PAIR>(d, st, in); break;
+    case 10: launch_step_bs<T, DIM, NS, 128, -3, PAIR>(d, st, in); break;
+    case 11: launch_step_bs<T, DIM, NS, 256, -3, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1205,17 +1380,19 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 
 // Autotuner: times a few transport steps with each candidate launch shape
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
-// for 1280 resident threads per SM, for 128 and 256 one for 1024, and an
-// FP32 resident grid that prefetches each warp's next tile) on the domain's
-// stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// for 1280 resident threads per SM, for 128 and 256 one for 1024, an FP32
+// resident grid that prefetches each warp's next link data, and FP32
+// resident grids of 128 and 256 threads that stage each warp's next tile in
+// shared memory, with and without registers capped for 1024 threads per SM)
+// on the domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[8] = {64, 128, 256, 64, 128, 128, 256, 128};
+constexpr int kNpVariantBlock[12] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 256, 128, 256};
 cdi_status tune_np(cdi_domain *d) {
-  // variant 7 (resident grid with prefetch) is an FP32 launch shape; for
-  // FP64 it is the plain 128-thread launch again
-  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7};
+  // variants 7-11 (resident grids) are FP32 launch shapes; for FP64 they
+  // are the plain 128- and 256-thread launches again
+  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
   const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
@@ -1260,6 +1437,8 @@ cdi_status tune_np(cdi_domain *d) {
 }
 
 }  // namespace
+
+int cdi_np_shape_block(int v) { return v >= 0 && v < 12 ? kNpVariantBlock[v] : 0; }
 
 cdi_status cdi_np_build_flags(cdi_domain *d) {
   dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);

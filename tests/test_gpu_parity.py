@@ -431,6 +431,45 @@ def test_autotuner_picks_a_block_size():
     assert t["np_block"] in (64, 128, 256)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [cdi.FP32, cdi.FP32_SPLIT, cdi.FP32_CPAIR])
+def test_every_launch_shape_same_bits(prec, dim):
+    """Each candidate launch shape of the two step kernels, fixed one at a
+    time, computes bitwise the same flow and transport state; the packs are
+    large enough that the resident-grid shapes walk several tiles per warp
+    (and so run their staging pipelines past the first tile)."""
+    if dim == 2:
+        m = inputs.grain_pack((256, 640), 0.6, 2.0, 6.0, seed=5)[0]
+    else:
+        m = inputs.grain_pack((64, 64, 96), 0.6, 2.0, 5.0, seed=5)[0]
+    with cdi.Domain(m, precision=prec) as d:
+        u_ref = None
+        for ls in range(6):
+            d.set_launch_shapes(ls, 1)
+            d.solve_flow(tol=0.0, max_steps=300)
+            u = d.u_lattice()
+            if u_ref is None:
+                u_ref = u
+            assert np.array_equal(u, u_ref), f"LBM shape {ls}"
+        d.set_potential(0.8)
+        C_ref = G_ref = None
+        for ns in range(12):
+            d.set_launch_shapes(1, ns)
+            d.init_transport(Z, D, c0=10.0)
+            d.step(40)
+            C, G = d.C(), d.adsorbed()
+            if C_ref is None:
+                C_ref, G_ref = C, G
+            assert np.array_equal(C, C_ref), f"transport shape {ns}"
+            assert np.array_equal(G, G_ref), f"transport shape {ns}"
+        t = d.timing()
+        assert t["np_block"] == 256 and t["lbm_block"] == 128
+        with pytest.raises(cdi.CDIError):
+            d.set_launch_shapes(6, -1)
+        with pytest.raises(cdi.CDIError):
+            d.set_launch_shapes(-1, 12)
+
+
 @pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT, cdi.FP32_CPAIR])
 def test_save_and_load_state_resume_bitwise(prec):
     """A run stopped after n1 steps, saved, loaded into a fresh domain of the
