@@ -217,9 +217,12 @@ def algorithmic_bytes(prec, dim, n_flow_pore, n_pore, ns=2):
     Tc = 8 if prec in (cdi.FP64, cdi.FP32_SPLIT, cdi.FP32_CPAIR) else 4  # a pair is 8 B
     Q = 9 if dim == 2 else 19
     lbm = n_flow_pore * Q * 2 * Tp
-    # odd step: a 4-byte flag word and one 4-byte rank base per lateral row
-    # offset (2 in 2D, 8 in 3D); the even step reads none
-    lbm_layout = n_flow_pore * (4 + 4 * (2 if dim == 2 else 8)) // 2
+    # odd step: a 4-byte flag word, one byte per lateral row offset (2 in 2D,
+    # 8 in 3D; in 4-byte words) and a 32-site tile's 4-byte bases once per
+    # tile; the even step reads none
+    n_off = 2 if dim == 2 else 8
+    lbm_layout = (n_flow_pore * (4 + (4 if dim == 2 else 8))
+                  + n_off * 4 * ((n_flow_pore + 31) // 32)) // 2
     npb = n_pore * (ns * 2 * Tc + dim * Tt + Tt + 1)
     # potential low words (FP32), 2-byte face flags instead of the mask byte,
     # 2 (d - 1) lateral neighbour ranks

@@ -296,10 +296,11 @@ cdi_status cdi_create_domain(const cdi_domain_desc *desc, const uint8_t *mask,
   const size_t Tpop = d->prec == CDI_FP64 ? 8 : d->prec == CDI_BF16_POP ? 2 : 4;
   d->d_g = A(nq * Tpop);
   if (d->prec == CDI_FP32_SPLIT) d->d_glo = (float *)A(nq * 4);
-  d->n_lovf = 2 * D.ny * D.nz;
+  // (the overflow table is sized and taken while the links are built)
+  d->n_ltiles = (int)((d->n_flow_pore + 31) / 32);
   d->d_lf = (unsigned *)A((size_t)d->n_flow_pore * sizeof(unsigned));
-  d->d_lr = (int *)A((size_t)(D.dim == 2 ? 2 : 8) * d->n_flow_pore * sizeof(int));
-  d->d_lovf = (int *)A((size_t)(Q - 1) * d->n_lovf * sizeof(int));
+  d->d_ld = (unsigned *)A((size_t)(D.dim == 2 ? 1 : 2) * d->n_flow_pore * sizeof(unsigned));
+  d->d_lb = (int *)A((size_t)(D.dim == 2 ? 2 : 8) * d->n_ltiles * sizeof(int));
   d->d_uflow = (double *)A((size_t)D.dim * Nf * 8);
   // transport fields by pore rank
   d->W = (D.nx + 31) / 32;
@@ -523,6 +524,11 @@ cdi_status cdi_set_launch_shapes(cdi_domain *d, int32_t lbm_shape, int32_t np_sh
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "no such LBM launch shape");
   if (np_shape < -1 || (np_shape >= 0 && cdi_np_shape_block(np_shape) == 0))
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "no such transport launch shape");
+  // captured step graphs hold the old launches: drop them (recaptured on use)
+  CDI_TRY(d, cudaStreamSynchronize(d->stream), "launch shapes");
+  if (d->flow_graph) cudaGraphExecDestroy(d->flow_graph);
+  if (d->np_graph) cudaGraphExecDestroy(d->np_graph);
+  d->flow_graph = d->np_graph = nullptr;
   if (lbm_shape >= 0) {
     d->lbm_variant = lbm_shape;
     d->lbm_block = cdi_lbm_shape_block(lbm_shape);

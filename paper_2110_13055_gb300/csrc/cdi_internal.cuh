@@ -245,10 +245,14 @@ struct cdi_domain {
   int *d_flow_list = nullptr;   // pore sites of the flow grid, ascending
   long long n_flow_pore = 0;
   // neighbour data of the odd LBM step (see flow.cu): per pore rank a flag
-  // word and the rank bases of the lateral rows; full neighbour ranks of the
-  // x-edge sites in an overflow table of n_lovf = 2 ny nz slots
+  // word and one signed byte per lateral row offset (the offset's rank base
+  // less the rank and the base of the rank's 32-rank tile); per tile the
+  // bases; full neighbour ranks of the x-edge sites and of the sites whose
+  // bytes overflow in a table of n_lovf = 2 ny nz + (those sites) slots
   unsigned *d_lf = nullptr;     // n_flow_pore
-  int *d_lr = nullptr;          // (2 in 2D, 8 in 3D) * n_flow_pore
+  unsigned *d_ld = nullptr;     // (1 in 2D, 2 in 3D) words * n_flow_pore
+  int *d_lb = nullptr;          // (2 in 2D, 8 in 3D) * n_ltiles
+  int n_ltiles = 0;             // ceil(n_flow_pore / 32)
   int *d_lovf = nullptr;        // (Q-1) * n_lovf
   int n_lovf = 0;
   int *d_cell_list = nullptr;   // pore cells of the transport grid, ascending:
@@ -357,7 +361,7 @@ enum {
 
 // Counter slots in d_counter.
 enum { C_RES = 0, C_ULAT = 1, C_CG1 = 2, C_CG2 = 3, C_DT = 4, C_OUT = 5, C_MASS = 6, C_ACC = 7,
-       C_GEOM = 8, C_IMP = 9 };
+       C_GEOM = 8, C_IMP = 9, C_LINK = 10 };
 
 enum { PH_FLOW = 0, PH_CHECK = 1, PH_PSI = 2, PH_NP = 3 };
 

@@ -150,19 +150,25 @@ __global__ void k_flow_flags(const uint8_t *__restrict__ mask,
 // rank k (site x_k = (x, row), row = (y, z)):
 //   lf[k]          the site's solid-neighbour bits (bit i: the site x_k + e_i
 //                  is solid or beyond a lateral wall, so the link bounces
-//                  back) and kLinkEdge when x is the first or last column,
-//                  where the periodic x neighbour wraps around;
-//   lr[o * n + k]  for each lateral row offset o = (ey, ez) of the lattice
+//                  back) and kLinkEdge when the site's ranks come from the
+//                  overflow table (below);
+//   R_o(k)         for each lateral row offset o = (ey, ez) of the lattice
 //                  (2 for D2Q9, 8 for D3Q19): the rank the site (x, row + o)
 //                  has, or would have if it is solid (the number of pore
 //                  sites before it in lattice order).
 // Pore sites of one row are consecutive ranks, so the neighbour along e_i is
-// k + ex when it stays in the row, and otherwise lr[o] (ex = 0), lr[o] - 1
-// (ex = -1) or lr[o] + [site (x, row + o) is pore] (ex = +1).  At an x-edge
-// site lr[0] instead indexes an overflow table holding all Q - 1 ranks
-// (ovf[(i - 1) * n_ovf + e]; -1 for a bounce-back link).  The odd step reads
-// 4 + 4 * (offsets) bytes per site this way (36 B in 3D) instead of
-// 4 * (Q - 1) (72 B).
+// k + ex when it stays in the row, and otherwise R_o (ex = 0), R_o - 1
+// (ex = -1) or R_o + [site (x, row + o) is pore] (ex = +1).  R_o - k changes
+// slowly along the rank order, so it is stored as a per-tile base (lb[o *
+// n_ltiles + k / 32], 32 consecutive ranks a tile) plus one signed byte per
+// offset and site (ld: byte o of the site's 4-byte words).  Sites at the
+// first or last column (where the periodic x neighbour wraps around) and
+// sites whose byte would overflow take all Q - 1 ranks from an overflow table
+// instead (ovf[(i - 1) * n_ovf + e], -1 for a bounce-back link; e in the
+// site's first word): slot 2 * row + (x != 0) for an x-edge site, 2 ny nz +
+// (a running count) for the others.  The odd step reads 4 + 8 bytes per site
+// in 3D (4 + 4 in 2D) this way, plus a tile's bases once per 32 sites,
+// instead of 4 * (Q - 1) bytes.
 constexpr unsigned kLinkEdge = 1u << 31;
 
 template <int DIM> struct LatOff;
@@ -201,10 +207,14 @@ template <int DIM> __host__ __device__ constexpr int dir_of_off(int o) {
 
 struct LinkGeo {
   const unsigned *lf;  // n: solid-neighbour bits | kLinkEdge
-  const int *lr;       // NO * n: rank bases of the lateral rows
-  const int *ovf;      // (Q - 1) * n_ovf: full neighbour ranks of x-edge sites
+  const unsigned *ld;  // LinkWords * n: the sites' row-base bytes (or slot)
+  const int *lb;       // NO * n_tiles: the tiles' row bases
+  const int *ovf;      // (Q - 1) * n_ovf: full neighbour ranks
   int n_ovf;
+  int n_tiles;
 };
+// 4-byte words of row-base bytes per site.
+template <int DIM> __host__ __device__ constexpr int link_words() { return (LatOff<DIM>::NO + 3) / 4; }
 
 // Where direction i of pore rank k lives: plane i of the population array
 // (plane i = direction i of every pore rank).  Planes<S, Q> passes the Q
@@ -269,12 +279,27 @@ template <int DIM> struct LinkData {
   unsigned f;
   int R[LatOff<DIM>::NO];
 };
+// (R[0] holds the overflow slot at a kLinkEdge site.)
 template <int DIM>
-__device__ __forceinline__ LinkData<DIM> load_link_data(const LinkGeo &lg, int k, long long n) {
+__device__ __forceinline__ LinkData<DIM> load_link_data(const LinkGeo &lg, int k, long long) {
+  constexpr int NO = LatOff<DIM>::NO;
   LinkData<DIM> ld;
   ld.f = lg.lf[k];
+  unsigned w[link_words<DIM>()];
+  if constexpr (link_words<DIM>() == 2) {
+    const uint2 v = reinterpret_cast<const uint2 *>(lg.ld)[k];
+    w[0] = v.x;
+    w[1] = v.y;
+  } else {
+    w[0] = lg.ld[k];
+  }
+  const int t = k >> 5;
 #pragma unroll
-  for (int o = 0; o < LatOff<DIM>::NO; o++) ld.R[o] = lg.lr[(size_t)o * n + k];
+  for (int o = 0; o < NO; o++) {
+    const int b = (int)(w[o >> 2] << (24 - 8 * (o & 3))) >> 24;  // signed byte o
+    ld.R[o] = k + lg.lb[(size_t)o * lg.n_tiles + t] + b;
+  }
+  if (ld.f & kLinkEdge) ld.R[0] = (int)w[0];
   return ld;
 }
 
@@ -322,47 +347,91 @@ __global__ void k_rank_scatter(const int *__restrict__ list, int n, int *__restr
     rank[list[k]] = k;
 }
 
-// Builds lf, lr and the overflow table (rank[site]: the pore rank, -1 for a
-// solid site).  The overflow slot of an x-edge site is 2 * row + (x != 0).
+// Builds lf, ld and lb (rank[site]: the pore rank, -1 for a solid site), one
+// warp per 32-rank tile.  A tile's base of offset o is R_o - k of its first
+// site that uses offset o (one of (x - 1, x, x + 1) in row + o is pore and
+// the row is not beyond a wall); a site whose R_o - k - base does not fit a
+// signed byte, like an x-edge site, is marked kLinkEdge and gets an overflow
+// slot (e in its first word), filled by k_links_ovf once the table is sized.
 template <int DIM>
 __global__ void k_links(const typename FlowFlag<DIM>::type *__restrict__ fl,
                         const int *__restrict__ list, int n, const int *__restrict__ rank,
-                        unsigned *__restrict__ lf, int *__restrict__ lr, int *__restrict__ ovf,
-                        int n_ovf, int NX, int ny, int nz, int walls) {
+                        unsigned *__restrict__ lf, unsigned *__restrict__ ld,
+                        int *__restrict__ lb, int n_tiles, unsigned *__restrict__ n_extra,
+                        int NX, int ny, int nz, int walls) {
   using L = Lat<DIM>;
   using O = LatOff<DIM>;
   using W = WrapBit<DIM>;
+  constexpr int NW = link_words<DIM>();
   constexpr unsigned kSolidBits = ((1u << L::Q) - 1u) & ~1u;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int s = list[k];
-    const unsigned f = fl[s];
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tiles; t += warps) {
+    const int k = 32 * t + lane;
+    const bool valid = k < n;
+    const int s = valid ? list[k] : 0;
+    const unsigned f = valid ? (unsigned)fl[s] : 0u;
     const int x = s % NX, row = s / NX, y = row % ny, z = row / ny;
-    const bool xedge = ((f >> W::XHI) & 1u) || ((f >> W::XLO) & 1u);
-    lf[k] = (f & kSolidBits) | (xedge ? kLinkEdge : 0u);
+    const bool xedge = valid && (((f >> W::XHI) & 1u) || ((f >> W::XLO) & 1u));
+    unsigned w[NW];
+#pragma unroll
+    for (int j = 0; j < NW; j++) w[j] = 0u;
+    bool wide = false;
 #pragma unroll
     for (int o = 0; o < O::NO; o++) {
       int Y = y + O::ey(o), Z = z + O::ez(o);
       int R = 0;
+      bool used = false;
       const bool beyond = Y < 0 || Y >= ny || Z < 0 || Z >= nz;
-      if (!xedge && !(beyond && walls)) {
+      if (valid && !xedge && !(beyond && walls)) {
         Y = (Y + ny) % ny;
         Z = (Z + nz) % nz;
         const int sp = (Z * ny + Y) * NX + x;  // x - 1 and x + 1 stay in the row
+        used = true;
         if (rank[sp] >= 0) R = rank[sp];
         else if (rank[sp + 1] >= 0) R = rank[sp + 1];
         else if (rank[sp - 1] >= 0) R = rank[sp - 1] + 1;
+        else used = false;  // all three links bounce back: R_o is never read
       }
-      lr[(size_t)o * n + k] = R;
+      const unsigned users = __ballot_sync(0xffffffffu, used);
+      const int D = R - k;
+      const int base = users ? __shfl_sync(0xffffffffu, D, __ffs(users) - 1) : 0;
+      if (lane == 0) lb[(size_t)o * n_tiles + t] = base;
+      const int b = used ? D - base : 0;
+      if (b < -128 || b > 127) wide = true;
+      w[o >> 2] |= ((unsigned)b & 0xffu) << (8 * (o & 3));
     }
+    if (!valid) continue;
     if (xedge) {
-      const int e = 2 * row + (x != 0 ? 1 : 0);
-      lr[k] = e;
-      const SiteIdx<DIM> ix(s, f, NX, ny, nz);
-#pragma unroll
-      for (int i = 1; i < L::Q; i++)
-        ovf[(size_t)(i - 1) * n_ovf + e] =
-            ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
+      w[0] = (unsigned)(2 * row + (x != 0 ? 1 : 0));
+    } else if (wide) {
+      w[0] = (unsigned)(2 * ny * nz) + atomicAdd(n_extra, 1u);
     }
+    lf[k] = (f & kSolidBits) | ((xedge || wide) ? kLinkEdge : 0u);
+#pragma unroll
+    for (int j = 0; j < NW; j++) ld[(size_t)k * NW + j] = w[j];
+  }
+}
+
+// Fills the overflow slots of the kLinkEdge sites: all Q - 1 neighbour ranks
+// (-1 for a bounce-back link).
+template <int DIM>
+__global__ void k_links_ovf(const typename FlowFlag<DIM>::type *__restrict__ fl,
+                            const int *__restrict__ list, int n, const int *__restrict__ rank,
+                            const unsigned *__restrict__ lf, const unsigned *__restrict__ ld,
+                            int *__restrict__ ovf, int n_ovf, int NX, int ny, int nz) {
+  using L = Lat<DIM>;
+  constexpr int NW = link_words<DIM>();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    if (!(lf[k] & kLinkEdge)) continue;
+    const int s = list[k];
+    const unsigned f = fl[s];
+    const int e = (int)ld[(size_t)k * NW];
+    const SiteIdx<DIM> ix(s, f, NX, ny, nz);
+#pragma unroll
+    for (int i = 1; i < L::Q; i++)
+      ovf[(size_t)(i - 1) * n_ovf + e] =
+          ((f >> i) & 1u) ? -1 : rank[ix.nb(L::ex(i), L::ey(i), L::ez(i))];
   }
 }
 
@@ -803,7 +872,7 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   // one thread per pore site of the flow grid (pore rank)
   const int n = (int)d->n_flow_pore;
   const int grid = (n + BS - 1) / BS;
-  const LinkGeo lk{d->d_lf, d->d_lr, d->d_lovf, d->n_lovf};
+  const LinkGeo lk{d->d_lf, d->d_ld, d->d_lb, d->d_lovf, d->n_lovf, d->n_ltiles};
   if (M == M_SPLIT) {
     const double fs = (1.0 - 0.5 / tau) * 3.0 * force;
     const SplitConst c{host_pair(1.0 / tau), host_pair(1.0 - 1.0 / tau), host_pair(0.5 * force),
@@ -1059,7 +1128,7 @@ cdi_status flow_batch(cdi_domain *const *doms, int n_doms, const cdi_flow_params
       LbmMember<S> m;
       m.g = (S *)d->d_g;
       m.glo = d->d_glo;
-      m.lg = LinkGeo{d->d_lf, d->d_lr, d->d_lovf, d->n_lovf};
+      m.lg = LinkGeo{d->d_lf, d->d_ld, d->d_lb, d->d_lovf, d->n_lovf, d->n_ltiles};
       m.n = (int)d->n_flow_pore;
       m.block0 = blocks;
       blocks += (m.n + kLbmBatchBlock - 1) / kLbmBatchBlock;
@@ -1193,25 +1262,44 @@ cdi_status cdi_flow_build_flags(cdi_domain *d) {
 
 // Neighbour data of the compact population layout (after the pore lists):
 // rank[site] scattered from the list (rank_work: Nf ints, -1 for solid), then
-// the flag words, row bases and overflow table of every pore rank.
+// the flag words, row-base bytes and tile bases of every pore rank; then the
+// overflow table, sized by the sites that need it, is taken and filled.
 cdi_status cdi_flow_build_links(cdi_domain *d, int *rank_work) {
   const int n = (int)d->n_flow_pore;
+  const int Q = d->dim == 2 ? 9 : 19;
+  unsigned *n_extra = d->d_counter + C_LINK;
   CDI_TRY(d, cudaMemsetAsync(rank_work, 0xff, (size_t)d->Nf * sizeof(int), d->stream),
           "rank reset");
-  CDI_TRY(d, cudaMemsetAsync(d->d_lovf, 0xff, (size_t)(d->dim == 2 ? 8 : 18) * d->n_lovf * 4,
-                             d->stream),
-          "overflow reset");
+  CDI_TRY(d, cudaMemsetAsync(n_extra, 0, sizeof(unsigned), d->stream), "overflow count reset");
   k_rank_scatter<<<kRedBlocks, kRedThreads, 0, d->stream>>>(d->d_flow_list, n, rank_work);
   if (d->dim == 2)
     k_links<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_lr,
-        d->d_lovf, d->n_lovf, d->NX, d->ny, d->nz, d->walls);
+        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_ld,
+        d->d_lb, d->n_ltiles, n_extra, d->NX, d->ny, d->nz, d->walls);
   else
     k_links<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
-        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_lr,
-        d->d_lovf, d->n_lovf, d->NX, d->ny, d->nz, d->walls);
-  d->timing.kernel_launches += 2;
+        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_ld,
+        d->d_lb, d->n_ltiles, n_extra, d->NX, d->ny, d->nz, d->walls);
   CDI_TRY(d, cudaGetLastError(), "neighbour data");
+  unsigned extra = 0;
+  CDI_TRY(d, cudaMemcpyAsync(&extra, n_extra, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             d->stream), "overflow count");
+  CDI_TRY(d, cudaStreamSynchronize(d->stream), "overflow count");
+  d->n_lovf = 2 * d->ny * d->nz + (int)extra;
+  d->d_lovf = (int *)cdi_dev_alloc(d, (size_t)(Q - 1) * d->n_lovf * sizeof(int));
+  if (!d->d_lovf) return cdi_fail(d, CDI_ERR_OOM, "neighbour overflow table");
+  CDI_TRY(d, cudaMemsetAsync(d->d_lovf, 0xff, (size_t)(Q - 1) * d->n_lovf * sizeof(int),
+                             d->stream), "overflow reset");
+  if (d->dim == 2)
+    k_links_ovf<2><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<2>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_ld,
+        d->d_lovf, d->n_lovf, d->NX, d->ny, d->nz);
+  else
+    k_links_ovf<3><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        (const FlowFlag<3>::type *)d->d_fflags, d->d_flow_list, n, rank_work, d->d_lf, d->d_ld,
+        d->d_lovf, d->n_lovf, d->NX, d->ny, d->nz);
+  d->timing.kernel_launches += 3;
+  CDI_TRY(d, cudaGetLastError(), "neighbour overflow table");
   return CDI_OK;
 }
 

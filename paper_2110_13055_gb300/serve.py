@@ -66,8 +66,12 @@ def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> in
     Tc = T + (4 if precision in (cdi.FP32_SPLIT, cdi.FP32_CPAIR) else 0)  # + low words
     nx = mask.shape[-1]
     rows = N // nx
-    n_ovf = 2 * rows                                  # x-edge overflow slots
-    flow = ((Q * Tpop + 4 + 4 * (2 if dim == 2 else 8)) * n_fp + (Q - 1) * 4 * n_ovf
+    # overflow slots: x-edge sites, plus an allowance for the sites whose
+    # row-base bytes overflow (under one in a thousand sites on the grain packs)
+    n_ovf = 2 * rows + n_fp // 256
+    n_off = 2 if dim == 2 else 8                      # lateral row offsets
+    links = (4 + (4 if dim == 2 else 8)) * n_fp + n_off * 4 * ((n_fp + 31) // 32)
+    flow = (Q * Tpop * n_fp + links + (Q - 1) * 4 * n_ovf
             + Nf * (2 if dim == 2 else 4) + dim * Nf * 8)
     transport = (n_pore * (4 + 8 + 2 + 2 * (dim - 1) * 4 + dim * T + 8 + 2 * 4 * Tc)
                  + rows * ((nx + 31) // 32) * 8)
