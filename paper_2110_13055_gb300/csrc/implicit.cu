@@ -66,14 +66,18 @@ __device__ __forceinline__ int ikind(const IGeo &g, unsigned f, int fc, int r, i
 __device__ __forceinline__ double phi_of(double v) { return v; }
 __device__ __forceinline__ double phi_of(float2 v) { return (double)v.x + (double)v.y; }
 
+// Per-species constants passed by value.
+struct PerSpecies {
+  double v[kMaxSpecies];
+};
+
 template <typename T, int DIM>
 __global__ void k_imp_coef(IGeo g, const T *__restrict__ u,
                            const typename PhiStore<T>::type *__restrict__ phi, int ns,
-                           double4 dxD, double4 Ddx, double4 Keff, double4 zf, double inv_dx,
-                           double c0, double *__restrict__ co) {
+                           PerSpecies dxD, PerSpecies Ddx, PerSpecies Keff, PerSpecies zf,
+                           double inv_dx, double c0, double *__restrict__ co) {
   using C = ICoef<DIM>;
-  const double dxDk[4] = {dxD.x, dxD.y, dxD.z, dxD.w}, Ddxk[4] = {Ddx.x, Ddx.y, Ddx.z, Ddx.w};
-  const double Kk[4] = {Keff.x, Keff.y, Keff.z, Keff.w}, zk[4] = {zf.x, zf.y, zf.z, zf.w};
+  const double *dxDk = dxD.v, *Ddxk = Ddx.v, *Kk = Keff.v, *zk = zf.v;
   const size_t n = (size_t)g.n;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.n; r += gridDim.x * blockDim.x) {
     const unsigned f = g.fl[r];
@@ -369,19 +373,17 @@ IGeo make_igeo(const cdi_domain *d) {
 
 template <typename T, int DIM>
 cdi_status imp_coefs(cdi_domain *d) {
-  double dxD[4], Ddx[4], Keff[4], zf[4];
+  PerSpecies dxD, Ddx, Keff, zf;
   for (int k = 0; k < kMaxSpecies; k++) {
     const double Dk = k < d->ns ? d->D[k] : 1.0;
-    dxD[k] = d->dx / Dk;
-    Ddx[k] = Dk / d->dx;
-    Keff[k] = d->Ka / (1.0 + d->Ka * d->dx / (2.0 * Dk));
-    zf[k] = k < d->ns ? d->z[k] : 0.0;
+    dxD.v[k] = d->dx / Dk;
+    Ddx.v[k] = Dk / d->dx;
+    Keff.v[k] = d->Ka / (1.0 + d->Ka * d->dx / (2.0 * Dk));
+    zf.v[k] = k < d->ns ? d->z[k] : 0.0;
   }
   k_imp_coef<T, DIM><<<kRedBlocks, kRedThreads, 0, d->stream>>>(
       make_igeo(d), (const T *)d->d_u, (const typename PhiStore<T>::type *)d->d_phi, d->ns,
-      make_double4(dxD[0], dxD[1], dxD[2], dxD[3]), make_double4(Ddx[0], Ddx[1], Ddx[2], Ddx[3]),
-      make_double4(Keff[0], Keff[1], Keff[2], Keff[3]), make_double4(zf[0], zf[1], zf[2], zf[3]),
-      1.0 / d->dx, d->c0, d->d_icoef);
+      dxD, Ddx, Keff, zf, 1.0 / d->dx, d->c0, d->d_icoef);
   d->timing.kernel_launches++;
   CDI_TRY(d, cudaGetLastError(), "implicit operator");
   d->imp_stale = false;

@@ -744,129 +744,6 @@ __global__ void __launch_bounds__(BS)
   }
 }
 
-// Asynchronous global-to-shared copies of 4 or 8 bytes (cp.async): the copy
-// lands in shared memory while the warp computes; cp.async.wait_group makes
-// it visible to the issuing thread.
-__device__ __forceinline__ void cp_async4(void *smem, const void *g) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *g) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// One warp tile's own fields in shared memory: entry e holds rank 31 w - 1 + e
-// (e = 0 the halo cell, e = 32 the next tile's first home cell); entries past
-// the last rank hold zeros.
-template <int DIM, int NS, bool PAIR> struct NPStage {
-  float2 phi[33];
-  float C[NS][33];
-  float Cl[PAIR ? NS : 1][33];
-  float u[DIM][33];
-};
-
-// Issues the copies of warp w's tile into S (lane l fills entry l, lane 31
-// also entry 32).
-template <int DIM, int NS, bool PAIR>
-__device__ __forceinline__ void np_stage_fill(const NPFields &F, int n_cells, int w,
-                                              NPStage<DIM, NS, PAIR> &S) {
-  const int lane = threadIdx.x & 31;
-  auto put = [&](int e, int r) {
-    if (r >= 0 && r < n_cells) {
-      cp_async8(&S.phi[e], F.phi + r);
-#pragma unroll
-      for (int s = 0; s < NS; s++) {
-        cp_async4(&S.C[s][e], F.C[s] + r);
-        if (PAIR) cp_async4(&S.Cl[s][e], F.Cl[s] + r);
-      }
-#pragma unroll
-      for (int a = 0; a < DIM; a++) cp_async4(&S.u[a][e], F.u[a] + r);
-    } else {
-      S.phi[e] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int s = 0; s < NS; s++) {
-        S.C[s][e] = 0.f;
-        if (PAIR) S.Cl[s][e] = 0.f;
-      }
-#pragma unroll
-      for (int a = 0; a < DIM; a++) S.u[a][e] = 0.f;
-    }
-  };
-  const int r = kHome * w + lane - 1;
-  put(lane, r);
-  if (lane == 31) put(32, r + 1);
-}
-
-// Own and +x values of the tile from its stage (the same values
-// np_load_global reads: zeros past the last rank, entry l + 1 for the +x
-// neighbour), then the lateral neighbours from the field arrays.
-template <int DIM, int NS, bool PAIR>
-__device__ __forceinline__ void np_load_stage(const NPFields &F, const NPStage<DIM, NS, PAIR> &S,
-                                              const int *q, NPLane<DIM, NS> &V) {
-  constexpr int NP = (NS + 1) / 2;
-  const int e = threadIdx.x & 31;
-#pragma unroll
-  for (int p = 0; p < NP; p++) {
-    V.CP[p] = make_float2(S.C[2 * p][e], S.C[np_k1<NS>(p)][e]);
-    V.CPl[p] = PAIR ? make_float2(S.Cl[2 * p][e], S.Cl[np_k1<NS>(p)][e]) : make_float2(0.f, 0.f);
-    V.Cx[p] = make_float2(S.C[2 * p][e + 1], S.C[np_k1<NS>(p)][e + 1]);
-    V.Cxl[p] =
-        PAIR ? make_float2(S.Cl[2 * p][e + 1], S.Cl[np_k1<NS>(p)][e + 1]) : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int a = 0; a < DIM; a++) V.uP[a] = S.u[a][e];
-  V.phP = S.phi[e];
-  V.ux = S.u[0][e + 1];
-  V.phx = S.phi[e + 1];
-  np_load_lateral<DIM, NS, PAIR>(F, q, V);
-}
-
-// The step with a resident grid whose warps stage their tiles in shared
-// memory one tile ahead: while a warp computes tile w it has the copies of
-// tile w + W's own fields (cp.async) and the loads of that tile's link data in
-// flight, so the only memory round trip left in front of its arithmetic is
-// the lateral neighbours'.  Tiles, values and accounts are those of the
-// other launch shapes, so it computes the same bits.
-// MINB > 0 caps the registers for MINB resident blocks per SM.
-template <int DIM, int NS, int BS, int MINB, bool PAIR>
-__global__ void __launch_bounds__(BS, MINB)
-    k_np_step32_cp(NPFields F, int n, int naccs, NPConst<float> c) {
-  __shared__ NPStage<DIM, NS, PAIR> stage[BS / 32][2];
-  const int nw = (int)np_warps(n);
-  const int W = gridDim.x * (BS / 32);
-  const int wi = threadIdx.x >> 5;
-  int w = (blockIdx.x * BS + threadIdx.x) >> 5;
-  if (w >= nw) return;  // whole warps leave together
-  np_stage_fill<DIM, NS, PAIR>(F, n, w, stage[wi][0]);
-  cp_async_commit();
-  NPLinks<DIM> cur = np_links<DIM>(F, n, w);
-  for (int t = 0;; t++) {
-    const int wn = w + W;
-    NPLinks<DIM> nxt;
-    if (wn < nw) {
-      np_stage_fill<DIM, NS, PAIR>(F, n, wn, stage[wi][(t + 1) & 1]);
-      nxt = np_links<DIM>(F, n, wn);
-    }
-    cp_async_commit();
-    cp_async_wait<1>();  // this tile's copies have landed
-    __syncwarp();
-    NPLane<DIM, NS> V;
-    np_load_stage<DIM, NS, PAIR>(F, stage[wi][t & 1], cur.q, V);
-    np_tile_update<DIM, NS, PAIR>(F, n, naccs, c, w, cur.f, cur.q, V);
-    __syncwarp();  // every lane has read the stage before it is refilled
-    if (wn >= nw) break;
-    w = wn;
-    cur = nxt;
-  }
-}
-
 // Blocks that fill every SM with the kernel at block size bs (once per
 // kernel; at most the blocks the work needs).
 template <typename K> int resident_grid(K kernel, int bs, long long units) {
@@ -1307,12 +1184,7 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   if constexpr (std::is_same<T, float>::value) {
     const NPFields F = fields32(d, d->d_C[in], Cinl, d->d_C[1 - in], Coutl, d->d_u, d->d_phi,
                                 d->d_acc);
-    if constexpr (MINT == -2 || MINT == -3) {
-      // -3: registers capped for 1024 resident threads per SM
-      auto *kern = k_np_step32_cp<DIM, NS, BS, MINT == -3 ? 1024 / BS : 0, PAIR>;
-      kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
-                                                          make_const<float>(d));
-    } else if constexpr (MINT < 0) {
+    if constexpr (MINT < 0) {
       auto *kern = k_np_step32_pf<DIM, NS, BS, PAIR>;
       kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
                                                           make_const<float>(d));
@@ -1345,10 +1217,6 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 5: launch_step_bs<T, DIM, NS, 128, 1024, PAIR>(d, st, in); break;
     case 6: launch_step_bs<T, DIM, NS, 256, 1024, PAIR>(d, st, in); break;
     case 7: launch_step_bs<T, DIM, NS, 128, -1, PAIR>(d, st, in); break;
-    case 8: launch_step_bs<T, DIM, NS, 128, -2, PAIR>(d, st, in); break;
-    case 9: launch_step_bs<T, DIM, NS, 256, -2, PAIR>(d, st, in); break;
-    case 10: launch_step_bs<T, DIM, NS, 128, -3, PAIR>(d, st, in); break;
-    case 11: launch_step_bs<T, DIM, NS, 256, -3, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1380,19 +1248,17 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 
 // Autotuner: times a few transport steps with each candidate launch shape
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
-// for 1280 resident threads per SM, for 128 and 256 one for 1024, an FP32
-// resident grid that prefetches each warp's next link data, and FP32
-// resident grids of 128 and 256 threads that stage each warp's next tile in
-// shared memory, with and without registers capped for 1024 threads per SM)
-// on the domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// for 1280 resident threads per SM, for 128 and 256 one for 1024, and an
+// FP32 resident grid that prefetches each warp's next link data) on the
+// domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[12] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 256, 128, 256};
+constexpr int kNpVariantBlock[8] = {64, 128, 256, 64, 128, 128, 256, 128};
 cdi_status tune_np(cdi_domain *d) {
-  // variants 7-11 (resident grids) are FP32 launch shapes; for FP64 they
-  // are the plain 128- and 256-thread launches again
-  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
+  // variant 7 (resident grid with prefetch) is an FP32 launch shape; for
+  // FP64 it is the plain 128-thread launch again
+  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7};
   const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
@@ -1438,7 +1304,7 @@ cdi_status tune_np(cdi_domain *d) {
 
 }  // namespace
 
-int cdi_np_shape_block(int v) { return v >= 0 && v < 12 ? kNpVariantBlock[v] : 0; }
+int cdi_np_shape_block(int v) { return v >= 0 && v < 8 ? kNpVariantBlock[v] : 0; }
 
 cdi_status cdi_np_build_flags(cdi_domain *d) {
   dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);

@@ -6,7 +6,10 @@ device footprint fits into the remaining memory budget (first fit in arrival
 order, with an ageing bound so that large requests are not passed over for
 ever); admitted requests run concurrently, each on its own domain with its
 own CUDA stream, so their kernels overlap on the device while earlier ones
-are still running.  Fields
+are still running.  Larger requests get higher stream priorities (the
+device's block scheduler then serves their launches first), so the long
+solves that set the latency tail are slowed little by the short ones that
+fill the gaps.  Fields
 stay resident in device memory for the whole solve; the domain (and its
 memory) is released when the request completes, which admits the next.
 
@@ -43,6 +46,7 @@ class Request:
     D: tuple = (1.33e-9, 2.03e-9)
     tag: object = None
     # filled in by the server
+    priority: int = 0  # CUDA stream priority of the request (lower: served first)
     t_arrival: float = 0.0
     t_start: float = 0.0
     t_done: float = 0.0
@@ -80,6 +84,15 @@ def footprint_bytes(mask: np.ndarray, precision: int, mirror: bool = True) -> in
     return flow + transport + lattice + work + (4 << 20)
 
 
+def size_priority(need: int) -> int:
+    """Stream priority for a request of `need` device bytes: 0 below 256 MiB,
+    then one level higher per doubling (the device clamps to its range)."""
+    levels = 0
+    while need >= (256 << 20) << levels and levels < 5:
+        levels += 1
+    return -levels
+
+
 class Server:
     """Admits requests while slots and memory allow; runs them concurrently.
 
@@ -91,8 +104,9 @@ class Server:
     fits."""
 
     def __init__(self, slots: int = 4, memory_budget: int = 16 << 30, device: int = 0,
-                 solver=None, max_bypass: int | None = None):
+                 solver=None, max_bypass: int | None = None, prioritise_large: bool = True):
         self.solver = solver or solve
+        self.prioritise_large = prioritise_large
         self.slots = slots
         self.budget = memory_budget
         self.device = device
@@ -144,6 +158,7 @@ class Server:
                     self._lock.wait(timeout=0.5)
                     continue
                 req, need, _ = self._waiting.pop(i)
+                req.priority = size_priority(need) if self.prioritise_large else 0
                 for _, _, passed in self._waiting[:i]:
                     passed[0] += 1
                 self._running += 1
@@ -189,8 +204,14 @@ class Server:
 
 
 def solve(req: Request) -> dict:
-    """One request end to end through the C ABI (the plain single solve)."""
-    with cdi.Domain(req.mask, precision=req.precision) as d:
+    """One request end to end through the C ABI (the plain single solve), on
+    a stream of the request's priority."""
+    stream = None
+    if req.priority:
+        import torch
+        stream = torch.cuda.Stream(priority=req.priority)
+    with cdi.Domain(req.mask, precision=req.precision,
+                    stream=stream.cuda_stream if stream is not None else None) as d:
         steps, res, st = d.solve_flow(tol=req.flow_tol, max_steps=req.max_flow_steps,
                                       U_target=req.U_mps, allow_not_converged=True)
         d.set_potential(req.applied_V, c_bulk=req.c0, tol=1e-12)

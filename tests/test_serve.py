@@ -153,3 +153,31 @@ def test_first_fit_admission_and_ageing():
     passed = [k for k in ("s1", "s2", "s3", "s4", "s5") if t[k] < t["big"]]
     assert len(passed) <= 3                      # ageing: big is not passed over for ever
     assert max(t.values()) > t["big"]
+
+
+def test_larger_requests_get_higher_stream_priority():
+    """Stream priority grows one level per doubling of the footprint past
+    256 MiB (lower numbers are served first); the server stamps it on each
+    admitted request, or leaves 0 when prioritising is off."""
+    mib = 1 << 20
+    assert serve.size_priority(10 * mib) == 0
+    assert serve.size_priority(300 * mib) == -1
+    assert serve.size_priority(600 * mib) == -2
+    assert serve.size_priority(1 << 40) == -5
+    seen = {}
+
+    def solver(req):
+        seen[req.tag] = req.priority
+        return {}
+    small, big = np.zeros((32, 64), np.uint8), np.zeros((40, 160, 160), np.uint8)
+    for flag in (True, False):
+        seen.clear()
+        srv = serve.Server(slots=2, memory_budget=64 << 30, solver=solver,
+                           prioritise_large=flag)
+        srv.submit(serve.Request(small, 1.0, 1e-4, 10, tag="small"))
+        srv.submit(serve.Request(big, 1.0, 1e-6, 10, tag="big"))
+        srv.drain(2, timeout=60)
+        srv.close()
+        want = serve.size_priority(serve.footprint_bytes(big, cdi.FP32)) if flag else 0
+        assert seen == {"small": 0, "big": want}
+        assert not flag or want < 0
