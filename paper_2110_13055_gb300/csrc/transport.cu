@@ -724,9 +724,9 @@ __global__ void __launch_bounds__(BS, MINT / BS)
 // (W the warps of the launch) and loads the next tile's link data while it
 // computes the current tile, so that load no longer adds a memory round trip
 // ahead of the neighbour loads.  Tiles and accounts are those of the other
-// launch shapes.
-template <int DIM, int NS, int BS, bool PAIR>
-__global__ void __launch_bounds__(BS)
+// launch shapes.  MINB > 0 caps the registers for MINB resident blocks per SM.
+template <int DIM, int NS, int BS, int MINB, bool PAIR>
+__global__ void __launch_bounds__(BS, MINB)
     k_np_step32_pf(NPFields F, int n, int naccs, NPConst<float> c) {
   const int nw = (int)np_warps(n);
   const int W = gridDim.x * (BS / 32);
@@ -1185,7 +1185,9 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
     const NPFields F = fields32(d, d->d_C[in], Cinl, d->d_C[1 - in], Coutl, d->d_u, d->d_phi,
                                 d->d_acc);
     if constexpr (MINT < 0) {
-      auto *kern = k_np_step32_pf<DIM, NS, BS, PAIR>;
+      // -1: registers as the compiler sees fit; -2: capped for 1024 threads
+      // per SM
+      auto *kern = k_np_step32_pf<DIM, NS, BS, MINT == -2 ? 1024 / BS : 0, PAIR>;
       kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
                                                           make_const<float>(d));
     } else if constexpr (MINT == 0)
@@ -1217,6 +1219,8 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 5: launch_step_bs<T, DIM, NS, 128, 1024, PAIR>(d, st, in); break;
     case 6: launch_step_bs<T, DIM, NS, 256, 1024, PAIR>(d, st, in); break;
     case 7: launch_step_bs<T, DIM, NS, 128, -1, PAIR>(d, st, in); break;
+    case 8: launch_step_bs<T, DIM, NS, 128, -2, PAIR>(d, st, in); break;
+    case 9: launch_step_bs<T, DIM, NS, 256, -2, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1248,17 +1252,18 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 
 // Autotuner: times a few transport steps with each candidate launch shape
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
-// for 1280 resident threads per SM, for 128 and 256 one for 1024, and an
-// FP32 resident grid that prefetches each warp's next link data) on the
-// domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// for 1280 resident threads per SM, for 128 and 256 one for 1024, and FP32
+// resident grids that prefetch each warp's next link data, with registers as
+// the compiler sees fit or capped for 1024 threads per SM) on the domain's
+// stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[8] = {64, 128, 256, 64, 128, 128, 256, 128};
+constexpr int kNpVariantBlock[10] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 256};
 cdi_status tune_np(cdi_domain *d) {
-  // variant 7 (resident grid with prefetch) is an FP32 launch shape; for
-  // FP64 it is the plain 128-thread launch again
-  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7};
+  // variants 7-9 (resident grids with prefetch) are FP32 launch shapes; for
+  // FP64 they are the plain 128- and 256-thread launches again
+  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9};
   const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
@@ -1304,7 +1309,7 @@ cdi_status tune_np(cdi_domain *d) {
 
 }  // namespace
 
-int cdi_np_shape_block(int v) { return v >= 0 && v < 8 ? kNpVariantBlock[v] : 0; }
+int cdi_np_shape_block(int v) { return v >= 0 && v < 10 ? kNpVariantBlock[v] : 0; }
 
 cdi_status cdi_np_build_flags(cdi_domain *d) {
   dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);
