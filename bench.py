@@ -256,6 +256,8 @@ def ours(args, w, mask):
     Nf = 2 * N
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     dom = cdi.Domain(mask, precision=w["prec"], torch_resources=res)
+    if args.launch_shapes:
+        dom.set_launch_shapes(*args.launch_shapes)
     for _ in range(args.warmup):
         run_pipeline(dom, w)
     torch.cuda.synchronize()
@@ -317,6 +319,8 @@ def ours(args, w, mask):
         d2h = 0
         for _ in range(args.e2e_steps):
             d2 = cdi.Domain(mask, precision=w["prec"], torch_resources=res)   # H2D of the mask
+            if args.launch_shapes:
+                d2.set_launch_shapes(*args.launch_shapes)
             run_pipeline(d2, w)
             C = d2.C()                                                          # D2H of the fields
             d2.close()
@@ -352,6 +356,8 @@ def ours(args, w, mask):
                    "flow_steps": info["flow_steps"], "flow_residual": info["flow_residual"],
                    "flow_converged": info["flow_status"] == 0,
                    "np_steps": w["np_steps"], "Gamma_mol_per_m": list(info["Gamma"]),
+                   "launch_shapes": (list(args.launch_shapes) if args.launch_shapes
+                                     else "autotuned"),
                    "C_out_molm3": list(info["C_out"]),
                    "l2": ("flushed between steps (256 MB write); the populations "
                           f"({lbm_bytes / 2e6:.0f} MB) "
@@ -376,14 +382,16 @@ def ours(args, w, mask):
                                         "avg_launch_us": lbm_avg * 1e6,
                                         "algorithmic_bytes_per_launch": lbm_bytes,
                                         "layout_bytes_per_launch": lbm_layout,
-                                        "block": tim["lbm_block"]},
+                                        "block": tim["lbm_block"],
+                                        "shape": tim["lbm_shape"]},
                          "k_np_step": {"GBps": np_bytes / np_avg / 1e9 if np_avg else None,
                                        "frac": np_bytes / np_avg / 1e9 / peak
                                        if np_avg else None,
                                        "avg_launch_us": np_avg * 1e6,
                                        "algorithmic_bytes_per_launch": np_bytes,
                                        "layout_bytes_per_launch": np_layout,
-                                       "block": tim["np_block"]}}},
+                                       "block": tim["np_block"],
+                                       "shape": tim["np_shape"]}}},
         "e2e": e2e,
         "gpu_launches": int(tim["kernel_launches"]),
         "clocks": clk.summary(),
@@ -725,6 +733,10 @@ def main():
     ap.add_argument("--ref-np-steps", type=int, default=0,
                     help="oracle sample: transport steps (0: about 2e7 cell updates)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch-shapes", type=int, nargs=2, default=None,
+                    metavar=("LBM", "NP"),
+                    help="fix the LBM (0-5) and transport (0-9) launch shapes instead of "
+                         "autotuning (a profiler's serialised launches mislead the tuner)")
     ap.add_argument("--flow-steps", type=int, default=0,
                     help="run exactly this many flow steps (multiple of 100) instead of "
                          "converging; for short profiling runs")

@@ -156,6 +156,8 @@ typedef struct {
   int32_t np_block;    /* transport step, picked by the library's autotuner
                           on the first solve (timing only: every block size
                           computes the same bits); 0 before it ran */
+  int32_t lbm_shape;   /* the launch shapes themselves (see */
+  int32_t np_shape;    /* cdi_set_launch_shapes); -1 before they are chosen */
 } cdi_timing;
 
 /* Create a domain from a voxel mask (Sec. 2: marker-and-cell grid, one grid

@@ -69,7 +69,8 @@ class cdi_timing(ctypes.Structure):
     _fields_ = [("flow_ms", c_double), ("flow_launches", c_int64),
                 ("flow_check_ms", c_double), ("psi_ms", c_double), ("psi_iters", c_int64),
                 ("np_ms", c_double), ("np_launches", c_int64), ("kernel_launches", c_int64),
-                ("lbm_block", ctypes.c_int32), ("np_block", ctypes.c_int32)]
+                ("lbm_block", ctypes.c_int32), ("np_block", ctypes.c_int32),
+                ("lbm_shape", ctypes.c_int32), ("np_shape", ctypes.c_int32)]
 
 
 class CDIError(RuntimeError):

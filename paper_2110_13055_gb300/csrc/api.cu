@@ -882,6 +882,8 @@ cdi_status cdi_query_timing(cdi_domain *d, cdi_timing *out, int reset) {
   *out = d->timing;
   out->lbm_block = d->lbm_tuned ? d->lbm_block : 0;
   out->np_block = d->np_tuned ? d->np_block : 0;
+  out->lbm_shape = d->lbm_tuned ? d->lbm_variant : -1;
+  out->np_shape = d->np_tuned ? d->np_variant : -1;
   if (reset) d->timing = cdi_timing{};
   return CDI_OK;
 }

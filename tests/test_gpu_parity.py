@@ -442,6 +442,7 @@ def test_autotuner_picks_a_block_size():
         t = d.timing()
     assert t["lbm_block"] in (64, 128, 256)
     assert t["np_block"] in (64, 128, 256)
+    assert 0 <= t["lbm_shape"] < 6 and 0 <= t["np_shape"] < 10
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -477,6 +478,7 @@ def test_every_launch_shape_same_bits(prec, dim):
             assert np.array_equal(G, G_ref), f"transport shape {ns}"
         t = d.timing()
         assert t["np_block"] == 256 and t["lbm_block"] == 128
+        assert t["np_shape"] == 9 and t["lbm_shape"] == 1
         with pytest.raises(cdi.CDIError):
             d.set_launch_shapes(6, -1)
         with pytest.raises(cdi.CDIError):
