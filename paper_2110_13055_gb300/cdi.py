@@ -530,7 +530,7 @@ class Domain:
 
     def set_launch_shapes(self, lbm_shape: int = -1, np_shape: int = -1):
         """Fix the launch shape of the LBM step (0-5) and of the transport
-        step (0-11); -1 leaves it to the autotuner.  Every shape computes the
+        step (0-9); -1 leaves it to the autotuner.  Every shape computes the
         same bits."""
         set_launch_shapes(self.handle, lbm_shape, np_shape)
 

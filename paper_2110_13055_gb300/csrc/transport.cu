@@ -516,8 +516,7 @@ __device__ __forceinline__ void np_load_lateral(const NPFields &F, const int *q,
 
 // Own, lateral and +x values of warp w's tile, read from the field arrays:
 // the +x neighbour is the next lane's cell (np_finish_x, a shuffle), or for
-// lane 31 the next tile's first home cell (loaded here).  Only loads: the
-// values may stay in flight until np_finish_x.
+// lane 31 the next tile's first home cell (loaded here).
 template <int DIM, int NS, bool PAIR>
 __device__ __forceinline__ void np_issue_loads(const NPFields &F, int n_cells, int w,
                                                unsigned f, const int *q, NPLane<DIM, NS> &V) {
@@ -763,44 +762,6 @@ __global__ void __launch_bounds__(BS, MINB)
     if (wn >= nw) break;
     w = wn;
     cur = nxt;
-  }
-}
-
-// The step software-pipelined over a resident grid: while a warp computes
-// tile w, the loads of tile w + W's own and lateral values (and of its +x
-// neighbour) are in flight, and so are those of tile w + 2W's link data.
-// Each tile's arithmetic then waits for no memory round trip of its own; the
-// price is a second tile's values held in registers.  Tiles, values and
-// accounts are those of the other launch shapes.
-template <int DIM, int NS, int BS, bool PAIR>
-__global__ void __launch_bounds__(BS)
-    k_np_step32_pp(NPFields F, int n, int naccs, NPConst<float> c) {
-  const int nw = (int)np_warps(n);
-  const int W = gridDim.x * (BS / 32);
-  int w = (blockIdx.x * BS + threadIdx.x) >> 5;
-  if (w >= nw) return;  // whole warps leave together
-  NPLinks<DIM> cur = np_links<DIM>(F, n, w);
-  NPLane<DIM, NS> V;
-  np_issue_loads<DIM, NS, PAIR>(F, n, w, cur.f, cur.q, V);
-  int wn = w + W;
-  NPLinks<DIM> nxt;
-  if (wn < nw) nxt = np_links<DIM>(F, n, wn);
-  while (true) {
-    const int wnn = wn + W;
-    NPLane<DIM, NS> Vn;
-    NPLinks<DIM> nxt2;
-    if (wn < nw) {
-      np_issue_loads<DIM, NS, PAIR>(F, n, wn, nxt.f, nxt.q, Vn);
-      if (wnn < nw) nxt2 = np_links<DIM>(F, n, wnn);
-    }
-    np_finish_x<DIM, NS, PAIR>(V);
-    np_tile_update<DIM, NS, PAIR>(F, n, naccs, c, w, cur.f, cur.q, V);
-    if (wn >= nw) break;
-    w = wn;
-    wn = wnn;
-    cur = nxt;
-    nxt = nxt2;
-    V = Vn;
   }
 }
 
@@ -1244,11 +1205,7 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
   if constexpr (std::is_same<T, float>::value) {
     const NPFields F = fields32(d, d->d_C[in], Cinl, d->d_C[1 - in], Coutl, d->d_u, d->d_phi,
                                 d->d_acc);
-    if constexpr (MINT == -3) {
-      auto *kern = k_np_step32_pp<DIM, NS, BS, PAIR>;
-      kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
-                                                          make_const<float>(d));
-    } else if constexpr (MINT < 0) {
+    if constexpr (MINT < 0) {
       // -1: registers as the compiler sees fit; -2: capped for 1024 threads
       // per SM
       auto *kern = k_np_step32_pf<DIM, NS, BS, MINT == -2 ? 1024 / BS : 0, PAIR>;
@@ -1285,8 +1242,6 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 7: launch_step_bs<T, DIM, NS, 128, -1, PAIR>(d, st, in); break;
     case 8: launch_step_bs<T, DIM, NS, 128, -2, PAIR>(d, st, in); break;
     case 9: launch_step_bs<T, DIM, NS, 256, -2, PAIR>(d, st, in); break;
-    case 10: launch_step_bs<T, DIM, NS, 64, -3, PAIR>(d, st, in); break;
-    case 11: launch_step_bs<T, DIM, NS, 128, -3, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1320,17 +1275,16 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
 // for 1280 resident threads per SM, for 128 and 256 one for 1024, and FP32
 // resident grids that prefetch each warp's next link data, with registers as
-// the compiler sees fit or capped for 1024 threads per SM, and software-
-// pipelined resident grids of 64 and 128 threads) on the domain's stream and
-// keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// the compiler sees fit or capped for 1024 threads per SM) on the domain's
+// stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[12] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 256, 64, 128};
+constexpr int kNpVariantBlock[10] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 256};
 cdi_status tune_np(cdi_domain *d) {
-  // variants 7-11 (resident grids) are FP32 launch shapes; for FP64 they
-  // are plain launches of the same block size again
-  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
+  // variants 7-9 (resident grids with prefetch) are FP32 launch shapes; for
+  // FP64 they are plain launches of the same block size again
+  static const int cand[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9};
   const uint64_t key = cdi_tune_key(2, d->dim, d->prec, d->ns, d->n_pore, 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
@@ -1376,7 +1330,7 @@ cdi_status tune_np(cdi_domain *d) {
 
 }  // namespace
 
-int cdi_np_shape_block(int v) { return v >= 0 && v < 12 ? kNpVariantBlock[v] : 0; }
+int cdi_np_shape_block(int v) { return v >= 0 && v < 10 ? kNpVariantBlock[v] : 0; }
 
 cdi_status cdi_np_build_flags(cdi_domain *d) {
   dim3 grid((d->nx + kRowBlock - 1) / kRowBlock, d->ny, d->nz);

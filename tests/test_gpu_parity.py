@@ -442,7 +442,7 @@ def test_autotuner_picks_a_block_size():
         t = d.timing()
     assert t["lbm_block"] in (64, 128, 256)
     assert t["np_block"] in (64, 128, 256)
-    assert 0 <= t["lbm_shape"] < 6 and 0 <= t["np_shape"] < 12
+    assert 0 <= t["lbm_shape"] < 6 and 0 <= t["np_shape"] < 10
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -467,7 +467,7 @@ def test_every_launch_shape_same_bits(prec, dim):
             assert np.array_equal(u, u_ref), f"LBM shape {ls}"
         d.set_potential(0.8)
         C_ref = G_ref = None
-        for ns in range(12):
+        for ns in range(10):
             d.set_launch_shapes(1, ns)
             d.init_transport(Z, D, c0=10.0)
             d.step(40)
@@ -477,12 +477,12 @@ def test_every_launch_shape_same_bits(prec, dim):
             assert np.array_equal(C, C_ref), f"transport shape {ns}"
             assert np.array_equal(G, G_ref), f"transport shape {ns}"
         t = d.timing()
-        assert t["np_block"] == 128 and t["lbm_block"] == 128
-        assert t["np_shape"] == 11 and t["lbm_shape"] == 1
+        assert t["np_block"] == 256 and t["lbm_block"] == 128
+        assert t["np_shape"] == 9 and t["lbm_shape"] == 1
         with pytest.raises(cdi.CDIError):
             d.set_launch_shapes(6, -1)
         with pytest.raises(cdi.CDIError):
-            d.set_launch_shapes(-1, 12)
+            d.set_launch_shapes(-1, 10)
 
 
 @pytest.mark.parametrize("prec", [cdi.FP64, cdi.FP32, cdi.FP32_SPLIT, cdi.FP32_CPAIR])
