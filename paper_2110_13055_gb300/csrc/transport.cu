@@ -356,10 +356,55 @@ __device__ __forceinline__ void np_account(T (&v)[3 * NS], bool io,
   }
 }
 
+// (t.x + t.y) + v as a renormalised FP32 pair (two-sum): acc_add without the
+// memory access.
+__device__ __forceinline__ float2 pair_add(float2 t, float v) {
+  const float s = __fadd_rn(t.x, v);
+  const float bp = __fsub_rn(s, t.x);
+  const float e = __fadd_rn(__fsub_rn(t.x, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+  return make_float2(s, __fadd_rn(t.y, e));
+}
+
+// The FP32 warp accounts of np_account, with the warp's adsorption slots
+// read ahead by lane 0 (np_account_read): a slot belongs to one warp tile, so
+// reading it before the tile's arithmetic gives the value acc_add would read
+// after it, and its latency no longer ends every tile.  (The inflow and
+// outflow slots, touched by the few warps at the inlet and outlet, are read
+// at the end as before.)  The same sums and the same bits as np_account.
 template <int NS>
-__device__ __forceinline__ void np_account_f32(float (&v)[3 * NS], bool io, float2 *acc, int wid,
+__device__ __forceinline__ void np_account_read(float2 (&a)[NS], const float2 *acc, int wid,
+                                                int nw) {
+  if ((threadIdx.x & 31) != 0) return;
+#pragma unroll
+  for (int k = 0; k < NS; k++) a[k] = acc[(size_t)(3 * k) * nw + wid];
+}
+template <int NS>
+__device__ __forceinline__ void np_account_f32(float (&v)[3 * NS], bool io,
+                                               const float2 (&a)[NS], float2 *acc, int wid,
                                                int nw) {
-  np_account<float, NS>(v, io, acc, wid, nw);
+  const bool any_io = __any_sync(0xffffffffu, io);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NS; k++) v[k] = r_add(v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+  if (any_io) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = NS; k < 3 * NS; k++)
+        v[k] = r_add(v[k], __shfl_down_sync(0xffffffffu, v[k], o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      float2 *p = acc + (size_t)(3 * k) * nw + wid;
+      p[0] = pair_add(a[k], v[k]);
+      if (any_io) {
+        acc_add(p + nw, v[NS + k]);
+        acc_add(p + 2 * (size_t)nw, v[2 * NS + k]);
+      }
+    }
+  }
 }
 
 // Two species per packed FP32x2 operation (each component rounded exactly as
@@ -605,6 +650,9 @@ __device__ __forceinline__ void np_tile_update(const NPFields &F, int n_cells, i
   const bool valid = r >= 0 && r < n_cells;
   const bool home = valid && lane != 0;
   const float2 z2 = make_float2(0.f, 0.f);
+  // the warp's adsorption account slots, read before the arithmetic
+  float2 acc_pre[NS];
+  np_account_read<NS>(acc_pre, F.acc, w, naccs);
   // +x face: open and inside the image, else the outlet ghost copies the cell
   const bool xs = (f >> kFaceBit) & 1u, xe = (f >> kEdgeBit) & 1u;
   const bool xp = valid && !xs && !xe;
@@ -700,7 +748,7 @@ __device__ __forceinline__ void np_tile_update(const NPFields &F, int n_cells, i
       if (2 * p + 1 < NS) F.Co[2 * p + 1][r] = Cn.y;
     }
   }
-  np_account_f32<NS>(v, home && (me || xe), F.acc, w, naccs);
+  np_account_f32<NS>(v, home && (me || xe), acc_pre, F.acc, w, naccs);
 }
 
 template <int DIM, int NS, bool PAIR>
@@ -1207,8 +1255,9 @@ void launch_step_bs(cdi_domain *d, cudaStream_t st, int in) {
                                 d->d_acc);
     if constexpr (MINT < 0) {
       // -1: registers as the compiler sees fit; -2: capped for 1024 threads
-      // per SM
-      auto *kern = k_np_step32_pf<DIM, NS, BS, MINT == -2 ? 1024 / BS : 0, PAIR>;
+      // per SM; -3: for 768
+      constexpr int MINB = MINT == -2 ? 1024 / BS : (MINT == -3 ? 768 / BS : 0);
+      auto *kern = k_np_step32_pf<DIM, NS, BS, MINB, PAIR>;
       kern<<<resident_grid(kern, BS, units), BS, 0, st>>>(F, (int)d->n_pore, d->np_accs,
                                                           make_const<float>(d));
     } else if constexpr (MINT == 0)
@@ -1241,7 +1290,7 @@ void launch_step_t(cdi_domain *d, cudaStream_t st, int in) {
     case 6: launch_step_bs<T, DIM, NS, 256, 1024, PAIR>(d, st, in); break;
     case 7: launch_step_bs<T, DIM, NS, 128, -1, PAIR>(d, st, in); break;
     case 8: launch_step_bs<T, DIM, NS, 128, -2, PAIR>(d, st, in); break;
-    case 9: launch_step_bs<T, DIM, NS, 256, -2, PAIR>(d, st, in); break;
+    case 9: launch_step_bs<T, DIM, NS, 128, -3, PAIR>(d, st, in); break;
     default: launch_step_bs<T, DIM, NS, 128, 0, PAIR>(d, st, in); break;
   }
 }
@@ -1275,12 +1324,12 @@ constexpr int kGraphSteps = 64;  // steps per captured transport graph (even)
 // (64, 128 or 256 threads per block; for 64 and 128 also a variant compiled
 // for 1280 resident threads per SM, for 128 and 256 one for 1024, and FP32
 // resident grids that prefetch each warp's next link data, with registers as
-// the compiler sees fit or capped for 1024 threads per SM) on the domain's
-// stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
+// the compiler sees fit or capped for 1024 or 768 threads per SM) on the
+// domain's stream and keeps the fastest.  Accounts are kept per warp of 32 ranks whatever the shape, and
 // the arithmetic of a thread does not depend on its register allocation, so
 // every choice computes the same bits.  Runs once per domain, before
 // cdi_np_init overwrites the concentrations and clears the accounts.
-constexpr int kNpVariantBlock[10] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 256};
+constexpr int kNpVariantBlock[10] = {64, 128, 256, 64, 128, 128, 256, 128, 128, 128};
 cdi_status tune_np(cdi_domain *d) {
   // variants 7-9 (resident grids with prefetch) are FP32 launch shapes; for
   // FP64 they are plain launches of the same block size again

@@ -477,7 +477,7 @@ def test_every_launch_shape_same_bits(prec, dim):
             assert np.array_equal(C, C_ref), f"transport shape {ns}"
             assert np.array_equal(G, G_ref), f"transport shape {ns}"
         t = d.timing()
-        assert t["np_block"] == 256 and t["lbm_block"] == 128
+        assert t["np_block"] == 128 and t["lbm_block"] == 128
         assert t["np_shape"] == 9 and t["lbm_shape"] == 1
         with pytest.raises(cdi.CDIError):
             d.set_launch_shapes(6, -1)
