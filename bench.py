@@ -186,6 +186,15 @@ def recorded_traffic(kernel, workload):
     return rec.get("dram_bytes_per_launch")
 
 
+def roofline_bound(traffic, abytes, layout):
+    """"l2" when the recorded DRAM traffic per launch is well below the bytes
+    the kernel touches (its working set stayed in L2 between launches), else
+    "hbm" (also when no traffic was recorded on the current source)."""
+    if traffic is not None and traffic < 0.8 * (abytes + layout):
+        return "l2"
+    return "hbm"
+
+
 def aggregate(elapsed, units):
     """Whole-job figures under torchrun: the max over ranks of the timed
     region and the sum of the units every rank processed (a host-side gloo
@@ -302,11 +311,7 @@ def ours(args, w, mask):
     peak, peak_kind = measured_peak_gbs()
     achieved = abytes / avg / 1e9 if avg > 0 else 0.0
     traffic = recorded_traffic(kname, args.workload)
-    # DRAM traffic well below the bytes the kernel touches means the working
-    # set stayed in L2 between launches: then the bound is L2, not HBM
-    bound = "hbm"
-    if traffic is not None and traffic < 0.8 * (abytes + layout):
-        bound = "l2"
+    bound = roofline_bound(traffic, abytes, layout)
 
     # end to end through the C ABI with host buffers
     e2e = None
