@@ -212,7 +212,7 @@ def aggregate(elapsed, units):
 
 def algorithmic_bytes(prec, dim, n_flow_pore, n_pore, ns=2):
     """Per-launch algorithmic bytes of the two step kernels, counted from the
-    method alone (populations and fields; SURVEY-style per-site figures):
+    method alone (populations and fields, per site and per cell):
     LBM: Q populations read and written per pore site (4 B FP32, 8 B FP64 or
     an FP32 pair, 2 B BF16); transport: ns concentrations read and written,
     dim velocity components, the potential (4 B in FP32 storage, 8 B in FP64)

@@ -1,5 +1,5 @@
 """Host-side arithmetic of bench.py's roofline: the method's bytes per
-launch (SURVEY-style per-site figures), the layout bytes reported beside
+launch (per site and per cell), the layout bytes reported beside
 them, the L2/HBM bound and the source-hash gate on recorded DRAM traffic."""
 import json
 import os
@@ -21,7 +21,7 @@ def test_method_bytes_per_site_and_cell():
     assert lbm_layout == (8 * n_fp + 2 * 4 * tiles) // 2
     assert npb == (2 * 2 * 8 + 2 * 4 + 4 + 1) * n_pore
     lbm, _, npb, _ = bench.algorithmic_bytes(cdi.FP32, 3, n_fp, n_pore)
-    assert lbm == 152 * n_fp and npb == 33 * n_pore   # the SURVEY figure for 3D FP32
+    assert lbm == 152 * n_fp and npb == 33 * n_pore   # plain FP32 storage in 3D
     lbm, _, npb, _ = bench.algorithmic_bytes(cdi.FP64, 2, n_fp, n_pore)
     assert lbm == 144 * n_fp and npb == (2 * 2 * 8 + 2 * 8 + 8 + 1) * n_pore
 

@@ -60,7 +60,7 @@ def test_coupled_half_channel_matches_oracle(prec, tol):
     relative error amplified by c / |C_Na - C_Cl|.  In this channel the
     charge sits in the resolved double layer, where |C_Na - C_Cl| is of the
     order of c, so the amplification is of order one: psi is held to twice
-    the spec concentration bar, 2e-4 (measured in FP32: 7.9e-5; FP64:
+    the FP32 concentration bar of 1e-4, 2e-4 (measured in FP32: 7.9e-5; FP64:
     1e-9)."""
     m, h, c, psi0, dt, eq10, vt = half_channel(50)
     K, steps = 10, 3001
