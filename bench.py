@@ -740,7 +740,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch-shapes", type=int, nargs=2, default=None,
                     metavar=("LBM", "NP"),
-                    help="fix the LBM (0-6) and transport (0-9) launch shapes instead of "
+                    help="fix the LBM (0-5) and transport (0-9) launch shapes instead of "
                          "autotuning (a profiler's serialised launches mislead the tuner)")
     ap.add_argument("--flow-steps", type=int, default=0,
                     help="run exactly this many flow steps (multiple of 100) instead of "

@@ -258,7 +258,7 @@ cdi_status cdi_set_implicit(cdi_domain *dom, double tol, int max_iter);
 
 /* Launch shapes of the two step kernels (the paper has no counterpart: it
  * states the method, not its launch configuration).  By default (-1) an autotuner
- * times every candidate shape of the LBM step (0-6) and of the transport
+ * times every candidate shape of the LBM step (0-5) and of the transport
  * step (0-9) on the domain's first flow solve and first transport
  * initialisation and keeps the fastest; every shape computes the same bits
  * (the arithmetic of a lattice site or pore cell, and the per-warp account

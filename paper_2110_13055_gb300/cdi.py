@@ -529,7 +529,7 @@ class Domain:
         set_implicit(self.handle, tol, max_iter)
 
     def set_launch_shapes(self, lbm_shape: int = -1, np_shape: int = -1):
-        """Fix the launch shape of the LBM step (0-6) and of the transport
+        """Fix the launch shape of the LBM step (0-5) and of the transport
         step (0-9); -1 leaves it to the autotuner.  Every shape computes the
         same bits."""
         set_launch_shapes(self.handle, lbm_shape, np_shape)

@@ -863,8 +863,7 @@ template <> struct ModeT<M_BF16> { using T = __nv_bfloat16; };
 
 // One even + one odd step.  MINT: 0 registers as the compiler sees fit; > 0
 // capped so that MINT threads share an SM; -1 the odd step as the
-// prefetching grid-stride kernel; -2 the odd step with registers for 640
-// resident threads per SM (single-word storage; pairs as 0).
+// prefetching grid-stride kernel.
 template <int M, int DIM, int BS, int MINT>
 void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
   using T = typename ModeT<M>::T;
@@ -887,7 +886,7 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
         k_lbm_step_split<DIM, false, T1, BS><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
       else
         k_lbm_step_split_occ<DIM, false, T1, BS, MI><<<grid, BS, 0, st>>>(gh, gl, lk, n, c);
-      if constexpr (MINT == -1) {
+      if constexpr (MINT < 0) {
         auto *kern = k_lbm_split_odd_pf<DIM, T1, BS>;
         kern<<<resident_grid(kern, BS, n), BS, 0, st>>>(gh, gl, lk, n, c);
       } else if constexpr (MI == 0) {
@@ -904,12 +903,9 @@ void step_pair_bs(cdi_domain *d, cudaStream_t st, double tau, double force) {
     const A fsrc = A((1.0 - 0.5 / tau) * 3.0 * force);
     const Planes<T, Q> g = make_planes<T, Q>((T *)d->d_g, n);
     k_lbm_step<T, DIM, false, BS, MI><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
-    if constexpr (MINT == -1) {
+    if constexpr (MINT < 0) {
       auto *kern = k_lbm_odd_pf<T, DIM, BS>;
       kern<<<resident_grid(kern, BS, n), BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
-    } else if constexpr (MINT == -2) {
-      // the odd step with registers for 640 resident threads per SM
-      k_lbm_step<T, DIM, true, BS, 640><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
     } else {
       k_lbm_step<T, DIM, true, BS, MI><<<grid, BS, 0, st>>>(g, lk, n, omega, fxh, fsrc);
     }
@@ -928,7 +924,6 @@ void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) 
     case 3: step_pair_bs<M, DIM, 64, OCC>(d, st, tau, force); break;
     case 4: step_pair_bs<M, DIM, 128, OCC>(d, st, tau, force); break;
     case 5: step_pair_bs<M, DIM, 128, -1>(d, st, tau, force); break;
-    case 6: step_pair_bs<M, DIM, 64, -2>(d, st, tau, force); break;
     default: step_pair_bs<M, DIM, 128, 0>(d, st, tau, force); break;
   }
 }
@@ -938,15 +933,14 @@ void launch_step_pair(cdi_domain *d, cudaStream_t st, double tau, double force) 
 // bits (one thread per site, no cross-thread arithmetic), so the choice only
 // changes speed.  Runs once per domain, before its first solve resets the
 // populations.
-constexpr int kLbmVariantBlock[7] = {64, 128, 256, 64, 128, 128, 64};
+constexpr int kLbmVariantBlock[6] = {64, 128, 256, 64, 128, 128};
 template <int M, int DIM>
 cdi_status tune_lbm(cdi_domain *d, double tau, double force) {
   // 64, 128 or 256 threads per block, 64 or 128 with registers capped for
   // more resident warps (FP64 storage skips those: too many spills), and 128
-  // with the prefetching odd step, and 64 with the odd step given registers
-  // for fewer resident warps (single-word storage)
-  static const int cand_all[] = {0, 1, 2, 5, 3, 4, 6};
-  const int n_cand = M == M_F64 ? 4 : (M == M_SPLIT ? 6 : 7);
+  // with the prefetching odd step
+  static const int cand_all[] = {0, 1, 2, 5, 3, 4};
+  const int n_cand = M == M_F64 ? 4 : 6;
   const uint64_t key = cdi_tune_key(1, DIM, M, 0, d->n_flow_pore, tau == 1.0 ? 1 : 0);
   int known = 0;
   if (cdi_tune_lookup(key, &known)) {
@@ -1260,7 +1254,7 @@ cdi_status build_flags(cdi_domain *d) {
 
 }  // namespace
 
-int cdi_lbm_shape_block(int v) { return v >= 0 && v < 7 ? kLbmVariantBlock[v] : 0; }
+int cdi_lbm_shape_block(int v) { return v >= 0 && v < 6 ? kLbmVariantBlock[v] : 0; }
 
 cdi_status cdi_flow_build_flags(cdi_domain *d) {
   return d->dim == 2 ? build_flags<2>(d) : build_flags<3>(d);

@@ -442,7 +442,7 @@ def test_autotuner_picks_a_block_size():
         t = d.timing()
     assert t["lbm_block"] in (64, 128, 256)
     assert t["np_block"] in (64, 128, 256)
-    assert 0 <= t["lbm_shape"] < 7 and 0 <= t["np_shape"] < 10
+    assert 0 <= t["lbm_shape"] < 6 and 0 <= t["np_shape"] < 10
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -458,7 +458,7 @@ def test_every_launch_shape_same_bits(prec, dim):
         m = inputs.grain_pack((64, 64, 96), 0.6, 2.0, 5.0, seed=5)[0]
     with cdi.Domain(m, precision=prec) as d:
         u_ref = None
-        for ls in range(7):
+        for ls in range(6):
             d.set_launch_shapes(ls, 1)
             d.solve_flow(tol=0.0, max_steps=300)
             u = d.u_lattice()
@@ -480,7 +480,7 @@ def test_every_launch_shape_same_bits(prec, dim):
         assert t["np_block"] == 128 and t["lbm_block"] == 128
         assert t["np_shape"] == 9 and t["lbm_shape"] == 1
         with pytest.raises(cdi.CDIError):
-            d.set_launch_shapes(7, -1)
+            d.set_launch_shapes(6, -1)
         with pytest.raises(cdi.CDIError):
             d.set_launch_shapes(-1, 10)
 
