@@ -199,6 +199,94 @@ def psi(mask, psi_s, *, dx=1e-7, c_bulk=10.0, T=T_DEFAULT, eps_r=EPS_R_DEFAULT,
     return out, it.value, rel.value
 
 
+def psi_operator(mask, psi_s, *, lateral_walls=False):
+    """The potential's face rules of Eq. 4 (Sec. 2) as a sparse matrix over
+    the pore cells: (A0 v)_P = sum_f T_f v_P - sum_{pore neighbours} v_nb with
+    T = 1 towards a pore neighbour or the inlet feed (psi = 0), 2 towards a
+    solid face (psi_s at half a cell), 0 at the outlet and at lateral walls;
+    b_P = 2 psi_s per solid face.  Returns ``(A0, b, cells)`` (scipy CSR,
+    right-hand side, lattice indices of the pore cells in order)."""
+    import scipy.sparse as sp
+    m = _mask(mask)
+    dim, nx, ny, nz = _dims(m)
+    m3 = m.reshape(nz, ny, nx)
+    cells = np.flatnonzero(m3.reshape(-1) == 0)
+    index = -np.ones(m3.size, dtype=np.int64)
+    index[cells] = np.arange(len(cells))
+    z, y, x = np.unravel_index(cells, (nz, ny, nx))
+    diag = np.zeros(len(cells))
+    b = np.zeros(len(cells))
+    rows, cols = [], []
+    for a, s in [(0, 1), (0, -1), (1, 1), (1, -1), (2, 1), (2, -1)][:2 * dim]:
+        X, Y, Z = x.copy(), y.copy(), z.copy()
+        if a == 0:
+            X += s
+            inlet, outlet = X < 0, X >= nx
+            inside = ~(inlet | outlet)
+            diag[inlet] += 1.0                   # the feed at psi = 0
+            wall = np.zeros_like(inside)
+        else:
+            C = Y if a == 1 else Z
+            ext = ny if a == 1 else nz
+            C += s
+            beyond = (C < 0) | (C >= ext)
+            wall = beyond if lateral_walls else np.zeros_like(beyond)
+            C %= ext
+            inside = ~wall
+        q = np.zeros(len(cells), dtype=np.int64)
+        q[inside] = (Z[inside] * ny + Y[inside]) * nx + X[inside]
+        solid = inside & (m3.reshape(-1)[q] == 1)
+        pore = inside & ~solid
+        diag[solid] += 2.0
+        b[solid] += 2.0 * psi_s
+        diag[pore] += 1.0
+        rows.append(np.flatnonzero(pore))
+        cols.append(index[q[pore]])
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    n = len(cells)
+    A0 = sp.csr_matrix((np.concatenate([diag, -np.ones(len(r))]),
+                        (np.concatenate([np.arange(n), r]), np.concatenate([np.arange(n), c]))),
+                       shape=(n, n))
+    return A0, b, cells
+
+
+def psi_pb(mask, psi_s, *, dx=1e-7, c_bulk=10.0, T=T_DEFAULT, eps_r=EPS_R_DEFAULT,
+           lambda_D=None, lateral_walls=False, tol=1e-12, max_newton=200):
+    """Eq. 4 with the charge of Eq. 5 at Boltzmann equilibrium (Eq. 9) for a
+    1:1 salt: the nonlinear Poisson-Boltzmann equation whose 1D solution is
+    Eq. 10.  Per pore cell, with the face rules of ``psi_operator`` and
+    kdx2 = (dx / lambda_D)^2,
+        (A0 psi)_P - b_P + kdx2 V_T sinh(psi_P / V_T) = 0.
+    Newton's method from psi = 0: each step solves
+        (A0 + kdx2 cosh(psi / V_T)) psi' = b + kdx2 (psi cosh(psi / V_T) - V_T sinh(psi / V_T))
+    with a sparse LU factorisation, until the residual is below ``tol``
+    relative to |b|.  Returns ``(psi, newton_steps, relres)``; psi in volts on
+    the lattice, 0 in solid cells."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    m = _mask(mask)
+    lam = lambda_D if lambda_D else debye_length(c_bulk, T, eps_r)
+    kdx2 = (dx / lam) ** 2
+    vt = thermal_voltage(T)
+    A0, b, cells = psi_operator(m, psi_s, lateral_walls=lateral_walls)
+    bb = np.linalg.norm(b)
+    psi = np.zeros(len(cells))
+    rel, it = 0.0, 0
+    while True:
+        F = A0 @ psi - b + kdx2 * vt * np.sinh(psi / vt)
+        rel = np.linalg.norm(F) / bb if bb > 0 else 0.0
+        if rel < tol or it >= max_newton:
+            break
+        ch = np.cosh(psi / vt)
+        J = (A0 + sp.diags(kdx2 * ch)).tocsc()
+        psi = spl.spsolve(J, b + kdx2 * (psi * ch - vt * np.sinh(psi / vt)))
+        it += 1
+    out = np.zeros(m.size)
+    out[cells] = psi
+    return out.reshape(m.shape), it, rel
+
+
 # --------------------------------------------------------------------------
 # Transport (Eq. 3) with adsorption (Eq. 6)
 # --------------------------------------------------------------------------
