@@ -123,9 +123,16 @@ typedef struct {
   double c_bulk_molm3; /* bulk salt concentration setting the Debye length of
                           Eq. 10's exponent */
   double lambda_D_m;   /* > 0 overrides that Debye length */
-  int mode;            /* 0: screened (Debye-Hueckel) field; 1: Laplace */
-  double tol;          /* relative residual of the conjugate-gradient solve */
-  int max_iter;
+  int mode;            /* 0: screened (Debye-Hueckel) field; 1: Laplace;
+                          2: nonlinear Poisson-Boltzmann (Eq. 4 with the
+                          Boltzmann charge of Eq. 9 for a 1:1 salt, whose 1D
+                          solution is Eq. 10), by Newton's method around the
+                          conjugate-gradient solve */
+  double tol;          /* relative residual of the conjugate-gradient solve
+                          (mode 2: of the nonlinear equation against the
+                          surface terms; each linear solve runs to tol / 10) */
+  int max_iter;        /* conjugate-gradient iterations (mode 2: per Newton
+                          step, at most 200 steps) */
 } cdi_elec_params;
 
 typedef struct {

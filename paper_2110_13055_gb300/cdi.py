@@ -461,7 +461,8 @@ class Domain:
     def set_potential(self, applied_V, *, T=298.15, eps_r=78.5, c_bulk=10.0, lambda_D=0.0,
                       mode="debye", tol=1e-12, max_iter=100000):
         p = cdi_elec_params(float(T), float(eps_r), float(c_bulk), float(lambda_D or 0.0),
-                            0 if mode == "debye" else 1, float(tol), int(max_iter))
+                            {"debye": 0, "laplace": 1, "pb": 2}[mode], float(tol),
+                            int(max_iter))
         return set_potential(self.handle, applied_V, p)
 
     def init_transport(self, z=(1, -1), D=(1.33e-9, 2.03e-9), c0=10.0, Ka=1e-6, dt=0.0):

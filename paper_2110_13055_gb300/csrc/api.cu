@@ -471,15 +471,16 @@ cdi_status cdi_set_potential(cdi_domain *d, double applied_V, const cdi_elec_par
   if (!d || !p) return cdi_fail(d, CDI_ERR_INVALID_ARG, "NULL argument");
   if (!(p->T_K > 0) || !(p->eps_r > 0) || !std::isfinite(applied_V))
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "T_K and eps_r must be positive");
-  if (p->mode != 0 && p->mode != 1) return cdi_fail(d, CDI_ERR_INVALID_ARG, "mode must be 0 or 1");
-  if (p->mode == 0 && !(p->lambda_D_m > 0) && !(p->c_bulk_molm3 > 0))
-    return cdi_fail(d, CDI_ERR_INVALID_ARG, "screened mode needs c_bulk or lambda_D");
+  if (p->mode < 0 || p->mode > 2)
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  if (p->mode != 1 && !(p->lambda_D_m > 0) && !(p->c_bulk_molm3 > 0))
+    return cdi_fail(d, CDI_ERR_INVALID_ARG, "screened modes need c_bulk or lambda_D");
   if (!(p->tol > 0) || p->max_iter < 1)
     return cdi_fail(d, CDI_ERR_INVALID_ARG, "tol must be > 0 and max_iter >= 1");
   // Physical constants (e and k_B as printed with Eq. 9-10).
   const double e = 1.6e-19, kB = 1.38e-23, F = 96485.0, eps0 = 8.854e-12;
   double kdx2 = 0.0;
-  if (p->mode == 0) {
+  if (p->mode != 1) {
     double lam = p->lambda_D_m > 0
                      ? p->lambda_D_m
                      : std::sqrt(p->eps_r * eps0 * kB * p->T_K / (2.0 * p->c_bulk_molm3 * e * F));
@@ -494,7 +495,9 @@ cdi_status cdi_set_potential(cdi_domain *d, double applied_V, const cdi_elec_par
   d->eps_r = p->eps_r;
   d->psi_tol = p->tol;
   d->psi_max_iter = p->max_iter;
-  cdi_status s = cdi_psi_solve(d, -applied_V, kdx2, nullptr, p->tol, p->max_iter, &it, &rel);
+  cdi_status s =
+      p->mode == 2 ? cdi_psi_pb(d, -applied_V, kdx2, p->tol, p->max_iter, &it, &rel)
+                   : cdi_psi_solve(d, -applied_V, kdx2, nullptr, p->tol, p->max_iter, &it, &rel);
   if (iters_out) *iters_out = it;
   if (relres_out) *relres_out = rel;
   if (s == CDI_OK || s == CDI_ERR_NOT_CONVERGED) d->psi_done = true;

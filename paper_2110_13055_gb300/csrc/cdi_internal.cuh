@@ -348,6 +348,7 @@ enum {
   S_ULAT = 3, S_SCALE = 4,                  // velocity export
   S_CG_RZ = 8, S_CG_PQ = 9, S_CG_ALPHA = 10, S_CG_BETA = 11, S_CG_RR = 12,
   S_CG_BB = 13, S_CG_REL = 14, S_CG_DONE = 15, S_CG_TOL = 16, S_CG_IT = 17,
+  S_PB_FF = 18, S_PB_BB = 19,               // Poisson-Boltzmann Newton residual
   S_RATE = 20, S_DT = 21,                   // time step
   S_OUT = 24,                               // 2*kMaxSpecies: outlet sums
   S_MASS = 32,                              // kMaxSpecies
@@ -420,6 +421,9 @@ cdi_status cdi_np_steps(cdi_domain *d, int64_t n);
 cdi_status cdi_np_reduce(cdi_domain *d);
 cdi_status cdi_np_column_means(cdi_domain *d, int species);
 cdi_status cdi_imp_prepare(cdi_domain *d);
+// Nonlinear Poisson-Boltzmann potential (Newton around the device CG).
+cdi_status cdi_psi_pb(cdi_domain *d, double psi_s, double kdx2, double tol, int max_iter,
+                      int *iters, double *relres);
 // Threads per block of LBM / transport launch shape v (0 if v is no shape).
 int cdi_lbm_shape_block(int v);
 int cdi_np_shape_block(int v);

@@ -118,6 +118,79 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
+// One Newton step of the nonlinear Poisson-Boltzmann equation (Eq. 4 with
+// the Boltzmann charge of Eq. 9 for a 1:1 salt; Eq. 10 in 1D), per pore cell
+//   F_P(psi) = (A0 psi)_P - b_P + kdx2 V_T sinh(psi_P / V_T) = 0,
+// A0 and b the face rules above.  Newton solves
+//   (A0 + kdx2 cosh(psi / V_T)) psi' = b + kdx2 (psi cosh(psi / V_T) - V_T sinh(psi / V_T))
+// by the CG below, warm-started at psi' = psi, so its first residual is -F.
+// This kernel forms F (F.F and b.b into S_PB_FF / S_PB_BB: the Newton test),
+// the CG's diagonal and its start (r = -F, p = r / diag, rz, and the
+// right-hand side's b.b for the CG's relative residual).  psi is only read.
+__global__ void __launch_bounds__(kRedThreads)
+    k_pb_setup(Geo g, const NFlag *__restrict__ fl, double kdx2, double psi_s, double vt,
+               double tol, const double *__restrict__ psi, double *__restrict__ r,
+               double *__restrict__ p, double *__restrict__ diag, double *__restrict__ part,
+               unsigned int *counter, double *scal) {
+  __shared__ double sm[4 * 32];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};  // rz, rhs.rhs, F.F, b.b
+  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < g.N;
+       P += (long long)gridDim.x * blockDim.x) {
+    if (fl[P] & 1) {
+      r[P] = 0.0;
+      p[P] = 0.0;
+      diag[P] = 1.0;
+      continue;
+    }
+    int cx, cy, cz;
+    coords(g, P, cx, cy, cz);
+    double t = 0.0, b = 0.0, off = 0.0;
+    for (int f = 0; f < 2 * g.dim; f++) {
+      long long nb;
+      const int k = face_kind(g, fl, P, cx, cy, cz, f, &nb);
+      if (k == 0) {
+        t += 1.0;
+        off += psi[nb];
+      } else if (k == 2) {
+        t += 1.0;
+      } else if (k == 1) {
+        t += 2.0;
+        b += 2.0 * psi_s;
+      }
+    }
+    const double x = psi[P], ph = x / vt;
+    const double sh = sinh(ph), ch = cosh(ph);
+    const double F = t * x - off - b + kdx2 * vt * sh;
+    const double dg = t + kdx2 * ch;
+    const double rhs = b + kdx2 * (x * ch - vt * sh);
+    diag[P] = dg;
+    r[P] = -F;
+    p[P] = -F / dg;
+    v[0] += F * (F / dg);
+    v[1] += rhs * rhs;
+    v[2] += F * F;
+    v[3] += b * b;
+  }
+  block_reduce<4>(v, sm, OpSum(), 0.0);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; k++) part[k * gridDim.x + blockIdx.x] = v[k];
+  if (last_block(counter, gridDim.x)) {
+    combine_partials<4>(part, gridDim.x, v, sm, OpSum(), 0.0);
+    if (threadIdx.x == 0) {
+      scal[S_CG_RZ] = v[0];
+      scal[S_CG_BB] = v[1];
+      scal[S_CG_RR] = v[2];
+      scal[S_CG_REL] = v[1] > 0.0 ? sqrt(v[2] / v[1]) : 0.0;
+      scal[S_CG_DONE] = (v[1] > 0.0 && v[2] > 0.0) ? 0.0 : 1.0;
+      scal[S_CG_TOL] = tol;
+      scal[S_CG_IT] = 0.0;
+      scal[S_PB_FF] = v[2];
+      scal[S_PB_BB] = v[3];
+      *counter = 0;
+    }
+  }
+}
+
 // q = A p and p.q; alpha = rz / p.q.
 __global__ void __launch_bounds__(kRedThreads)
     k_cg_spmv(Geo g, const NFlag *__restrict__ fl, const double *__restrict__ p,
@@ -233,20 +306,14 @@ __global__ void k_phi(int n, const int *__restrict__ cells, const double *__rest
 
 }  // namespace
 
-cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double *src,
-                         double tol, int max_iter, int *iters, double *relres) {
-  Geo g{d->nx, d->ny, d->nz, d->dim, d->walls, d->N};
-  double *r = d->d_cg, *p = d->d_cg + d->N, *q = d->d_cg + 2 * d->N, *dg = d->d_cg + 3 * d->N;
-  cudaEvent_t ev;
-  cdi_timing_begin(d, &ev);
-  k_cg_setup<<<kRedBlocks, kRedThreads, 0, d->stream>>>(g, d->d_nflags, kdx2, psi_s, src, tol,
-                                                         d->d_psi, r, p, dg, d->d_part,
-                                                         d->d_counter + C_CG1, d->d_scal);
-  d->timing.kernel_launches++;
-  CDI_TRY(d, cudaGetLastError(), "cg setup");
+// CG iterations (the scalars set up by k_cg_setup or k_pb_setup) until the
+// device flags convergence or max_iter iterations ran; the host polls the
+// flag after 8, 16, 32, ... iterations (at most 256 between polls).
+static cdi_status cg_iterate(cdi_domain *d, const Geo &g, double *r, double *p, double *q,
+                             const double *dg, int max_iter, bool *done) {
   int launched = 0;
   int chunk = 8;
-  bool done = false;
+  *done = false;
   while (launched < max_iter) {
     const int n = std::min(chunk, max_iter - launched);
     for (int k = 0; k < n; k++) {
@@ -264,11 +331,37 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double 
             "cg poll");
     CDI_TRY(d, cudaStreamSynchronize(d->stream), "cg poll");
     if (d->h_scal[S_CG_DONE] != 0.0) {
-      done = true;
+      *done = true;
       break;
     }
     chunk = std::min(chunk * 2, 256);
   }
+  return CDI_OK;
+}
+
+static cdi_status finish_potential(cdi_domain *d, cudaEvent_t ev, bool done, int *iters,
+                                   double *relres);
+
+cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double *src,
+                         double tol, int max_iter, int *iters, double *relres) {
+  Geo g{d->nx, d->ny, d->nz, d->dim, d->walls, d->N};
+  double *r = d->d_cg, *p = d->d_cg + d->N, *q = d->d_cg + 2 * d->N, *dg = d->d_cg + 3 * d->N;
+  cudaEvent_t ev;
+  cdi_timing_begin(d, &ev);
+  k_cg_setup<<<kRedBlocks, kRedThreads, 0, d->stream>>>(g, d->d_nflags, kdx2, psi_s, src, tol,
+                                                         d->d_psi, r, p, dg, d->d_part,
+                                                         d->d_counter + C_CG1, d->d_scal);
+  d->timing.kernel_launches++;
+  CDI_TRY(d, cudaGetLastError(), "cg setup");
+  bool done = false;
+  cdi_status cs = cg_iterate(d, g, r, p, q, dg, max_iter, &done);
+  if (cs != CDI_OK) return cs;
+  return finish_potential(d, ev, done, iters, relres);
+}
+
+// phi = psi / V_T for the transport step, the solve's figures to the host.
+static cdi_status finish_potential(cdi_domain *d, cudaEvent_t ev, bool done, int *iters,
+                                   double *relres) {
   // phi keeps FP64 accuracy in both precisions (a double, or an FP32 hi/lo
   // pair): the Boltzmann factor exp(z phi) of a face turns an absolute error
   // of phi into a relative error of C.
@@ -291,6 +384,54 @@ cdi_status cdi_psi_solve(cdi_domain *d, double psi_s, double kdx2, const double 
   if (iters) *iters = it;
   if (relres) *relres = d->h_scal[S_CG_REL];
   return (done || d->h_scal[S_CG_DONE] != 0.0) ? CDI_OK : CDI_ERR_NOT_CONVERGED;
+}
+
+// Nonlinear Poisson-Boltzmann potential: Newton from psi = 0 (its first step
+// is the screened Debye-Hueckel field), each step a CG solve warm-started at
+// the current psi (k_pb_setup), until |F| <= tol |b| (b the surface terms).
+// The problem is the minimum of a strictly convex energy and, psi keeping the
+// sign of psi_s, Newton's iterates approach it monotonically after the first
+// step.  Each CG runs to 0.1 tol of its right-hand side, at most max_iter
+// iterations.  iters: the CG iterations of all steps; relres: |F| / |b|.
+cdi_status cdi_psi_pb(cdi_domain *d, double psi_s, double kdx2, double tol, int max_iter,
+                      int *iters, double *relres) {
+  constexpr int kMaxNewton = 200;
+  Geo g{d->nx, d->ny, d->nz, d->dim, d->walls, d->N};
+  double *r = d->d_cg, *p = d->d_cg + d->N, *q = d->d_cg + 2 * d->N, *dg = d->d_cg + 3 * d->N;
+  cudaEvent_t ev;
+  cdi_timing_begin(d, &ev);
+  CDI_TRY(d, cudaMemsetAsync(d->d_psi, 0, (size_t)d->N * 8, d->stream), "pb start");
+  bool converged = false;
+  double rel = 0.0;
+  int cg_total = 0;
+  for (int step = 0;; step++) {
+    k_pb_setup<<<kRedBlocks, kRedThreads, 0, d->stream>>>(
+        g, d->d_nflags, kdx2, psi_s, d->VT, 0.1 * tol, d->d_psi, r, p, dg, d->d_part,
+        d->d_counter + C_CG1, d->d_scal);
+    d->timing.kernel_launches++;
+    CDI_TRY(d, cudaGetLastError(), "pb setup");
+    CDI_TRY(d, cudaMemcpyAsync(d->h_scal + S_PB_FF, d->d_scal + S_PB_FF, 2 * sizeof(double),
+                               cudaMemcpyDeviceToHost, d->stream),
+            "pb residual");
+    CDI_TRY(d, cudaStreamSynchronize(d->stream), "pb residual");
+    const double ff = d->h_scal[S_PB_FF], bb = d->h_scal[S_PB_BB];
+    rel = bb > 0.0 ? std::sqrt(ff / bb) : 0.0;
+    if (rel < tol) {
+      converged = true;
+      break;
+    }
+    if (step == kMaxNewton) break;
+    bool done = false;
+    cdi_status cs = cg_iterate(d, g, r, p, q, dg, max_iter, &done);
+    if (cs != CDI_OK) return cs;
+    cg_total += (int)d->h_scal[S_CG_IT];
+  }
+  cdi_status s = finish_potential(d, ev, true, nullptr, nullptr);
+  if (s != CDI_OK) return s;
+  d->timing.psi_iters += cg_total;
+  if (iters) *iters = cg_total;
+  if (relres) *relres = rel;
+  return converged ? CDI_OK : CDI_ERR_NOT_CONVERGED;
 }
 
 // Coupled re-solve (Eq. 3-5): the charge term of the current concentrations,
