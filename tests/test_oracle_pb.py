@@ -102,3 +102,13 @@ def test_sign_symmetry_and_bounds():
     b, *_ = O.psi_pb(m, 0.5, dx=1e-7, lambda_D=1e-7, tol=1e-13)
     np.testing.assert_allclose(a, -b, rtol=0, atol=1e-15)
     assert np.all(a[m == 1] == 0) and a.min() >= -0.5 and a.max() <= 0.0
+
+
+def test_first_newton_step_is_the_screened_field():
+    """At psi = 0 the Jacobian is A0 + kdx2 and the right-hand side b: one
+    Newton step gives exactly the Debye-Hueckel field of the C solver."""
+    m, _ = grain_pack((20, 26), 0.6, 1.5, 3.0, seed=10)
+    one, it, _ = O.psi_pb(m, -0.8, dx=1e-7, lambda_D=1.5e-7, max_newton=1)
+    dh, *_ = O.psi(m, -0.8, dx=1e-7, lambda_D=1.5e-7, tol=1e-15)
+    assert it == 1
+    np.testing.assert_allclose(one, dh, rtol=1e-10, atol=1e-14)
